@@ -1,0 +1,702 @@
+/*
+ * nphc_oracle.c -- plain, slow, FP64 CPU restatement of the numerical polynomial
+ * homotopy continuation (NPHC) method of Mehta, "Finding All the Stationary Points
+ * of a Potential Energy Landscape via Numerical Polynomial Homotopy Continuation
+ * Method" (arXiv:1104.5497).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the CUDA library is checked
+ * against.  Only the test suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no code, header, table or constant generator with
+ * the CUDA path, and it never calls it.
+ *
+ * What it computes, step by step and in the paper's order:
+ *   - couplings of the power-law XY ring (section "A First Application", the potential
+ *     V and its exponent), written as J_ij = d_ij^-sigma with d_ij the ring distance,
+ *     optionally scaled by a per-pair disorder factor (1 + eps * g_ij);
+ *   - the polynomial system of Eq. (alg_dec_XY_model_poly): for each free site k the
+ *     gradient equation in s_k = sin(theta_k), c_k = cos(theta_k) and the constraint
+ *     s_k^2 + c_k^2 - 1, with theta_N pinned to 0 (the gauge fixing of that section),
+ *     stored as a plain list of quadratic terms;
+ *   - the total-degree start system Q_i = z_i^2 - 1 with start points z_i = +-1 and the
+ *     gamma-trick homotopy H = gamma (1-t) Q + t P (section "Numerical Polynomial
+ *     Homotopy Continuation Method");
+ *   - a predictor-corrector path tracker from t=0 to t=1 (same section: "Euler's
+ *     predictor and Newton's corrector"; the predictor here is classical RK4 on
+ *     dz/dt = -H_z^-1 H_t, see the readings in the design notes);
+ *   - refinement of endpoints by Newton's method on P to machine precision, the
+ *     solution tolerance Delta_sol and the real tolerance Delta_R (same section);
+ *   - Smale alpha-theory certification (the alphaCertified step of the same section):
+ *     beta = ||DP^-1 P||, gamma <= ||DP^-1|| * ||D^2 P / 2||, alpha = beta * gamma <
+ *     (13 - 3 sqrt 17)/4, a real test at Re z and a non-real test ||Im z|| > 2 beta;
+ *   - theta recovery theta_k = atan2(s_k, c_k) in (-pi, pi], the Hessian of V in
+ *     theta_1..theta_{N-1}, its index (number of negative eigenvalues, introduction)
+ *     and the energy V (section "A First Application").
+ *
+ * Linear algebra is textbook: LU with partial pivoting on the largest modulus (ties to
+ * the lowest row), cyclic Jacobi for symmetric eigenvalues.  No blocking, no fusion.
+ * Every function that has a fixed meaning is exported for the tests to pin.
+ */
+#define _DEFAULT_SOURCE
+#include <complex.h>
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+/* ---------------------------------------------------------------- path statuses -- */
+enum {
+    OR_RUNNING = 0,
+    OR_REACHED = 1,      /* tracked to t = 1 */
+    OR_DIVERGED = 2,     /* ||z||_inf exceeded the divergence radius before t = 1 */
+    OR_MIN_STEP = 3,     /* step size fell below h_min */
+    OR_STEP_BUDGET = 4,  /* more than max_steps step attempts */
+    OR_NONFINITE = 5     /* NaN/Inf appeared */
+};
+
+/* ------------------------------------------------------------ endpoint classes -- */
+enum {
+    OC_NONE = 0,         /* diverged or failed path: no endpoint */
+    OC_SINGULAR = 1,     /* finite endpoint that does not certify (singular or not a solution) */
+    OC_REAL = 2,         /* certified approximate solution, certified real */
+    OC_NONREAL = 3,      /* certified approximate solution, certified non-real */
+    OC_UNDECIDED = 4,    /* certified approximate solution, reality not decided */
+    OC_DUPLICATE = 5,    /* certified, but another path reached the same solution */
+    OC_FAILED = 6        /* tracking stopped before t = 1 without diverging */
+};
+
+/* ------------------------------------------------------------ quadratic system -- */
+/* P_i(z) = sum over terms with eq == i of coef * w(a) * w(b), where w(-1) = 1 and
+ * w(k) = z_k.  Every equation has degree <= 2 (the XY system has degree exactly 2). */
+typedef struct {
+    int n;
+    int nterms;
+    const int *eq, *va, *vb;
+    const double *cre, *cim;
+} qsys;
+
+static inline cplx wvar(const cplx *z, int a) { return a < 0 ? 1.0 : z[a]; }
+
+/* P(z) */
+static void sys_eval(const qsys *S, const cplx *z, cplx *P) {
+    for (int i = 0; i < S->n; i++) P[i] = 0;
+    for (int t = 0; t < S->nterms; t++) {
+        cplx c = S->cre[t] + I * S->cim[t];
+        P[S->eq[t]] += c * wvar(z, S->va[t]) * wvar(z, S->vb[t]);
+    }
+}
+
+/* DP(z), row-major n x n: d/dz_c of c*w(a)*w(b) = c*(delta_ac w(b) + delta_bc w(a)) */
+static void sys_jac(const qsys *S, const cplx *z, cplx *D) {
+    int n = S->n;
+    for (int i = 0; i < n * n; i++) D[i] = 0;
+    for (int t = 0; t < S->nterms; t++) {
+        cplx c = S->cre[t] + I * S->cim[t];
+        int e = S->eq[t], a = S->va[t], b = S->vb[t];
+        if (a >= 0) D[e * n + a] += c * wvar(z, b);
+        if (b >= 0) D[e * n + b] += c * wvar(z, a);
+    }
+}
+
+/* Exported for the tests: P(z) and DP(z) (row-major) of a term-list system. */
+void oracle_sys_eval_jac(int n, int nterms, const int *eq, const int *va, const int *vb,
+                         const double *cre, const double *cim, const double *zre,
+                         const double *zim, double *pre, double *pim, double *dre, double *dim) {
+    qsys S = {n, nterms, eq, va, vb, cre, cim};
+    cplx *z = malloc(sizeof(cplx) * n), *P = malloc(sizeof(cplx) * n),
+         *D = malloc(sizeof(cplx) * n * n);
+    for (int i = 0; i < n; i++) z[i] = zre[i] + I * zim[i];
+    sys_eval(&S, z, P);
+    sys_jac(&S, z, D);
+    for (int i = 0; i < n; i++) { pre[i] = creal(P[i]); pim[i] = cimag(P[i]); }
+    for (int i = 0; i < n * n; i++) { dre[i] = creal(D[i]); dim[i] = cimag(D[i]); }
+    free(z); free(P); free(D);
+}
+
+/* ---------------------------------------------------------------- LU (textbook) -- */
+/* In-place LU with partial pivoting (largest modulus; ties keep the lowest row).
+ * Returns 0, or 1 when a pivot is exactly zero.  piv[k] is the row swapped into k. */
+static int lu_factor(int n, cplx *A, int *piv) {
+    for (int k = 0; k < n; k++) {
+        int p = k;
+        double best = cabs(A[k * n + k]);
+        for (int r = k + 1; r < n; r++) {
+            double v = cabs(A[r * n + k]);
+            if (v > best) { best = v; p = r; }
+        }
+        piv[k] = p;
+        if (best == 0.0 || !isfinite(best)) return 1;
+        if (p != k)
+            for (int c = 0; c < n; c++) {
+                cplx tmp = A[k * n + c]; A[k * n + c] = A[p * n + c]; A[p * n + c] = tmp;
+            }
+        for (int r = k + 1; r < n; r++) {
+            cplx l = A[r * n + k] / A[k * n + k];
+            A[r * n + k] = l;
+            for (int c = k + 1; c < n; c++) A[r * n + c] -= l * A[k * n + c];
+        }
+    }
+    return 0;
+}
+
+/* Solve with the factors of lu_factor (P A = L U, P the interchanges in order k = 0..n-1,
+ * applied to whole rows): b <- P b, then L y = b, then U x = y.  b is overwritten with x. */
+static void lu_apply(int n, const cplx *A, const int *piv, cplx *b) {
+    for (int k = 0; k < n; k++)
+        if (piv[k] != k) { cplx tmp = b[k]; b[k] = b[piv[k]]; b[piv[k]] = tmp; }
+    for (int k = 0; k < n; k++)
+        for (int r = k + 1; r < n; r++) b[r] -= A[r * n + k] * b[k];
+    for (int k = n - 1; k >= 0; k--) {
+        cplx s = b[k];
+        for (int c = k + 1; c < n; c++) s -= A[k * n + c] * b[c];
+        b[k] = s / A[k * n + k];
+    }
+}
+
+static double norm2(int n, const cplx *v) {
+    double s = 0;
+    for (int i = 0; i < n; i++) s += creal(v[i]) * creal(v[i]) + cimag(v[i]) * cimag(v[i]);
+    return sqrt(s);
+}
+
+static double norminf(int n, const cplx *v) {
+    double s = 0;
+    for (int i = 0; i < n; i++) { double a = cabs(v[i]); if (a > s || isnan(a)) s = a; }
+    return s;
+}
+
+/* Exported for the tests: solve A x = b (row-major A, split re/im).  Returns 0 or 1. */
+int oracle_lu_solve(int n, const double *are, const double *aim, const double *bre,
+                    const double *bim, double *xre, double *xim) {
+    cplx *A = malloc(sizeof(cplx) * n * n), *b = malloc(sizeof(cplx) * n);
+    int *piv = malloc(sizeof(int) * n);
+    for (int i = 0; i < n * n; i++) A[i] = are[i] + I * aim[i];
+    for (int i = 0; i < n; i++) b[i] = bre[i] + I * bim[i];
+    int rc = lu_factor(n, A, piv);
+    if (!rc) {
+        lu_apply(n, A, piv, b);
+        for (int i = 0; i < n; i++) { xre[i] = creal(b[i]); xim[i] = cimag(b[i]); }
+    }
+    free(A); free(b); free(piv);
+    return rc;
+}
+
+/* ------------------------------------------------------- symmetric eigenvalues -- */
+/* Cyclic Jacobi rotations on a real symmetric n x n matrix (row-major, destroyed);
+ * eigenvalues, unsorted, in w.  Sweeps until the off-diagonal mass is negligible. */
+static void jacobi_eig(int n, double *A, double *w) {
+    for (int sweep = 0; sweep < 100; sweep++) {
+        double off = 0, tot = 0;
+        for (int p = 0; p < n; p++)
+            for (int q = 0; q < n; q++) {
+                tot += A[p * n + q] * A[p * n + q];
+                if (p != q) off += A[p * n + q] * A[p * n + q];
+            }
+        if (off <= 1e-30 * tot || off == 0.0) break;
+        for (int p = 0; p < n - 1; p++)
+            for (int q = p + 1; q < n; q++) {
+                double apq = A[p * n + q];
+                if (apq == 0.0) continue;
+                double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < n; k++) {   /* columns p, q */
+                    double akp = A[k * n + p], akq = A[k * n + q];
+                    A[k * n + p] = c * akp - s * akq;
+                    A[k * n + q] = s * akp + c * akq;
+                }
+                for (int k = 0; k < n; k++) {   /* rows p, q */
+                    double apk = A[p * n + k], aqk = A[q * n + k];
+                    A[p * n + k] = c * apk - s * aqk;
+                    A[q * n + k] = s * apk + c * aqk;
+                }
+            }
+    }
+    for (int i = 0; i < n; i++) w[i] = A[i * n + i];
+}
+
+/* Exported for the tests: eigenvalues of a real symmetric matrix (unsorted). */
+void oracle_sym_eig(int n, const double *A, double *w) {
+    double *B = malloc(sizeof(double) * n * n);
+    memcpy(B, A, sizeof(double) * n * n);
+    jacobi_eig(n, B, w);
+    free(B);
+}
+
+/* -------------------------------------------------------------- XY power law -- */
+/* Ring distance d_ij = min(|i-j|, N-|i-j|) and couplings J_ij = d_ij^-sigma, each
+ * scaled by (1 + eps * g_ij) when g (an N x N matrix of per-pair draws, symmetric) is
+ * given.  J_ii = 0.  Returns 0, or 1 for invalid arguments. */
+int oracle_xy_couplings(int N, double sigma, const double *g, double eps, double *J) {
+    if (N < 3) return 1;
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            if (i == j) { J[i * N + j] = 0.0; continue; }
+            int d = abs(i - j);
+            if (N - d < d) d = N - d;
+            double v = pow((double)d, -sigma);
+            if (g) v *= 1.0 + eps * g[i * N + j];
+            J[i * N + j] = v;
+        }
+    return 0;
+}
+
+/* Eq. (alg_dec_XY_model_poly) as a term list, with the unknowns ordered
+ * z = (c_1..c_m, s_1..s_m), m = N-1, and theta_N = 0 pinned (c_N = 1, s_N = 0).
+ * Equation k (0 <= k < m):  sum_{j != k} J_kj (s_k c_j - s_j c_k) = 0,
+ * equation m+k:             c_k^2 + s_k^2 - 1 = 0.
+ * The paper's overall factor K (and its split j = 1..(N-1)/2 in both directions) only
+ * rescales each gradient equation; summing over all j != k with J_kj = J_jk is the same
+ * sum.  The arrays must hold at least 2*m*(N-1) + 3*m terms.  Returns nterms. */
+int oracle_xy_terms(int N, const double *J, int *eq, int *va, int *vb, double *cre, double *cim) {
+    int m = N - 1, nt = 0;
+#define TERM(E, A, B, C) do { eq[nt] = (E); va[nt] = (A); vb[nt] = (B); cre[nt] = (C); cim[nt] = 0.0; nt++; } while (0)
+    for (int k = 0; k < m; k++) {
+        int ck = k, sk = m + k;
+        for (int j = 0; j < N; j++) {
+            if (j == k) continue;
+            double Jkj = J[k * N + j];
+            if (j == N - 1) {           /* pinned site: c_N = 1, s_N = 0 */
+                TERM(k, sk, -1, Jkj);   /* s_k * c_N */
+            } else {
+                TERM(k, sk, j, Jkj);        /*  J s_k c_j */
+                TERM(k, m + j, ck, -Jkj);   /* -J s_j c_k */
+            }
+        }
+    }
+    for (int k = 0; k < m; k++) {
+        TERM(m + k, k, k, 1.0);
+        TERM(m + k, m + k, m + k, 1.0);
+        TERM(m + k, -1, -1, -1.0);
+    }
+#undef TERM
+    return nt;
+}
+
+/* ------------------------------------------------------------- path tracking -- */
+typedef struct {
+    double h0;          /* first step size */
+    double h_max;       /* largest step size */
+    double h_min;       /* smallest step size before giving up */
+    double eps_corr;    /* Newton corrector: accept when ||dz|| <= eps (1 + ||z||) */
+    double trust;       /* reject when the first correction exceeds trust (1 + ||z||) */
+    double r_div;       /* divergence radius on ||z||_inf */
+    int max_newton;     /* corrector iterations per step */
+    int max_steps;      /* step attempts per path */
+    int grow_after;     /* consecutive accepted steps before doubling h */
+} oracle_track_opts;
+
+typedef struct {
+    int n;
+    cplx *A, *b, *hz, *k1, *k2, *k3, *k4, *zs, *zp, *P, *Q;
+    int *piv;
+} work;
+
+static void work_init(work *w, int n) {
+    w->n = n;
+    w->A = malloc(sizeof(cplx) * n * n);
+    cplx **v[] = {&w->b, &w->hz, &w->k1, &w->k2, &w->k3, &w->k4, &w->zs, &w->zp, &w->P, &w->Q};
+    for (unsigned i = 0; i < sizeof(v) / sizeof(v[0]); i++) *v[i] = malloc(sizeof(cplx) * n);
+    w->piv = malloc(sizeof(int) * n);
+}
+
+static void work_free(work *w) {
+    free(w->A); free(w->b); free(w->hz); free(w->k1); free(w->k2); free(w->k3); free(w->k4);
+    free(w->zs); free(w->zp); free(w->P); free(w->Q); free(w->piv);
+}
+
+/* H_z(z,t) = gamma (1-t) diag(2 z) + t DP(z), written into w->A. */
+static void hom_jac(const qsys *S, cplx gamma, const cplx *z, double t, work *w) {
+    int n = S->n;
+    sys_jac(S, z, w->A);
+    for (int i = 0; i < n * n; i++) w->A[i] *= t;
+    for (int i = 0; i < n; i++) w->A[i * n + i] += gamma * (1.0 - t) * 2.0 * z[i];
+}
+
+/* dz/dt = -H_z^-1 H_t with H_t = P - gamma Q.  Returns 0 or 1 (singular H_z). */
+static int dzdt(const qsys *S, cplx gamma, const cplx *z, double t, work *w, cplx *out) {
+    int n = S->n;
+    sys_eval(S, z, w->P);
+    for (int i = 0; i < n; i++) out[i] = -(w->P[i] - gamma * (z[i] * z[i] - 1.0));
+    hom_jac(S, gamma, z, t, w);
+    if (lu_factor(n, w->A, w->piv)) return 1;
+    lu_apply(n, w->A, w->piv, out);
+    return 0;
+}
+
+/* One Newton step on H(., t): z += -H_z^-1 H.  Writes ||dz||_2 to *dn. */
+static int newton_hom(const qsys *S, cplx gamma, cplx *z, double t, work *w, double *dn) {
+    int n = S->n;
+    sys_eval(S, z, w->P);
+    for (int i = 0; i < n; i++)
+        w->b[i] = -(gamma * (1.0 - t) * (z[i] * z[i] - 1.0) + t * w->P[i]);
+    hom_jac(S, gamma, z, t, w);
+    if (lu_factor(n, w->A, w->piv)) return 1;
+    lu_apply(n, w->A, w->piv, w->b);
+    for (int i = 0; i < n; i++) z[i] += w->b[i];
+    *dn = norm2(n, w->b);
+    return 0;
+}
+
+static int all_finite(int n, const cplx *z) {
+    for (int i = 0; i < n; i++)
+        if (!isfinite(creal(z[i])) || !isfinite(cimag(z[i]))) return 0;
+    return 1;
+}
+
+/* Track one path from its start point z (in) to its end (out). */
+static int track_path(const qsys *S, cplx gamma, const oracle_track_opts *o, cplx *z,
+                      int *steps_out, double *t_out, work *w) {
+    int n = S->n, accepted = 0, attempts = 0, run = 0, status = OR_RUNNING;
+    double t = 0.0, h = o->h0;
+    while (status == OR_RUNNING) {
+        if (t >= 1.0) { status = OR_REACHED; break; }
+        if (attempts >= o->max_steps) { status = OR_STEP_BUDGET; break; }
+        attempts++;
+        double t1 = t + h, hh = h;
+        if (t1 >= 1.0) { t1 = 1.0; hh = 1.0 - t; }
+        /* classical RK4 on dz/dt = -H_z^-1 H_t */
+        int bad = dzdt(S, gamma, z, t, w, w->k1);
+        if (!bad) { for (int i = 0; i < n; i++) w->zs[i] = z[i] + 0.5 * hh * w->k1[i];
+                    bad = dzdt(S, gamma, w->zs, t + 0.5 * hh, w, w->k2); }
+        if (!bad) { for (int i = 0; i < n; i++) w->zs[i] = z[i] + 0.5 * hh * w->k2[i];
+                    bad = dzdt(S, gamma, w->zs, t + 0.5 * hh, w, w->k3); }
+        if (!bad) { for (int i = 0; i < n; i++) w->zs[i] = z[i] + hh * w->k3[i];
+                    bad = dzdt(S, gamma, w->zs, t1, w, w->k4); }
+        int ok = 0;
+        if (!bad) {
+            for (int i = 0; i < n; i++)
+                w->zp[i] = z[i] + hh / 6.0 * (w->k1[i] + 2.0 * w->k2[i] + 2.0 * w->k3[i] + w->k4[i]);
+            /* Newton corrector at t1; a large first correction means the prediction
+             * left the path's neighbourhood, so the step is rejected */
+            double zn = norm2(n, w->zp);
+            for (int it = 0; it < o->max_newton; it++) {
+                double dn;
+                if (newton_hom(S, gamma, w->zp, t1, w, &dn)) break;
+                if (!all_finite(n, w->zp)) break;
+                if (it == 0 && dn > o->trust * (1.0 + zn)) break;
+                if (dn <= o->eps_corr * (1.0 + norm2(n, w->zp))) { ok = 1; break; }
+            }
+        }
+        if (ok) {
+            memcpy(z, w->zp, sizeof(cplx) * n);
+            t = t1;
+            accepted++;
+            if (++run >= o->grow_after) { run = 0; h = fmin(2.0 * h, o->h_max); }
+            if (norminf(n, z) > o->r_div) status = OR_DIVERGED;
+        } else {
+            run = 0;
+            h *= 0.5;
+            if (h < o->h_min) status = OR_MIN_STEP;
+        }
+    }
+    if (status != OR_DIVERGED && !all_finite(n, z)) status = OR_NONFINITE;
+    *steps_out = accepted;
+    *t_out = t;
+    return status;
+}
+
+typedef struct {
+    const qsys *S;
+    cplx gamma;
+    const oracle_track_opts *o;
+    int64_t path0, npaths;
+    double *zre, *zim;
+    int *status, *steps;
+    double *tend;
+    int64_t next;   /* shared work counter */
+} track_job;
+
+static void *track_worker(void *arg) {
+    track_job *J = arg;
+    int n = J->S->n;
+    work w;
+    work_init(&w, n);
+    cplx *z = malloc(sizeof(cplx) * n);
+    for (;;) {
+        int64_t i = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (i >= J->npaths) break;
+        int64_t p = J->path0 + i;
+        /* start point of path p: z_i = -1 when bit i of p is set, else +1 (the roots of
+         * z_i^2 - 1 = 0, one of the 2^n combinations per path) */
+        for (int k = 0; k < n; k++) z[k] = ((p >> k) & 1) ? -1.0 : 1.0;
+        int steps;
+        double t;
+        int st = track_path(J->S, J->gamma, J->o, z, &steps, &t, &w);
+        for (int k = 0; k < n; k++) {
+            J->zre[i * n + k] = creal(z[k]);
+            J->zim[i * n + k] = cimag(z[k]);
+        }
+        J->status[i] = st;
+        J->steps[i] = steps;
+        J->tend[i] = t;
+    }
+    free(z);
+    work_free(&w);
+    return NULL;
+}
+
+/* Track paths path0 .. path0+npaths-1 of the total-degree homotopy of the quadratic
+ * system (terms), with nthreads host threads.  Endpoints are path-major:
+ * z[i*n + k].  Returns 0, or 1 for invalid arguments. */
+int oracle_track(int n, int nterms, const int *eq, const int *va, const int *vb,
+                 const double *cre, const double *cim, double gamma_re, double gamma_im,
+                 const oracle_track_opts *o, int64_t path0, int64_t npaths, int nthreads,
+                 double *zre, double *zim, int *status, int *steps, double *tend) {
+    if (n < 1 || n > 62 || nthreads < 1 || npaths < 0) return 1;
+    qsys S = {n, nterms, eq, va, vb, cre, cim};
+    track_job J = {&S, gamma_re + I * gamma_im, o, path0, npaths, zre, zim, status, steps, tend, 0};
+    pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
+    for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, track_worker, &J);
+    for (int i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
+    free(th);
+    return 0;
+}
+
+/* -------------------------------------------------------- refine and certify -- */
+/* ||D^2 P / 2|| bound: the quadratic part of P_i is z^T M_i z with M_i symmetric
+ * (a term c z_a z_b puts c on (a,a) when a == b, else c/2 on (a,b) and (b,a)); the
+ * bilinear map (u,v) -> (u^T M_i v)_i has operator norm <= sqrt(sum_i ||M_i||_F^2). */
+double oracle_d2_norm(int n, int nterms, const int *eq, const int *va, const int *vb,
+                      const double *cre, const double *cim) {
+    cplx *M = calloc((size_t)n * n * n, sizeof(cplx));
+    for (int t = 0; t < nterms; t++) {
+        int e = eq[t], a = va[t], b = vb[t];
+        if (a < 0 || b < 0) continue;
+        cplx c = cre[t] + I * cim[t];
+        if (a == b) M[(size_t)e * n * n + a * n + a] += c;
+        else { M[(size_t)e * n * n + a * n + b] += 0.5 * c; M[(size_t)e * n * n + b * n + a] += 0.5 * c; }
+    }
+    double s = 0;
+    for (size_t i = 0; i < (size_t)n * n * n; i++) s += creal(M[i]) * creal(M[i]) + cimag(M[i]) * cimag(M[i]);
+    free(M);
+    return sqrt(s);
+}
+
+/* beta = ||DP(z)^-1 P(z)||_2 and ||DP(z)^-1||_F at z.  Returns 1 if DP(z) is singular. */
+static int beta_and_inv_norm(const qsys *S, const cplx *z, double *beta, double *invF, work *w) {
+    int n = S->n;
+    sys_jac(S, z, w->A);
+    if (lu_factor(n, w->A, w->piv)) return 1;
+    sys_eval(S, z, w->b);
+    lu_apply(n, w->A, w->piv, w->b);
+    *beta = norm2(n, w->b);
+    double s = 0;
+    for (int c = 0; c < n; c++) {
+        for (int i = 0; i < n; i++) w->P[i] = (i == c) ? 1.0 : 0.0;
+        lu_apply(n, w->A, w->piv, w->P);
+        double v = norm2(n, w->P);
+        s += v * v;
+    }
+    *invF = sqrt(s);
+    return 0;
+}
+
+typedef struct {
+    double tol_sol;       /* Delta_sol: ||P(z)||_inf at the refined point */
+    double refine_eps;    /* Newton refinement stops when ||dz|| <= eps (1 + ||z||) */
+    int refine_iters;     /* at most this many refinement steps */
+    double alpha0;        /* alpha threshold, (13 - 3 sqrt 17) / 4 */
+} oracle_cert_opts;
+
+/* Refine and certify one endpoint.  Outputs: class, alpha, beta, residual, alpha at
+ * Re z (the real test).  z is refined in place. */
+static int refine_certify_one(const qsys *S, double d2, const oracle_cert_opts *o, cplx *z,
+                              double *alpha_out, double *beta_out, double *gam_out,
+                              double *res_out, double *alpha_re_out, work *w) {
+    int n = S->n;
+    *alpha_out = INFINITY; *beta_out = INFINITY; *gam_out = INFINITY; *res_out = INFINITY;
+    *alpha_re_out = INFINITY;
+    /* Newton on P at t = 1 */
+    for (int it = 0; it < o->refine_iters; it++) {
+        sys_jac(S, z, w->A);
+        if (lu_factor(n, w->A, w->piv)) break;
+        sys_eval(S, z, w->b);
+        lu_apply(n, w->A, w->piv, w->b);
+        for (int i = 0; i < n; i++) z[i] -= w->b[i];
+        if (!all_finite(n, z)) return OC_SINGULAR;
+        if (norm2(n, w->b) <= o->refine_eps * (1.0 + norm2(n, z))) break;
+    }
+    sys_eval(S, z, w->P);
+    double res = norminf(n, w->P);
+    *res_out = res;
+    double beta, invF;
+    if (beta_and_inv_norm(S, z, &beta, &invF, w)) return OC_SINGULAR;
+    double gam = invF * d2, alpha = beta * gam;
+    *alpha_out = alpha; *beta_out = beta; *gam_out = gam;
+    if (!(res <= o->tol_sol) || !(alpha < o->alpha0)) return OC_SINGULAR;
+    /* real test: alpha at x = Re z, a real point of a real system, so that Newton's
+     * iterates from x stay real and converge to a real solution */
+    cplx *x = w->zs;
+    for (int i = 0; i < n; i++) x[i] = creal(z[i]);
+    double beta_r, invF_r;
+    if (!beta_and_inv_norm(S, x, &beta_r, &invF_r, w)) {
+        double ar = beta_r * invF_r * d2;
+        *alpha_re_out = ar;
+        if (ar < o->alpha0) return OC_REAL;
+    }
+    /* non-real test: z and conj(z) have distinct associated solutions when
+     * ||z - conj z|| = 2 ||Im z|| > 2 (beta(z) + beta(conj z)) = 4 beta(z) */
+    double im = 0;
+    for (int i = 0; i < n; i++) im += cimag(z[i]) * cimag(z[i]);
+    if (2.0 * sqrt(im) > 4.0 * beta) return OC_NONREAL;
+    return OC_UNDECIDED;
+}
+
+typedef struct {
+    const qsys *S;
+    double d2;
+    const oracle_cert_opts *o;
+    int64_t count;
+    double *zre, *zim;
+    const int *status;
+    const double *tend;
+    int *cls;
+    double *alpha, *beta, *gam, *res, *alpha_re;
+    int64_t next;
+} cert_job;
+
+static void *cert_worker(void *arg) {
+    cert_job *C = arg;
+    int n = C->S->n;
+    work w;
+    work_init(&w, n);
+    cplx *z = malloc(sizeof(cplx) * n);
+    for (;;) {
+        int64_t i = __atomic_fetch_add(&C->next, 1, __ATOMIC_RELAXED);
+        if (i >= C->count) break;
+        int st = C->status[i];
+        C->alpha[i] = INFINITY; C->beta[i] = INFINITY; C->gam[i] = INFINITY;
+        C->res[i] = INFINITY; C->alpha_re[i] = INFINITY;
+        if (st == OR_DIVERGED) { C->cls[i] = OC_NONE; continue; }
+        if (st != OR_REACHED) { C->cls[i] = OC_FAILED; continue; }
+        for (int k = 0; k < n; k++) z[k] = C->zre[i * n + k] + I * C->zim[i * n + k];
+        C->cls[i] = refine_certify_one(C->S, C->d2, C->o, z, &C->alpha[i], &C->beta[i],
+                                       &C->gam[i], &C->res[i], &C->alpha_re[i], &w);
+        for (int k = 0; k < n; k++) { C->zre[i * n + k] = creal(z[k]); C->zim[i * n + k] = cimag(z[k]); }
+    }
+    free(z);
+    work_free(&w);
+    return NULL;
+}
+
+/* Refine (in place) and certify count endpoints (path-major z).  cls gets the
+ * endpoint class; duplicates are marked by oracle_dedup afterwards. */
+int oracle_refine_certify(int n, int nterms, const int *eq, const int *va, const int *vb,
+                          const double *cre, const double *cim, const oracle_cert_opts *o,
+                          int64_t count, int nthreads, double *zre, double *zim,
+                          const int *status, const double *tend, int *cls, double *alpha,
+                          double *beta, double *gam, double *res, double *alpha_re) {
+    if (n < 1 || nthreads < 1 || count < 0) return 1;
+    qsys S = {n, nterms, eq, va, vb, cre, cim};
+    double d2 = oracle_d2_norm(n, nterms, eq, va, vb, cre, cim);
+    cert_job C = {&S, d2, o, count, zre, zim, status, tend, cls, alpha, beta, gam, res, alpha_re, 0};
+    pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
+    for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, cert_worker, &C);
+    for (int i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
+    free(th);
+    return 0;
+}
+
+/* ------------------------------------------------------------------- dedup -- */
+typedef struct { double key; int64_t idx; } keyed;
+
+static int cmp_keyed(const void *a, const void *b) {
+    double x = ((const keyed *)a)->key, y = ((const keyed *)b)->key;
+    if (x < y) return -1;
+    if (x > y) return 1;
+    int64_t i = ((const keyed *)a)->idx, j = ((const keyed *)b)->idx;
+    return (i > j) - (i < j);
+}
+
+/* alpha-theory decides whether two certified endpoints z1, z2 approximate the same
+ * solution: they do when alpha(z1) < 0.03 and ||z1 - z2|| < 1 / (20 gamma(z1)), and they
+ * do not when ||z1 - z2|| > 2 (beta1 + beta2) (each lies within 2 beta of its
+ * solution).  A pair that is not proved distinct is counted as the same solution.
+ * Within each such pair the higher path index becomes OC_DUPLICATE.  Candidates are
+ * found by sorting on Re z_0 and comparing every pair whose keys differ by no more
+ * than the largest radius in play.  Returns the number of duplicates. */
+int64_t oracle_dedup(int n, int64_t count, const double *zre, const double *zim,
+                     const double *beta, const double *gam, int *cls) {
+    keyed *K = malloc(sizeof(keyed) * (count > 0 ? count : 1));
+    int64_t nk = 0;
+    double rmax = 0;
+    for (int64_t i = 0; i < count; i++)
+        if (cls[i] == OC_REAL || cls[i] == OC_NONREAL || cls[i] == OC_UNDECIDED) {
+            K[nk].key = zre[i * n];
+            K[nk].idx = i;
+            nk++;
+            double r = fmax(4.0 * beta[i], 1.0 / (20.0 * gam[i]));
+            if (r > rmax) rmax = r;
+        }
+    qsort(K, nk, sizeof(keyed), cmp_keyed);
+    int64_t dups = 0;
+    for (int64_t a = 0; a < nk; a++) {
+        int64_t i = K[a].idx;
+        for (int64_t b = a + 1; b < nk && K[b].key - K[a].key <= rmax; b++) {
+            int64_t j = K[b].idx;
+            double d = 0;
+            for (int k = 0; k < n; k++) {
+                double dr = zre[i * n + k] - zre[j * n + k], di = zim[i * n + k] - zim[j * n + k];
+                d += dr * dr + di * di;
+            }
+            d = sqrt(d);
+            int same_i = beta[i] * gam[i] < 0.03 && d < 1.0 / (20.0 * gam[i]);
+            int same_j = beta[j] * gam[j] < 0.03 && d < 1.0 / (20.0 * gam[j]);
+            int distinct = d > 2.0 * (beta[i] + beta[j]);
+            if (same_i || same_j || !distinct) {
+                int64_t hi = i < j ? j : i;
+                if (cls[hi] != OC_DUPLICATE) { cls[hi] = OC_DUPLICATE; dups++; }
+            }
+        }
+    }
+    free(K);
+    return dups;
+}
+
+/* --------------------------------------------------------------- classify -- */
+/* For a real stationary point (c, s) of the XY ring (m = N-1 free sites):
+ * theta_k = atan2(s_k, c_k) in (-pi, pi] (theta_N = 0), the Hessian of
+ * V = sum_{i<j} J_ij (1 - cos(theta_i - theta_j)) in theta_1..theta_m,
+ *   H_kk = sum_{j != k} J_kj cos(theta_k - theta_j),  H_kl = -J_kl cos(theta_k - theta_l),
+ * its index (number of negative eigenvalues), its smallest |eigenvalue| and the energy V.
+ * hess_out (m*m, may be NULL) receives H. */
+int oracle_xy_classify(int N, const double *J, const double *c, const double *s,
+                       double *theta, int *index, double *energy, double *min_abs_eig,
+                       double *hess_out) {
+    int m = N - 1;
+    double *th = malloc(sizeof(double) * N), *H = malloc(sizeof(double) * m * m),
+           *w = malloc(sizeof(double) * m);
+    for (int k = 0; k < m; k++) {
+        double a = atan2(s[k], c[k]);
+        if (a <= -M_PI) a = M_PI;
+        th[k] = a;
+        theta[k] = a;
+    }
+    th[m] = 0.0;
+    for (int k = 0; k < m; k++)
+        for (int l = 0; l < m; l++) {
+            if (k == l) {
+                double d = 0;
+                for (int j = 0; j < N; j++) if (j != k) d += J[k * N + j] * cos(th[k] - th[j]);
+                H[k * m + k] = d;
+            } else {
+                H[k * m + l] = -J[k * N + l] * cos(th[k] - th[l]);
+            }
+        }
+    if (hess_out) memcpy(hess_out, H, sizeof(double) * m * m);
+    double V = 0;
+    for (int i = 0; i < N; i++)
+        for (int j = i + 1; j < N; j++) V += J[i * N + j] * (1.0 - cos(th[i] - th[j]));
+    jacobi_eig(m, H, w);
+    int neg = 0;
+    double mn = INFINITY;
+    for (int k = 0; k < m; k++) { if (w[k] < 0) neg++; if (fabs(w[k]) < mn) mn = fabs(w[k]); }
+    *index = neg;
+    *energy = V;
+    *min_abs_eig = mn;
+    free(th); free(H); free(w);
+    return 0;
+}

@@ -1,0 +1,100 @@
+"""Pins for the oracle's homotopy tracker, refinement, certification and dedup on
+systems whose solutions are known in closed form."""
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def x2_minus_5():
+    # P(x) = x^2 - 5 as terms: 1 * x * x  +  (-5) * 1 * 1
+    return O.Terms(1, [0, 0], [0, -1], [0, -1], [1.0, -5.0])
+
+
+def test_paper_worked_example_x2_minus_5():
+    """Section 'Numerical Polynomial Homotopy Continuation Method': x^2 - 5 from x^2 - 1
+    gives +-sqrt(5); the paper prints +-(2.236067977 + i 1e-10)."""
+    printed, prec = [float(v) for v in open(os.path.join(GOLDEN, "x2_minus_5.txt"))
+                     .read().split("\n")[-2].split()]
+    for phi in (0.3, 1.9, 4.4):
+        out = O.solve_system(x2_minus_5(), complex(math.cos(phi), math.sin(phi)))
+        assert list(out["status"]) == [O.REACHED, O.REACHED]
+        z = np.sort_complex(out["z"][:, 0])
+        # start point +1 ends at +sqrt 5 and -1 at -sqrt 5 (the paths are x(t) = +-sqrt(1 + 4t)
+        # up to the gamma twist, which cannot swap them because they never meet)
+        assert abs(out["z"][0, 0] - math.sqrt(5)) < 1e-12
+        assert abs(out["z"][1, 0] + math.sqrt(5)) < 1e-12
+        assert abs(abs(z[0].real) - printed) < prec and abs(z[1].real - printed) < prec
+        assert list(out["cls"]) == [O.C_REAL, O.C_REAL]
+        assert out["n_duplicates"] == 0
+
+
+def test_alpha_closed_form_univariate():
+    """For f = x^2 - 5: beta = |f/f'| = |x^2-5|/|2x|, gamma = |f''/(2 f')| = 1/|2x|,
+    so alpha = |x^2 - 5| / (4 |x|^2).  The oracle's bound is exact for n = 1."""
+    T = x2_minus_5()
+    assert T.d2_norm() == pytest.approx(1.0)
+    opts = O.default_cert_opts(refine_iters=0)
+    for x in (2.2 + 0.01j, 2.3, -2.0 + 0.3j):
+        tr = dict(z=np.array([[x]]), status=np.array([O.REACHED], np.int32), tend=np.ones(1))
+        rc = O.refine_certify(T, tr, opts)
+        beta = abs(x * x - 5) / abs(2 * x)
+        gam = 1 / abs(2 * x)
+        assert rc["beta"][0] == pytest.approx(beta, rel=1e-13)
+        assert rc["gamma"][0] == pytest.approx(gam, rel=1e-13)
+        assert rc["alpha"][0] == pytest.approx(beta * gam, rel=1e-13)
+
+
+def product_system(n, seed):
+    """P_i(z) = (w_i - a_i)(w_i - b_i) with w = A z: its 2^n roots are z = A^-1 w,
+    w in prod_i {a_i, b_i}, all nonsingular when a_i != b_i and A is invertible."""
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n)) + 0.5 * np.eye(n)
+    a = rng.standard_normal(n)
+    b = rng.standard_normal(n) + 1j * rng.standard_normal(n) * (rng.random(n) < 0.5)
+    eq, va, vb, co = [], [], [], []
+    for i in range(n):
+        for j in range(n):
+            for k in range(n):
+                eq.append(i); va.append(j); vb.append(k); co.append(A[i, j] * A[i, k])
+        for j in range(n):
+            eq.append(i); va.append(j); vb.append(-1); co.append(-(a[i] + b[i]) * A[i, j])
+        eq.append(i); va.append(-1); vb.append(-1); co.append(a[i] * b[i])
+    roots = [np.linalg.solve(A, np.array(w)) for w in itertools.product(*zip(a, b))]
+    return O.Terms(n, eq, va, vb, co), np.array(roots)
+
+
+@pytest.mark.parametrize("n,seed", [(2, 0), (3, 1), (4, 2), (5, 3)])
+def test_product_system_all_roots(n, seed):
+    T, roots = product_system(n, seed)
+    out = O.solve_system(T, np.exp(1j * 2.1))
+    cert = np.isin(out["cls"], [O.C_REAL, O.C_NONREAL, O.C_UNDECIDED])
+    assert cert.sum() == 2 ** n and out["n_duplicates"] == 0
+    found = out["z"][cert]
+    for r in roots:
+        d = np.linalg.norm(found - r, axis=1)
+        assert d.min() < 1e-10 * (1 + np.linalg.norm(r))
+    # the real test agrees with the construction (w real <=> b_i real for the chosen pair)
+    real_roots = sum(np.abs(r.imag).max() < 1e-12 for r in roots)
+    assert (out["cls"] == O.C_REAL).sum() == real_roots
+
+
+def test_dedup_flags_second_copy():
+    T, roots = product_system(2, 0)
+    z = np.stack([roots[0], roots[1], roots[0] + 1e-13])
+    tr = dict(z=z, status=np.full(3, O.REACHED, np.int32), tend=np.ones(3))
+    rc = O.refine_certify(T, tr)
+    assert O.dedup(2, rc) == 1
+    assert rc["cls"][2] == O.C_DUPLICATE and rc["cls"][0] != O.C_DUPLICATE
+
+
+def test_every_path_gets_a_final_status():
+    T, _ = product_system(3, 7)
+    out = O.track(T, np.exp(0.4j))
+    assert (out["status"] != 0).all() and len(out["status"]) == 8
