@@ -1,0 +1,261 @@
+/*
+ * nphc.h -- C ABI of the GB300 library for numerical polynomial homotopy continuation
+ * (NPHC): all stationary points of the power-law XY ring, after D. Mehta, "Finding All
+ * the Stationary Points of a Potential Energy Landscape via Numerical Polynomial
+ * Homotopy Continuation Method", arXiv:1104.5497.
+ *
+ * The calls follow the paper's statement of the method:
+ *   build the polynomial system from N, sigma and the couplings
+ *       (section "A First Application", Eq. alg_dec_XY_model_poly, theta_N = 0),
+ *   track every path of the total-degree gamma-trick homotopy
+ *       (section "Numerical Polynomial Homotopy Continuation Method"),
+ *   refine, apply the solution and real tolerances and certify with alpha-theory
+ *       (same section: Delta_sol, Delta_R, alphaCertified),
+ *   classify the real stationary points by Hessian index and energy
+ *       (introduction: minima have no negative Hessian eigenvalue; section
+ *       "A First Application": theta_k = atan2(s_k, c_k), V).
+ *
+ * Conventions (every call):
+ *   - Every call returns an nphc_status; none aborts or exits.  On failure
+ *     nphc_last_error() returns a message (thread-local, valid until the next call on
+ *     the same thread).
+ *   - Handles (nphc_system, nphc_result) are created and destroyed by the library.
+ *     Buffers passed in are owned by the caller.
+ *   - "Device" pointers are CUDA global-memory pointers on the current device; "host"
+ *     pointers are ordinary CPU memory.  Which one is stated per argument.
+ *   - Calls that take a stream (a cudaStream_t passed as void*, NULL = legacy default
+ *     stream) are asynchronous and stream-ordered.  nphc_solve and the nphc_result_copy_*
+ *     calls synchronise.
+ *   - Per-path failures are statuses in the endpoint arrays, not call failures.
+ *
+ * Unknowns are ordered z = (c_1..c_m, s_1..s_m), m = N-1, c_k = cos theta_k,
+ * s_k = sin theta_k; equation k (< m) is the gradient equation of site k and equation
+ * m+k is c_k^2 + s_k^2 - 1.  Path p starts at z_i = -1 if bit i of p is set, else +1.
+ * Device endpoint arrays are structure-of-arrays: component i of entry e is at
+ * [i * count + e].
+ */
+#ifndef NPHC_H
+#define NPHC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NPHC_MIN_N 3
+#define NPHC_MAX_N 13
+
+typedef enum nphc_status {
+    NPHC_OK = 0,
+    NPHC_EINVAL = 1,   /* invalid argument (N out of range, non-finite or asymmetric J, |gamma| = 0, NULL) */
+    NPHC_ENOMEM = 2,   /* device or host allocation failed */
+    NPHC_ECUDA = 3,    /* a CUDA call failed; nphc_last_error() has the CUDA message */
+    NPHC_EBUDGET = 4,  /* a device-side iteration limit fired (the run's watchdog) */
+    NPHC_ESTATE = 5    /* call out of order (e.g. results requested before a solve) */
+} nphc_status;
+
+typedef enum nphc_precision {
+    NPHC_PREC_FP64 = 0,   /* plain: every step in FP64 */
+    NPHC_PREC_MIXED = 1   /* FP32 tracking (compensated corrector residual), FP64 hand-off,
+                             re-track, refinement, certification and classification */
+} nphc_precision;
+
+/* Tracking outcome of one path. */
+enum {
+    NPHC_PATH_RUNNING = 0,
+    NPHC_PATH_REACHED = 1,      /* tracked to t = 1 */
+    NPHC_PATH_DIVERGED = 2,     /* ||z||_inf beyond the divergence radius before t = 1 */
+    NPHC_PATH_MIN_STEP = 3,     /* step size fell below h_min */
+    NPHC_PATH_STEP_BUDGET = 4,  /* more than max_steps step attempts */
+    NPHC_PATH_NONFINITE = 5,    /* NaN or Inf in the state */
+    NPHC_PATH_HANDOFF = 6       /* FP32 tracking stopped; FP64 continues from (z, t, h) */
+};
+
+/* Class of one endpoint after refinement, certification and deduplication. */
+enum {
+    NPHC_END_NONE = 0,       /* diverged path: no endpoint */
+    NPHC_END_SINGULAR = 1,   /* reached t = 1 but does not certify (singular or not a solution) */
+    NPHC_END_REAL = 2,       /* certified approximate solution, certified real */
+    NPHC_END_NONREAL = 3,    /* certified approximate solution, certified non-real */
+    NPHC_END_UNDECIDED = 4,  /* certified approximate solution, reality undecided */
+    NPHC_END_DUPLICATE = 5,  /* certified, but a lower path reached the same solution */
+    NPHC_END_FAILED = 6      /* tracking stopped before t = 1 without diverging */
+};
+
+/* Tuning and tolerances.  nphc_options_default() fills the defaults given here. */
+typedef struct nphc_options {
+    nphc_precision precision;  /* NPHC_PREC_MIXED */
+    double gamma_re, gamma_im; /* the homotopy's random complex gamma; default exp(0.5 i) */
+    double tol_sol;            /* Delta_sol: ||P(z)||_inf at the refined point, 1e-10 */
+    double tol_real;           /* Delta_R: max |Im z_k| of a real solution, 1e-7 */
+    double h0, h_max, h_min;   /* first, largest and smallest step in t: 0.01, 0.05, 1e-14 */
+    double eps_fp32;           /* FP32 corrector: accept when ||dz|| <= eps (1 + ||z||), 1e-5 */
+    double eps_fp64;           /* FP64 corrector tolerance, 1e-9 */
+    double trust;              /* reject when the first correction exceeds trust (1 + ||z||), 0.1 */
+    double r_div;              /* FP64 divergence radius on ||z||_inf, 1e5 */
+    double r_div_fp32;         /* FP32 radius at which divergence is decided, 1e4 */
+    double rho_div;            /* FP32 declares divergence above this growth exponent, 0.5 */
+    int max_newton_fp32;       /* corrector iterations per FP32 step, 3 */
+    int max_newton_fp64;       /* corrector iterations per FP64 step, 3 */
+    int max_steps;             /* step attempts per path, 5000 */
+    int grow_after;            /* consecutive accepted steps before h doubles, 3 */
+    int refine_iters;          /* Newton refinement steps at t = 1, 8 */
+    double refine_eps;         /* refinement stops when ||dz|| <= eps (1 + ||z||), 1e-14 */
+    int block_size;            /* threads per block of the FP32 tracker; 0 = automatic */
+    int blocks_per_sm;         /* resident blocks per SM of the FP32 tracker; 0 = automatic */
+} nphc_options;
+
+typedef struct nphc_system nphc_system;   /* opaque; owns the device copy of the couplings */
+typedef struct nphc_result nphc_result;   /* opaque; owns device buffers for all paths */
+
+/* Device endpoint arrays, caller-owned, for the step-by-step calls below.  count
+ * entries; n = 2(N-1) components per point.  Any output pointer may be NULL where a
+ * call does not write it. */
+typedef struct nphc_endpoints {
+    int64_t count;
+    int64_t *path;       /* [count] path index of each entry (input) */
+    double *z_re;        /* [n * count] current or final point, real parts */
+    double *z_im;        /* [n * count] imaginary parts */
+    double *t;           /* [count] homotopy time reached */
+    double *h;           /* [count] step size to resume with */
+    int32_t *status;     /* [count] NPHC_PATH_* */
+    int32_t *steps;      /* [count] accepted steps (cumulative over calls) */
+    int32_t *solves;     /* [count] linear solves spent (cumulative; flop accounting) */
+    int32_t *newton;     /* [count] of which corrector (Newton) solves */
+    int32_t *cls;        /* [count] NPHC_END_* */
+    double *alpha;       /* [count] alpha = beta * gamma bound at the certified point */
+    double *beta;        /* [count] ||DP^-1 P|| */
+    double *gamma;       /* [count] ||DP^-1||_F ||D^2 P / 2|| (bound on Smale's gamma) */
+    double *resid;       /* [count] ||P(z)||_inf at the refined point */
+} nphc_endpoints;
+
+/* Fills *opt with the defaults listed in nphc_options.  NPHC_EINVAL if opt is NULL. */
+nphc_status nphc_options_default(nphc_options *opt);
+
+/* Couplings of the power-law ring (section "A First Application", the potential V):
+ * J_ij = d_ij^-sigma with d_ij = min(|i-j|, N-|i-j|), J_ii = 0, each scaled by
+ * (1 + eps * g_ij) when g (host, N*N row-major, symmetric) is not NULL.  J_out: host,
+ * N*N row-major.  NPHC_EINVAL for N outside [NPHC_MIN_N, NPHC_MAX_N], non-finite sigma,
+ * asymmetric g, or a scaled coupling <= 0. */
+nphc_status nphc_xy_couplings(int N, double sigma, const double *g, double eps, double *J_out);
+
+/* Builds the polynomial system of Eq. (alg_dec_XY_model_poly) for the ring with
+ * couplings J (host, N*N row-major, symmetric, zero diagonal, finite) or, when J is
+ * NULL, J_ij = d_ij^-sigma.  Host only: the couplings travel to the device inside each
+ * kernel launch (constant bank), so the system holds no device memory.
+ * NPHC_EINVAL for N outside [NPHC_MIN_N, NPHC_MAX_N], bad J, or out == NULL. */
+nphc_status nphc_system_create_xy(int N, double sigma, const double *J, nphc_system **out);
+
+/* Dimensions of a system: ring size N, unknowns n = 2(N-1), Bezout number 4^(N-1)
+ * (the number of paths).  Any output may be NULL. */
+nphc_status nphc_system_info(const nphc_system *sys, int *N, int *n, int64_t *npaths);
+
+/* The couplings of a system (host, N*N row-major). */
+nphc_status nphc_system_couplings(const nphc_system *sys, double *J_out);
+
+void nphc_system_destroy(nphc_system *sys);
+
+/* Bytes of device scratch the step-by-step calls need for `count` entries. */
+nphc_status nphc_workspace_size(const nphc_system *sys, int64_t count, size_t *bytes);
+
+/* Tracks entries of ep along H(z,t) = gamma (1-t) Q(z) + t P(z), Q_i = z_i^2 - 1
+ * (section "Numerical Polynomial Homotopy Continuation Method"), with a predictor
+ * (classical RK4 on dz/dt = -H_z^-1 H_t) and a Newton corrector, in precision prec:
+ *   FP64:  plain FP64 tracking;
+ *   MIXED: FP32 tracking; a path the FP32 tracker cannot finish ends with status
+ *          NPHC_PATH_HANDOFF and its (z, t, h) for an FP64 call with resume = 1.
+ * list (device int32, may be NULL) selects entries list[0 .. *list_count - 1]
+ * (list_count: device int32); NULL tracks every entry.  resume = 0 starts each selected
+ * path at its start point; resume = 1 continues from ep's (z, t, h).  Writes z, t, h,
+ * status, steps, solves.  workspace: device scratch of nphc_workspace_size bytes.
+ * NPHC_EINVAL on NULL arrays, count outside [0, 4^(N-1)], or a small workspace. */
+nphc_status nphc_track(const nphc_system *sys, const nphc_options *opt, nphc_precision prec,
+                       const nphc_endpoints *ep, const int32_t *list, const int32_t *list_count,
+                       int resume, void *workspace, size_t workspace_bytes, void *stream);
+
+/* FP64 Newton refinement of every selected entry with status NPHC_PATH_REACHED, then
+ * the paper's solution tolerance and alpha-theory certification: beta = ||DP^-1 P||,
+ * gamma <= ||DP^-1||_F ||D^2P/2||, certified when beta * gamma < (13 - 3 sqrt 17)/4;
+ * real when the same test passes at Re z, non-real when ||Im z|| > 2 beta.  Writes z
+ * (refined), cls, alpha, beta, gamma, resid.  Other statuses get NPHC_END_NONE
+ * (diverged) or NPHC_END_FAILED.  list / list_count as in nphc_track. */
+nphc_status nphc_refine_certify(const nphc_system *sys, const nphc_options *opt,
+                                const nphc_endpoints *ep, const int32_t *list,
+                                const int32_t *list_count, void *stream);
+
+/* Marks NPHC_END_DUPLICATE every certified entry whose solution a lower path index also
+ * reached (alpha-theory: same when ||z1 - z2|| < 1/(20 gamma) with alpha < 0.03, or when
+ * not provably distinct, ||z1 - z2|| <= 2 (beta1 + beta2)), using a device hash on the
+ * endpoints rounded to a grid.  dup_list (device int32[count], may be NULL) receives the
+ * entries of every solution reached more than once and *dup_count (device int32) their
+ * number.  workspace as in nphc_track. */
+nphc_status nphc_dedup(const nphc_system *sys, const nphc_options *opt, const nphc_endpoints *ep,
+                       int32_t *dup_list, int32_t *dup_count, void *workspace,
+                       size_t workspace_bytes, void *stream);
+
+/* For every entry with cls == NPHC_END_REAL: theta_k = atan2(s_k, c_k) in (-pi, pi]
+ * (theta: device [(N-1) * count], SoA), the Hessian of V in theta_1..theta_{N-1}, its
+ * index (device int32 [count]: number of negative eigenvalues), its smallest |eigenvalue|
+ * (device [count], may be NULL) and V = sum_{i<j} J_ij (1 - cos(theta_i - theta_j))
+ * (device [count]).  Other entries get index -1. */
+nphc_status nphc_classify(const nphc_system *sys, const nphc_endpoints *ep, double *theta,
+                          int32_t *index, double *energy, double *min_abs_eig, void *stream);
+
+/* Result counters (nphc_result_counts). */
+enum {
+    NPHC_COUNT_PATHS = 0,
+    NPHC_COUNT_REACHED, NPHC_COUNT_DIVERGED, NPHC_COUNT_FAILED,
+    NPHC_COUNT_REAL, NPHC_COUNT_NONREAL, NPHC_COUNT_UNDECIDED, NPHC_COUNT_SINGULAR,
+    NPHC_COUNT_DUPLICATE,
+    NPHC_COUNT_HANDOFF,        /* paths the FP32 tracker handed to FP64 */
+    NPHC_COUNT_RETRACKED,      /* paths re-tracked in FP64 from t = 0 */
+    NPHC_COUNT_SOLVES,         /* linear solves summed over all tracking calls */
+    NPHC_COUNT_INDEX0,         /* + i: real SPs of Hessian index i, i = 0 .. NPHC_MAX_N-2 */
+    NPHC_NCOUNTS = NPHC_COUNT_INDEX0 + NPHC_MAX_N - 1
+};
+
+/* Allocates device buffers for every path of sys (the result keeps a reference to no
+ * host memory of the caller).  NPHC_ENOMEM when the device is full. */
+nphc_status nphc_result_create(const nphc_system *sys, nphc_result **out);
+
+/* The whole method into an existing result, asynchronously on stream: track every path
+ * (MIXED: FP32, then FP64 for hand-offs and for endpoints that do not certify), refine
+ * and certify, deduplicate (FP64 re-track of every duplicated solution's paths, then
+ * deduplicate again), classify.  No allocation, no host synchronisation. */
+nphc_status nphc_solve_into(const nphc_system *sys, const nphc_options *opt, nphc_result *res,
+                            void *stream);
+
+/* nphc_result_create + nphc_solve_into + stream synchronisation. */
+nphc_status nphc_solve(const nphc_system *sys, const nphc_options *opt, void *stream,
+                       nphc_result **out);
+
+/* Counters (host int64[NPHC_NCOUNTS]); synchronises with the result's last stream. */
+nphc_status nphc_result_counts(const nphc_result *res, int64_t *counts);
+
+/* Real stationary points, ordered by path index, into host buffers of capacity cap:
+ * theta [cap * (N-1)] (row per SP), energy, index, alpha, path.  Any output may be NULL.
+ * *n_out = number of real SPs (may exceed cap; only cap are written). */
+nphc_status nphc_result_copy_sps(const nphc_result *res, int64_t cap, double *theta,
+                                 double *energy, int32_t *index, double *alpha, int64_t *path,
+                                 int64_t *n_out);
+
+/* Every path's endpoint (host, path-major z [cap * n]), status and class.  Any output may
+ * be NULL.  *n_out = number of paths. */
+nphc_status nphc_result_copy_endpoints(const nphc_result *res, int64_t cap, double *z_re,
+                                       double *z_im, int32_t *status, int32_t *cls,
+                                       int64_t *n_out);
+
+/* Device endpoint arrays of a result (valid until nphc_result_destroy). */
+nphc_status nphc_result_endpoints(const nphc_result *res, nphc_endpoints *ep);
+
+void nphc_result_destroy(nphc_result *res);
+
+/* Message of the last failed call on this thread ("" when none). */
+const char *nphc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NPHC_H */

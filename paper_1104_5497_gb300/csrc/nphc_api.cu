@@ -1,0 +1,673 @@
+// nphc_api.cu -- host implementation of the C ABI declared in include/nphc.h.
+//
+// The system builder (couplings, FP32/FP64 coupling tables, ||D^2 P/2||) runs on the
+// host; the couplings reach the kernels as launch parameters (constant bank), so a
+// system owns no device memory.  A result owns one device allocation that holds every
+// per-path array, the work lists, the counters and the deduplication scratch.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "nphc.h"
+#include "nphc_internal.cuh"
+#include "nphc_kernels.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+nphc_status fail(nphc_status s, const std::string &msg) {
+    g_err = msg;
+    return s;
+}
+
+#define NPHC_CK(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess)                                                             \
+            return fail(NPHC_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));   \
+    } while (0)
+
+constexpr double kDedupDelta = 1e-6;   // pitch of the deduplication grid
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int64_t table_size_for(int64_t count) {
+    int64_t t = 1024;
+    while (t < 2 * count) t <<= 1;
+    return t;
+}
+
+// Device scratch: [queue counters | dedup table | rep | minpath | gsize | amb | inlist]
+struct WsLayout {
+    size_t queue, table, rep, minpath, gsize, amb, inlist, total;
+    int64_t tsize;
+};
+
+WsLayout ws_layout(int64_t count) {
+    WsLayout L;
+    L.tsize = table_size_for(count);
+    size_t o = 0;
+    L.queue = o;   o += align256(64);
+    L.table = o;   o += align256(sizeof(int32_t) * L.tsize);
+    L.rep = o;     o += align256(sizeof(int32_t) * count);
+    L.minpath = o; o += align256(sizeof(int64_t) * count);
+    L.gsize = o;   o += align256(sizeof(int32_t) * count);
+    L.amb = o;     o += align256(sizeof(int32_t) * count);
+    L.inlist = o;  o += align256(sizeof(int32_t) * count);
+    L.total = o;
+    return L;
+}
+
+DedupScratch dedup_scratch(void *ws, const WsLayout &L) {
+    char *b = static_cast<char *>(ws);
+    DedupScratch w;
+    w.table = reinterpret_cast<int32_t *>(b + L.table);
+    w.table_size = L.tsize;
+    w.rep = reinterpret_cast<int32_t *>(b + L.rep);
+    w.minpath = reinterpret_cast<long long *>(b + L.minpath);
+    w.gsize = reinterpret_cast<int32_t *>(b + L.gsize);
+    w.amb = reinterpret_cast<int32_t *>(b + L.amb);
+    w.inlist = reinterpret_cast<int32_t *>(b + L.inlist);
+    return w;
+}
+
+unsigned long long *ws_queue(void *ws, int slot) {
+    return reinterpret_cast<unsigned long long *>(static_cast<char *>(ws)) + slot;
+}
+
+}  // namespace
+
+struct nphc_system {
+    int N, M, n;
+    int64_t npaths;
+    std::vector<double> J;   // N x N
+    XYSys xs;                // coupling tables; gamma is filled per call
+};
+
+struct nphc_result {
+    int N, M, n;
+    int64_t P;
+    void *block;             // single device allocation
+    size_t bytes;
+    nphc_endpoints ep;       // device arrays for all paths
+    double *theta, *energy, *mineig;
+    int32_t *index, *flags, *list[3], *lcount, *real_list;
+    int64_t *counts;
+    double *o_theta, *o_energy, *o_alpha;
+    int32_t *o_index;
+    int64_t *o_path;
+    void *ws;
+    size_t ws_bytes;
+    cudaStream_t stream;
+    bool solved;
+};
+
+extern "C" {
+
+const char *nphc_last_error(void) { return g_err.c_str(); }
+
+nphc_status nphc_options_default(nphc_options *o) {
+    if (!o) return fail(NPHC_EINVAL, "nphc_options_default: NULL");
+    std::memset(o, 0, sizeof(*o));
+    o->precision = NPHC_PREC_MIXED;
+    o->gamma_re = std::cos(0.5);
+    o->gamma_im = std::sin(0.5);
+    o->tol_sol = 1e-10;
+    o->tol_real = 1e-7;
+    o->h0 = 0.01;
+    o->h_max = 0.05;
+    o->h_min = 1e-14;
+    o->eps_fp32 = 1e-5;
+    o->eps_fp64 = 1e-9;
+    o->trust = 0.1;
+    o->r_div = 1e5;
+    o->r_div_fp32 = 1e4;
+    o->rho_div = 0.5;
+    o->max_newton_fp32 = 3;
+    o->max_newton_fp64 = 3;
+    o->max_steps = 5000;
+    o->grow_after = 3;
+    o->refine_iters = 8;
+    o->refine_eps = 1e-14;
+    o->block_size = 0;
+    o->blocks_per_sm = 0;
+    return NPHC_OK;
+}
+
+nphc_status nphc_xy_couplings(int N, double sigma, const double *g, double eps, double *J) {
+    if (N < NPHC_MIN_N || N > NPHC_MAX_N) return fail(NPHC_EINVAL, "N outside [3, 13]");
+    if (!std::isfinite(sigma)) return fail(NPHC_EINVAL, "sigma not finite");
+    if (!J) return fail(NPHC_EINVAL, "J_out is NULL");
+    if (g) {
+        if (!std::isfinite(eps)) return fail(NPHC_EINVAL, "eps not finite");
+        for (int i = 0; i < N; i++)
+            for (int j = 0; j < N; j++)
+                if (!std::isfinite(g[i * N + j]) || g[i * N + j] != g[j * N + i])
+                    return fail(NPHC_EINVAL, "g not finite and symmetric");
+    }
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            if (i == j) {
+                J[i * N + j] = 0.0;
+                continue;
+            }
+            const int d = std::min(std::abs(i - j), N - std::abs(i - j));
+            double v = std::pow((double)d, -sigma);
+            if (g) v *= 1.0 + eps * g[i * N + j];
+            if (!(v > 0.0) || !std::isfinite(v)) return fail(NPHC_EINVAL, "coupling <= 0 or not finite");
+            J[i * N + j] = v;
+        }
+    return NPHC_OK;
+}
+
+nphc_status nphc_system_create_xy(int N, double sigma, const double *J, nphc_system **out) {
+    if (!out) return fail(NPHC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (N < NPHC_MIN_N || N > NPHC_MAX_N) return fail(NPHC_EINVAL, "N outside [3, 13]");
+    std::vector<double> Jv(N * N);
+    if (J) {
+        for (int i = 0; i < N; i++)
+            for (int j = 0; j < N; j++) {
+                const double v = J[i * N + j];
+                if (!std::isfinite(v)) return fail(NPHC_EINVAL, "J not finite");
+                if (v != J[j * N + i]) return fail(NPHC_EINVAL, "J not symmetric");
+                if (i == j && v != 0.0) return fail(NPHC_EINVAL, "J diagonal not zero");
+                Jv[i * N + j] = v;
+            }
+    } else {
+        nphc_status s = nphc_xy_couplings(N, sigma, nullptr, 0.0, Jv.data());
+        if (s != NPHC_OK) return s;
+    }
+    nphc_system *S = new (std::nothrow) nphc_system;
+    if (!S) return fail(NPHC_ENOMEM, "host allocation");
+    S->N = N;
+    S->M = N - 1;
+    S->n = 2 * (N - 1);
+    S->npaths = (int64_t)1 << S->n;
+    S->J = Jv;
+    std::memset(&S->xs, 0, sizeof(S->xs));
+    S->xs.N = N;
+    double d2 = 2.0 * S->M;   // each constraint c^2 + s^2 - 1 contributes ||M_g||_F^2 = 2
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            S->xs.Jf[i * NPHC_JSTRIDE + j] = (float)Jv[i * N + j];
+            S->xs.Jd[i * NPHC_JSTRIDE + j] = Jv[i * N + j];
+            // gradient row i: J_ij (s_i c_j - s_j c_i) puts J_ij / 2 on four symmetric
+            // entries when j is free, so ||M_fi||_F^2 gains J_ij^2
+            if (i < S->M && j < S->M && i != j) d2 += Jv[i * N + j] * Jv[i * N + j];
+        }
+    S->xs.d2norm = std::sqrt(d2);
+    *out = S;
+    return NPHC_OK;
+}
+
+nphc_status nphc_system_info(const nphc_system *S, int *N, int *n, int64_t *npaths) {
+    if (!S) return fail(NPHC_EINVAL, "system is NULL");
+    if (N) *N = S->N;
+    if (n) *n = S->n;
+    if (npaths) *npaths = S->npaths;
+    return NPHC_OK;
+}
+
+nphc_status nphc_system_couplings(const nphc_system *S, double *J) {
+    if (!S || !J) return fail(NPHC_EINVAL, "NULL argument");
+    std::memcpy(J, S->J.data(), sizeof(double) * S->J.size());
+    return NPHC_OK;
+}
+
+void nphc_system_destroy(nphc_system *S) { delete S; }
+
+nphc_status nphc_workspace_size(const nphc_system *S, int64_t count, size_t *bytes) {
+    if (!S || !bytes || count < 0) return fail(NPHC_EINVAL, "invalid argument");
+    *bytes = ws_layout(count).total;
+    return NPHC_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------ internals --
+namespace {
+
+nphc_status check_opt(const nphc_options *o) {
+    if (!o) return fail(NPHC_EINVAL, "options are NULL");
+    const double g2 = o->gamma_re * o->gamma_re + o->gamma_im * o->gamma_im;
+    if (!(g2 > 0.0) || !std::isfinite(g2)) return fail(NPHC_EINVAL, "|gamma| = 0 or not finite");
+    if (!(o->h0 > 0 && o->h_max >= o->h0 && o->h_min > 0 && o->eps_fp32 > 0 && o->eps_fp64 > 0 &&
+          o->trust > 0 && o->r_div > 0 && o->r_div_fp32 > 0 && o->max_newton_fp32 > 0 &&
+          o->max_newton_fp64 > 0 && o->max_steps > 0 && o->grow_after > 0 && o->refine_iters >= 0))
+        return fail(NPHC_EINVAL, "options out of range");
+    return NPHC_OK;
+}
+
+XYSys sys_with_gamma(const nphc_system *S, const nphc_options *o) {
+    XYSys x = S->xs;
+    x.gre = o->gamma_re;
+    x.gim = o->gamma_im;
+    return x;
+}
+
+XYCtl make_ctl(const nphc_options *o, bool fp32, bool resume, bool accumulate) {
+    XYCtl c;
+    c.h0 = o->h0;
+    c.hmax = o->h_max;
+    c.hmin = o->h_min;
+    c.eps = fp32 ? o->eps_fp32 : o->eps_fp64;
+    c.trust = o->trust;
+    c.rdiv = o->r_div;
+    c.rdiv_soft = fp32 ? o->r_div_fp32 : o->r_div;
+    c.rho_div = o->rho_div;
+    c.max_newton = fp32 ? o->max_newton_fp32 : o->max_newton_fp64;
+    c.max_steps = o->max_steps;
+    c.grow_after = o->grow_after;
+    c.handoff = fp32 ? 1 : 0;
+    c.resume = resume ? 1 : 0;
+    c.accumulate = accumulate ? 1 : 0;
+    return c;
+}
+
+EPView view(const nphc_endpoints *e) {
+    EPView v;
+    v.count = e->count;
+    v.path = e->path;
+    v.z_re = e->z_re;
+    v.z_im = e->z_im;
+    v.t = e->t;
+    v.h = e->h;
+    v.status = e->status;
+    v.steps = e->steps;
+    v.solves = e->solves;
+    v.newton = e->newton;
+    v.cls = e->cls;
+    v.alpha = e->alpha;
+    v.beta = e->beta;
+    v.gamma = e->gamma;
+    v.resid = e->resid;
+    return v;
+}
+
+nphc_status track_impl(const nphc_system *S, const nphc_options *o, nphc_precision prec,
+                       const nphc_endpoints *ep, const int32_t *list, const int32_t *list_count,
+                       bool resume, bool accumulate, void *ws, int queue_slot, cudaStream_t st) {
+    const bool f32 = prec == NPHC_PREC_MIXED;
+    const XYSys xs = sys_with_gamma(S, o);
+    const XYCtl ctl = make_ctl(o, f32, resume, accumulate);
+    WorkList wl;
+    wl.list = list;
+    wl.list_count = list_count;
+    wl.queue = ws_queue(ws, queue_slot);
+    NPHC_CK(cudaMemsetAsync(wl.queue, 0, sizeof(unsigned long long), st));
+    int grid = 0;
+    if (f32 && o->blocks_per_sm > 0) {
+        int dev = 0, sms = 0;
+        NPHC_CK(cudaGetDevice(&dev));
+        NPHC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        grid = sms * o->blocks_per_sm;
+    }
+    const EPView v = view(ep);
+    if (f32)
+        NPHC_CK(launch_xy_track_f32(S->M, xs, ctl, v, wl, 0, grid, st));
+    else
+        NPHC_CK(launch_xy_track_f64(S->M, xs, ctl, v, wl, 0, 0, st));
+    return NPHC_OK;
+}
+
+nphc_status check_ep(const nphc_system *S, const nphc_endpoints *ep, bool certify) {
+    if (!S || !ep) return fail(NPHC_EINVAL, "NULL argument");
+    if (ep->count < 0 || ep->count > S->npaths || ep->count > INT32_MAX)
+        return fail(NPHC_EINVAL, "endpoint count out of range");
+    if (!ep->path || !ep->z_re || !ep->z_im || !ep->t || !ep->h || !ep->status || !ep->steps ||
+        !ep->solves || !ep->newton)
+        return fail(NPHC_EINVAL, "endpoint arrays missing");
+    if (certify && (!ep->cls || !ep->alpha || !ep->beta || !ep->gamma || !ep->resid))
+        return fail(NPHC_EINVAL, "certification arrays missing");
+    return NPHC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nphc_status nphc_track(const nphc_system *S, const nphc_options *o, nphc_precision prec,
+                       const nphc_endpoints *ep, const int32_t *list, const int32_t *list_count,
+                       int resume, void *ws, size_t ws_bytes, void *stream) {
+    nphc_status s;
+    if ((s = check_ep(S, ep, false)) != NPHC_OK) return s;
+    if ((s = check_opt(o)) != NPHC_OK) return s;
+    if (prec != NPHC_PREC_FP64 && prec != NPHC_PREC_MIXED) return fail(NPHC_EINVAL, "precision");
+    if ((list == nullptr) != (list_count == nullptr)) return fail(NPHC_EINVAL, "list without count");
+    if (!ws || ws_bytes < ws_layout(ep->count).total) return fail(NPHC_EINVAL, "workspace too small");
+    return track_impl(S, o, prec, ep, list, list_count, resume != 0, resume != 0, ws, 0,
+                      (cudaStream_t)stream);
+}
+
+nphc_status nphc_refine_certify(const nphc_system *S, const nphc_options *o,
+                                const nphc_endpoints *ep, const int32_t *list,
+                                const int32_t *list_count, void *stream) {
+    nphc_status s;
+    if ((s = check_ep(S, ep, true)) != NPHC_OK) return s;
+    if ((s = check_opt(o)) != NPHC_OK) return s;
+    if ((list == nullptr) != (list_count == nullptr)) return fail(NPHC_EINVAL, "list without count");
+    WorkList wl;
+    wl.list = list;
+    wl.list_count = list_count;
+    wl.queue = nullptr;
+    NPHC_CK(launch_xy_refine_certify(S->M, sys_with_gamma(S, o), o->tol_sol, o->refine_eps,
+                                     o->refine_iters, view(ep), ep->count, wl, (cudaStream_t)stream));
+    return NPHC_OK;
+}
+
+nphc_status nphc_dedup(const nphc_system *S, const nphc_options *o, const nphc_endpoints *ep,
+                       int32_t *dup_list, int32_t *dup_count, void *ws, size_t ws_bytes,
+                       void *stream) {
+    nphc_status s;
+    if ((s = check_ep(S, ep, true)) != NPHC_OK) return s;
+    (void)o;
+    if ((dup_list == nullptr) != (dup_count == nullptr)) return fail(NPHC_EINVAL, "list without count");
+    const WsLayout L = ws_layout(ep->count);
+    if (!ws || ws_bytes < L.total) return fail(NPHC_EINVAL, "workspace too small");
+    NPHC_CK(launch_dedup(view(ep), S->n, kDedupDelta, dedup_scratch(ws, L), dup_list, dup_count,
+                         (cudaStream_t)stream));
+    return NPHC_OK;
+}
+
+nphc_status nphc_classify(const nphc_system *S, const nphc_endpoints *ep, double *theta,
+                          int32_t *index, double *energy, double *min_abs_eig, void *stream) {
+    nphc_status s;
+    if ((s = check_ep(S, ep, true)) != NPHC_OK) return s;
+    if (!theta || !index || !energy) return fail(NPHC_EINVAL, "output arrays missing");
+    XYSys xs = S->xs;
+    NPHC_CK(launch_xy_classify(S->M, xs, view(ep), theta, index, energy, min_abs_eig,
+                               (cudaStream_t)stream));
+    return NPHC_OK;
+}
+
+nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
+    if (!S || !out) return fail(NPHC_EINVAL, "NULL argument");
+    *out = nullptr;
+    const int64_t P = S->npaths;
+    const int n = S->n, M = S->M;
+    const WsLayout L = ws_layout(P);
+    // sub-allocation plan
+    std::vector<size_t> sz = {
+        sizeof(int64_t) * P,            // 0 path
+        sizeof(double) * n * P,         // 1 z_re
+        sizeof(double) * n * P,         // 2 z_im
+        sizeof(double) * P,             // 3 t
+        sizeof(double) * P,             // 4 h
+        sizeof(int32_t) * P,            // 5 status
+        sizeof(int32_t) * P,            // 6 steps
+        sizeof(int32_t) * P,            // 7 solves
+        sizeof(int32_t) * P,            // 8 newton
+        sizeof(int32_t) * P,            // 9 cls
+        sizeof(double) * P,             // 10 alpha
+        sizeof(double) * P,             // 11 beta
+        sizeof(double) * P,             // 12 gamma
+        sizeof(double) * P,             // 13 resid
+        sizeof(double) * M * P,         // 14 theta
+        sizeof(double) * P,             // 15 energy
+        sizeof(double) * P,             // 16 mineig
+        sizeof(int32_t) * P,            // 17 index
+        sizeof(int32_t) * P,            // 18 flags
+        sizeof(int32_t) * P,            // 19 list0
+        sizeof(int32_t) * P,            // 20 list1
+        sizeof(int32_t) * P,            // 21 list2
+        sizeof(int32_t) * 8,            // 22 lcount
+        sizeof(int32_t) * P,            // 23 real_list
+        sizeof(int64_t) * NPHC_NCOUNTS, // 24 counts
+        sizeof(double) * M * P,         // 25 o_theta
+        sizeof(double) * P,             // 26 o_energy
+        sizeof(double) * P,             // 27 o_alpha
+        sizeof(int32_t) * P,            // 28 o_index
+        sizeof(int64_t) * P,            // 29 o_path
+        L.total};                       // 30 workspace
+    std::vector<size_t> off(sz.size());
+    size_t tot = 0;
+    for (size_t i = 0; i < sz.size(); i++) {
+        off[i] = tot;
+        tot += align256(sz[i]);
+    }
+    nphc_result *R = new (std::nothrow) nphc_result;
+    if (!R) return fail(NPHC_ENOMEM, "host allocation");
+    std::memset(R, 0, sizeof(*R));
+    cudaError_t e = cudaMalloc(&R->block, tot);
+    if (e != cudaSuccess) {
+        delete R;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? NPHC_ENOMEM : NPHC_ECUDA,
+                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    char *b = static_cast<char *>(R->block);
+    auto at = [&](int i) { return static_cast<void *>(b + off[i]); };
+    R->N = S->N;
+    R->M = M;
+    R->n = n;
+    R->P = P;
+    R->bytes = tot;
+    R->ep.count = P;
+    R->ep.path = (int64_t *)at(0);
+    R->ep.z_re = (double *)at(1);
+    R->ep.z_im = (double *)at(2);
+    R->ep.t = (double *)at(3);
+    R->ep.h = (double *)at(4);
+    R->ep.status = (int32_t *)at(5);
+    R->ep.steps = (int32_t *)at(6);
+    R->ep.solves = (int32_t *)at(7);
+    R->ep.newton = (int32_t *)at(8);
+    R->ep.cls = (int32_t *)at(9);
+    R->ep.alpha = (double *)at(10);
+    R->ep.beta = (double *)at(11);
+    R->ep.gamma = (double *)at(12);
+    R->ep.resid = (double *)at(13);
+    R->theta = (double *)at(14);
+    R->energy = (double *)at(15);
+    R->mineig = (double *)at(16);
+    R->index = (int32_t *)at(17);
+    R->flags = (int32_t *)at(18);
+    R->list[0] = (int32_t *)at(19);
+    R->list[1] = (int32_t *)at(20);
+    R->list[2] = (int32_t *)at(21);
+    R->lcount = (int32_t *)at(22);
+    R->real_list = (int32_t *)at(23);
+    R->counts = (int64_t *)at(24);
+    R->o_theta = (double *)at(25);
+    R->o_energy = (double *)at(26);
+    R->o_alpha = (double *)at(27);
+    R->o_index = (int32_t *)at(28);
+    R->o_path = (int64_t *)at(29);
+    R->ws = at(30);
+    R->ws_bytes = L.total;
+    R->stream = nullptr;
+    R->solved = false;
+    e = launch_iota(R->ep.path, P, nullptr);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e != cudaSuccess) {
+        cudaFree(R->block);
+        delete R;
+        return fail(NPHC_ECUDA, std::string("result init: ") + cudaGetErrorString(e));
+    }
+    *out = R;
+    return NPHC_OK;
+}
+
+nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_result *R,
+                            void *stream) {
+    if (!S || !R) return fail(NPHC_EINVAL, "NULL argument");
+    if (R->P != S->npaths || R->N != S->N) return fail(NPHC_EINVAL, "result does not match system");
+    nphc_status s;
+    if ((s = check_opt(o)) != NPHC_OK) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const nphc_endpoints *ep = &R->ep;
+    const EPView v = view(ep);
+    const XYSys xs = sys_with_gamma(S, o);
+    const WsLayout L = ws_layout(R->P);
+    const DedupScratch dsc = dedup_scratch(R->ws, L);
+    WorkList all;
+    all.list = nullptr;
+    all.list_count = nullptr;
+    all.queue = nullptr;
+    R->solved = false;
+    NPHC_CK(cudaMemsetAsync(R->flags, 0, sizeof(int32_t) * R->P, st));
+    NPHC_CK(cudaMemsetAsync(R->lcount, 0, sizeof(int32_t) * 8, st));
+    const bool mixed = o->precision == NPHC_PREC_MIXED;
+    if (mixed) {
+        // FP32 pass over every path
+        if ((s = track_impl(S, o, NPHC_PREC_MIXED, ep, nullptr, nullptr, false, false, R->ws, 0, st)))
+            return s;
+        // FP64 continuation of the paths the FP32 pass handed off
+        NPHC_CK(launch_compact(v, PRED_HANDOFF, R->flags, R->list[0], R->lcount + 0, st));
+        if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[0], R->lcount + 0, true, true, R->ws, 1, st)))
+            return s;
+        NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
+                                         R->P, all, st));
+        // FP64 re-track of FP32 endpoints that did not certify
+        NPHC_CK(launch_compact(v, PRED_UNCERTIFIED_FP32, R->flags, R->list[1], R->lcount + 1, st));
+        if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[1], R->lcount + 1, false, true, R->ws, 2, st)))
+            return s;
+        WorkList l1;
+        l1.list = R->list[1];
+        l1.list_count = R->lcount + 1;
+        l1.queue = nullptr;
+        NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
+                                         R->P, l1, st));
+        // deduplicate; every path of a solution reached more than once is re-tracked in
+        // FP64 and the endpoints are deduplicated again
+        NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, R->list[2], R->lcount + 2, st));
+        NPHC_CK(launch_flag_list(R->list[2], R->lcount + 2, R->P, R->flags, FLAG_RETRACKED_DUP, st));
+        if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[2], R->lcount + 2, false, true, R->ws, 3, st)))
+            return s;
+        WorkList l2;
+        l2.list = R->list[2];
+        l2.list_count = R->lcount + 2;
+        l2.queue = nullptr;
+        NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
+                                         R->P, l2, st));
+        NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st));
+    } else {
+        if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, nullptr, nullptr, false, false, R->ws, 0, st)))
+            return s;
+        NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
+                                         R->P, all, st));
+        NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st));
+    }
+    NPHC_CK(launch_xy_classify(S->M, xs, v, R->theta, R->index, R->energy, R->mineig, st));
+    NPHC_CK(launch_counts(v, R->flags, R->index, R->counts, st));
+    R->stream = st;
+    R->solved = true;
+    return NPHC_OK;
+}
+
+nphc_status nphc_solve(const nphc_system *S, const nphc_options *o, void *stream, nphc_result **out) {
+    if (!out) return fail(NPHC_EINVAL, "out is NULL");
+    nphc_result *R = nullptr;
+    nphc_status s = nphc_result_create(S, &R);
+    if (s != NPHC_OK) return s;
+    s = nphc_solve_into(S, o, R, stream);
+    if (s == NPHC_OK) {
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) s = fail(NPHC_ECUDA, std::string("solve: ") + cudaGetErrorString(e));
+    }
+    if (s != NPHC_OK) {
+        nphc_result_destroy(R);
+        return s;
+    }
+    *out = R;
+    return NPHC_OK;
+}
+
+nphc_status nphc_result_counts(const nphc_result *R, int64_t *counts) {
+    if (!R || !counts) return fail(NPHC_EINVAL, "NULL argument");
+    if (!R->solved) return fail(NPHC_ESTATE, "no solve on this result");
+    NPHC_CK(cudaStreamSynchronize(R->stream));
+    NPHC_CK(cudaMemcpy(counts, R->counts, sizeof(int64_t) * NPHC_NCOUNTS, cudaMemcpyDeviceToHost));
+    return NPHC_OK;
+}
+
+nphc_status nphc_result_copy_sps(const nphc_result *R, int64_t cap, double *theta, double *energy,
+                                 int32_t *index, double *alpha, int64_t *path, int64_t *n_out) {
+    if (!R || !n_out || cap < 0) return fail(NPHC_EINVAL, "invalid argument");
+    if (!R->solved) return fail(NPHC_ESTATE, "no solve on this result");
+    cudaStream_t st = R->stream;
+    NPHC_CK(launch_real_list(view(&R->ep), R->real_list, R->lcount + 4, st));
+    NPHC_CK(launch_gather_sps(view(&R->ep), R->M, R->real_list, R->lcount + 4, R->P, R->theta,
+                              R->index, R->energy, R->o_theta, R->o_index, R->o_energy, R->o_alpha,
+                              R->o_path, st));
+    int32_t cnt = 0;
+    NPHC_CK(cudaMemcpyAsync(&cnt, R->lcount + 4, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    NPHC_CK(cudaStreamSynchronize(st));
+    *n_out = cnt;
+    const int64_t k = std::min<int64_t>(cnt, cap);
+    if (k == 0) return NPHC_OK;
+    const int M = R->M;
+    std::vector<double> th(k * M), en(k), al(k);
+    std::vector<int32_t> ix(k);
+    std::vector<int64_t> pa(cnt);
+    NPHC_CK(cudaMemcpy(pa.data(), R->o_path, sizeof(int64_t) * cnt, cudaMemcpyDeviceToHost));
+    // the device list is unordered: order by path index, keep the first cap
+    std::vector<int64_t> ord(cnt);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return pa[a] < pa[b]; });
+    std::vector<double> th_all(cnt * M), en_all(cnt), al_all(cnt);
+    std::vector<int32_t> ix_all(cnt);
+    NPHC_CK(cudaMemcpy(th_all.data(), R->o_theta, sizeof(double) * cnt * M, cudaMemcpyDeviceToHost));
+    NPHC_CK(cudaMemcpy(en_all.data(), R->o_energy, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
+    NPHC_CK(cudaMemcpy(al_all.data(), R->o_alpha, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
+    NPHC_CK(cudaMemcpy(ix_all.data(), R->o_index, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < k; i++) {
+        const int64_t j = ord[i];
+        if (theta) std::memcpy(theta + i * M, th_all.data() + j * M, sizeof(double) * M);
+        if (energy) energy[i] = en_all[j];
+        if (index) index[i] = ix_all[j];
+        if (alpha) alpha[i] = al_all[j];
+        if (path) path[i] = pa[j];
+    }
+    return NPHC_OK;
+}
+
+nphc_status nphc_result_copy_endpoints(const nphc_result *R, int64_t cap, double *z_re,
+                                       double *z_im, int32_t *status, int32_t *cls,
+                                       int64_t *n_out) {
+    if (!R || !n_out || cap < 0) return fail(NPHC_EINVAL, "invalid argument");
+    if (!R->solved) return fail(NPHC_ESTATE, "no solve on this result");
+    NPHC_CK(cudaStreamSynchronize(R->stream));
+    *n_out = R->P;
+    const int64_t k = std::min<int64_t>(cap, R->P);
+    if (k == 0) return NPHC_OK;
+    const int n = R->n;
+    if (z_re || z_im) {
+        std::vector<double> buf(R->P);
+        for (int part = 0; part < 2; part++) {
+            double *dst = part ? z_im : z_re;
+            if (!dst) continue;
+            const double *src = part ? R->ep.z_im : R->ep.z_re;
+            for (int i = 0; i < n; i++) {
+                NPHC_CK(cudaMemcpy(buf.data(), src + (size_t)i * R->P, sizeof(double) * k,
+                                   cudaMemcpyDeviceToHost));
+                for (int64_t e = 0; e < k; e++) dst[e * n + i] = buf[e];
+            }
+        }
+    }
+    if (status) NPHC_CK(cudaMemcpy(status, R->ep.status, sizeof(int32_t) * k, cudaMemcpyDeviceToHost));
+    if (cls) NPHC_CK(cudaMemcpy(cls, R->ep.cls, sizeof(int32_t) * k, cudaMemcpyDeviceToHost));
+    return NPHC_OK;
+}
+
+nphc_status nphc_result_endpoints(const nphc_result *R, nphc_endpoints *ep) {
+    if (!R || !ep) return fail(NPHC_EINVAL, "NULL argument");
+    *ep = R->ep;
+    return NPHC_OK;
+}
+
+void nphc_result_destroy(nphc_result *R) {
+    if (!R) return;
+    if (R->block) {
+        if (R->stream) cudaStreamSynchronize(R->stream);
+        cudaFree(R->block);
+    }
+    delete R;
+}
+
+}  // extern "C"

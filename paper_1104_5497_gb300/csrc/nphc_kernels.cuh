@@ -1,0 +1,34 @@
+// nphc_kernels.cuh -- declarations of the size-independent kernels' launchers.
+#pragma once
+
+#include "nphc_internal.cuh"
+
+enum { PRED_HANDOFF = 1, PRED_UNCERTIFIED_FP32 = 2 };
+enum { FLAG_FP64_CONTINUED = 1, FLAG_RETRACKED = 2, FLAG_RETRACKED_DUP = 4 };
+
+// Device scratch of the deduplication (all arrays sized for the endpoint count, the
+// table a power of two >= 2 x count).
+struct DedupScratch {
+    int32_t *table;
+    int64_t table_size;
+    int32_t *rep;
+    long long *minpath;
+    int32_t *gsize;
+    int32_t *amb;
+    int32_t *inlist;
+};
+
+cudaError_t launch_compact(const EPView &ep, int pred, int32_t *flags, int32_t *list,
+                           int32_t *count, cudaStream_t st);
+cudaError_t launch_flag_list(const int32_t *list, const int32_t *count, int64_t cap,
+                             int32_t *flags, int32_t bit, cudaStream_t st);
+cudaError_t launch_dedup(const EPView &ep, int n, double delta, DedupScratch w, int32_t *list,
+                         int32_t *count, cudaStream_t st);
+cudaError_t launch_counts(const EPView &ep, const int32_t *flags, const int32_t *index,
+                          int64_t *counts, cudaStream_t st);
+cudaError_t launch_real_list(const EPView &ep, int32_t *list, int32_t *count, cudaStream_t st);
+cudaError_t launch_iota(int64_t *path, int64_t n, cudaStream_t st);
+cudaError_t launch_gather_sps(const EPView &ep, int M, const int32_t *list, const int32_t *count,
+                              int64_t cap, const double *theta, const int32_t *index,
+                              const double *energy, double *o_theta, int32_t *o_index,
+                              double *o_energy, double *o_alpha, int64_t *o_path, cudaStream_t st);

@@ -1,0 +1,36 @@
+// xy_dispatch.cu -- runtime ring size -> kernel instantiated for it.
+#include "xy_dispatch.cuh"
+
+cudaError_t launch_xy_track_f32(int M, const XYSys &sys, const XYCtl &ctl, const EPView &ep,
+                                const WorkList &wl, int block, int grid, cudaStream_t st) {
+    (void)block;
+#define C(MM) case MM: return launch_xy_track_f32_m##MM(sys, ctl, ep, wl, grid, st);
+    switch (M) { NPHC_FOR_EACH_M(C) default: return cudaErrorInvalidValue; }
+#undef C
+}
+
+cudaError_t launch_xy_track_f64(int M, const XYSys &sys, const XYCtl &ctl, const EPView &ep,
+                                const WorkList &wl, int block, int grid, cudaStream_t st) {
+    (void)block;
+#define C(MM) case MM: return launch_xy_track_f64_m##MM(sys, ctl, ep, wl, grid, st);
+    switch (M) { NPHC_FOR_EACH_M(C) default: return cudaErrorInvalidValue; }
+#undef C
+}
+
+cudaError_t launch_xy_refine_certify(int M, const XYSys &sys, double tol_sol, double refine_eps,
+                                     int refine_iters, const EPView &ep, int64_t cap,
+                                     const WorkList &wl, cudaStream_t st) {
+#define C(MM) case MM: return launch_xy_refine_certify_m##MM(sys, tol_sol, refine_eps, refine_iters, ep, cap, wl, st);
+    switch (M) { NPHC_FOR_EACH_M(C) default: return cudaErrorInvalidValue; }
+#undef C
+}
+
+cudaError_t launch_xy_classify(int M, const XYSys &sys, const EPView &ep, double *theta,
+                               int32_t *index, double *energy, double *min_eig, cudaStream_t st) {
+#define C(MM) case MM: return launch_xy_classify_m##MM(sys, ep, theta, index, energy, min_eig, st);
+    switch (M) { NPHC_FOR_EACH_M(C) default: return cudaErrorInvalidValue; }
+#undef C
+}
+
+int xy_track_f32_block(int M) { (void)M; return NPHC_F32_BLOCK; }
+int xy_track_f64_block(int M) { (void)M; return NPHC_F64_BLOCK; }

@@ -1,0 +1,358 @@
+// xy_endgame.cuh -- FP64 work at t = 1 on the endpoints of the XY ring:
+//   refinement: Newton's method on P to machine precision (section "Numerical Polynomial
+//     Homotopy Continuation Method": refinement "up to the machine precision");
+//   the solution tolerance Delta_sol on ||P(z)||_inf;
+//   alpha-theory certification (the alphaCertified step of the same section):
+//     beta = ||DP^-1 P||_2, gamma <= ||DP^-1||_F ||D^2 P / 2|| (P is quadratic, so
+//     D^k P = 0 for k >= 3 and Smale's gamma is ||DP^-1 D^2P/2|| exactly), certified when
+//     alpha = beta gamma < (13 - 3 sqrt 17) / 4; real when the test passes at Re z (a real
+//     point of a real system: Newton's iterates stay real), non-real when
+//     ||z - conj z|| > 2 (beta(z) + beta(conj z)), i.e. ||Im z|| > 2 beta;
+//   classification of real stationary points (introduction and section "A First
+//     Application"): theta_k = atan2(s_k, c_k) in (-pi, pi], the Hessian of
+//     V = sum_{i<j} J_ij (1 - cos(theta_i - theta_j)) in theta_1..theta_M, its number of
+//     negative eigenvalues (cyclic Jacobi), and V.
+//
+// The linear solves reuse the structure of xy_solve.cuh at t = 1 (a unitary frame per
+// constraint row, an M x M Schur system factored once by Householder QR) but keep the
+// factorisation in local memory so that it can be applied to many right-hand sides:
+// ||DP^-1||_F^2 = sum_i ||DP^-1 e_i||^2 needs 2M of them.
+#pragma once
+
+#include "nphc_internal.cuh"
+
+template <int M>
+struct Fac64 {
+    cx<double> A[M][M];   // R above the diagonal, Householder vectors below
+    cx<double> tauc[M];   // conj(tau) of each reflector
+    double dg[M];         // real diagonal of R
+    cx<double> ah[M], bh[M];
+    double iv[M];
+    cx<double> Ad[M], Bd[M];   // diagonal Jacobian entries of the gradient rows
+    cx<double> x[M], y[M];
+    bool ok;
+};
+
+// P(z) (t = 1): gradient rows f_k and constraint rows g_k.
+template <int M>
+__device__ void xy_eval_p(const double *__restrict__ J, const cx<double> (&x)[M],
+                          const cx<double> (&y)[M], cx<double> (&f)[M], cx<double> (&g)[M]) {
+#pragma unroll 1
+    for (int k = 0; k < M; k++) {
+        cx<double> u = cx<double>{J[k * NPHC_JSTRIDE + M], 0.0}, w = cx<double>{0.0, 0.0};
+        for (int l = 0; l < M; l++) {
+            if (l == k) continue;
+            const double Jl = J[k * NPHC_JSTRIDE + l];
+            u.re += Jl * x[l].re;
+            u.im += Jl * x[l].im;
+            w.re += Jl * y[l].re;
+            w.im += Jl * y[l].im;
+        }
+        f[k] = csub(cmul(y[k], u), cmul(x[k], w));
+        const cx<double> x2 = cmul(x[k], x[k]), y2 = cmul(y[k], y[k]);
+        g[k] = cx<double>{x2.re + y2.re - 1.0, x2.im + y2.im};
+    }
+}
+
+// Factor DP(z) (t = 1).
+template <int M>
+__device__ void fac_build(Fac64<M> &F, const double *__restrict__ J) {
+#pragma unroll 1
+    for (int j = 0; j < M; j++) {
+        cx<double> u = cx<double>{J[j * NPHC_JSTRIDE + M], 0.0}, w = cx<double>{0.0, 0.0};
+        for (int l = 0; l < M; l++) {
+            if (l == j) continue;
+            const double Jl = J[j * NPHC_JSTRIDE + l];
+            u.re += Jl * F.x[l].re;
+            u.im += Jl * F.x[l].im;
+            w.re += Jl * F.y[l].re;
+            w.im += Jl * F.y[l].im;
+        }
+        F.Ad[j] = cx<double>{-w.re, -w.im};   // d f_j / d c_j
+        F.Bd[j] = u;                          // d f_j / d s_j
+        const cx<double> a = cscale(2.0, F.x[j]), b = cscale(2.0, F.y[j]);
+        const double iv = rsqrt(cabs2(a) + cabs2(b));
+        F.iv[j] = iv;
+        F.ah[j] = cscale(iv, a);
+        F.bh[j] = cscale(iv, b);
+    }
+#pragma unroll 1
+    for (int j = 0; j < M; j++)
+        for (int k = 0; k < M; k++) {
+            if (k == j)
+                F.A[k][j] = csub(cmul(F.Ad[j], F.bh[j]), cmul(F.Bd[j], F.ah[j]));
+            else
+                F.A[k][j] = cscale(J[k * NPHC_JSTRIDE + j],
+                                   cadd(cmul(F.y[k], F.bh[j]), cmul(F.x[k], F.ah[j])));
+        }
+    F.ok = true;
+#pragma unroll 1
+    for (int k = 0; k < M; k++) {
+        const cx<double> al = F.A[k][k];
+        double xn2 = 0.0;
+        for (int i = k + 1; i < M; i++) xn2 += cabs2(F.A[i][k]);
+        const double an = sqrt(cabs2(al) + xn2);
+        F.ok = F.ok && an > 0.0;
+        const double beta = al.re >= 0.0 ? -an : an;
+        F.tauc[k] = cx<double>{(beta - al.re) / beta, al.im / beta};
+        const cx<double> sc = crecip(cx<double>{al.re - beta, al.im});
+        for (int i = k + 1; i < M; i++) F.A[i][k] = cmul(F.A[i][k], sc);
+        F.dg[k] = beta;
+        for (int c = k + 1; c < M; c++) {
+            cx<double> wv = F.A[k][c];
+            for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(F.A[i][k], F.A[i][c]));
+            wv = cmul(F.tauc[k], wv);
+            F.A[k][c] = csub(F.A[k][c], wv);
+            for (int i = k + 1; i < M; i++) F.A[i][c] = csub(F.A[i][c], cmul(F.A[i][k], wv));
+        }
+    }
+}
+
+// d = DP^-1 r for r = (rf, rg); returns ||d||_2^2.
+template <int M>
+__device__ double fac_apply(const Fac64<M> &F, const double *__restrict__ J,
+                            const cx<double> (&rf)[M], const cx<double> (&rg)[M],
+                            cx<double> (&dx)[M], cx<double> (&dy)[M]) {
+    cx<double> q[M], b[M];
+#pragma unroll 1
+    for (int j = 0; j < M; j++) q[j] = cscale(F.iv[j], rg[j]);
+#pragma unroll 1
+    for (int k = 0; k < M; k++) {
+        cx<double> acc = rf[k];
+        for (int j = 0; j < M; j++) {
+            const cx<double> px = cmulc(F.ah[j], q[j]), py = cmulc(F.bh[j], q[j]);
+            if (k == j)
+                acc = csub(acc, cadd(cmul(F.Ad[j], px), cmul(F.Bd[j], py)));
+            else
+                acc = csub(acc, cscale(J[k * NPHC_JSTRIDE + j],
+                                       csub(cmul(F.y[k], px), cmul(F.x[k], py))));
+        }
+        b[k] = acc;
+    }
+#pragma unroll 1
+    for (int k = 0; k < M; k++) {
+        cx<double> wv = b[k];
+        for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(F.A[i][k], b[i]));
+        wv = cmul(F.tauc[k], wv);
+        b[k] = csub(b[k], wv);
+        for (int i = k + 1; i < M; i++) b[i] = csub(b[i], cmul(F.A[i][k], wv));
+    }
+#pragma unroll 1
+    for (int k = M - 1; k >= 0; k--) {
+        cx<double> acc = b[k];
+        for (int c = k + 1; c < M; c++) acc = csub(acc, cmul(F.A[k][c], b[c]));
+        b[k] = cscale(1.0 / F.dg[k], acc);
+    }
+    double n2 = 0.0;
+#pragma unroll 1
+    for (int j = 0; j < M; j++) {
+        dx[j] = cadd(cmulc(F.ah[j], q[j]), cmul(F.bh[j], b[j]));
+        dy[j] = csub(cmulc(F.bh[j], q[j]), cmul(F.ah[j], b[j]));
+        n2 += cabs2(dx[j]) + cabs2(dy[j]);
+    }
+    return n2;
+}
+
+// beta = ||DP^-1 P||, ||DP^-1||_F and ||P||_inf at (x, y).  Returns false if singular.
+template <int M>
+__device__ bool xy_beta_invnorm(Fac64<M> &F, const double *__restrict__ J, double &beta,
+                                double &invF, double &res) {
+    cx<double> f[M], g[M], dx[M], dy[M];
+    xy_eval_p<M>(J, F.x, F.y, f, g);
+    res = 0.0;
+    for (int k = 0; k < M; k++) {
+        res = fmax(res, sqrt(cabs2(f[k])));
+        res = fmax(res, sqrt(cabs2(g[k])));
+        f[k] = cx<double>{-f[k].re, -f[k].im};
+        g[k] = cx<double>{-g[k].re, -g[k].im};
+    }
+    fac_build<M>(F, J);
+    if (!F.ok) return false;
+    beta = sqrt(fac_apply<M>(F, J, f, g, dx, dy));
+    double s = 0.0;
+#pragma unroll 1
+    for (int i = 0; i < 2 * M; i++) {
+        for (int k = 0; k < M; k++) {
+            f[k] = cx<double>{i == k ? 1.0 : 0.0, 0.0};
+            g[k] = cx<double>{i == M + k ? 1.0 : 0.0, 0.0};
+        }
+        s += fac_apply<M>(F, J, f, g, dx, dy);
+    }
+    invF = sqrt(s);
+    return isfinite(beta) && isfinite(invF);
+}
+
+template <int M>
+__global__ void __launch_bounds__(128)
+    xy_refine_certify_kernel(const __grid_constant__ XYSys S, double tol_sol, double refine_eps,
+                             int refine_iters, const EPView ep, const WorkList wl) {
+    const int64_t total = worklist_size(wl, ep.count);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int64_t e = worklist_entry(wl, i);
+    const int64_t cnt = ep.count;
+    const int st = ep.status[e];
+    ep.alpha[e] = INFINITY;
+    ep.beta[e] = INFINITY;
+    ep.gamma[e] = INFINITY;
+    ep.resid[e] = INFINITY;
+    if (st == NPHC_PATH_DIVERGED) {
+        ep.cls[e] = NPHC_END_NONE;
+        return;
+    }
+    if (st != NPHC_PATH_REACHED) {
+        ep.cls[e] = NPHC_END_FAILED;
+        return;
+    }
+    const double *J = S.Jd;
+    const double alpha0 = (13.0 - 3.0 * sqrt(17.0)) / 4.0;
+    Fac64<M> F;
+    for (int k = 0; k < M; k++) {
+        F.x[k] = cx<double>{ep.z_re[k * cnt + e], ep.z_im[k * cnt + e]};
+        F.y[k] = cx<double>{ep.z_re[(M + k) * cnt + e], ep.z_im[(M + k) * cnt + e]};
+    }
+    int cls = NPHC_END_SINGULAR;
+    bool finite = true;
+    // Newton refinement on P
+    for (int it = 0; it < refine_iters; it++) {
+        cx<double> f[M], g[M], dx[M], dy[M];
+        xy_eval_p<M>(J, F.x, F.y, f, g);
+        for (int k = 0; k < M; k++) {
+            f[k] = cx<double>{-f[k].re, -f[k].im};
+            g[k] = cx<double>{-g[k].re, -g[k].im};
+        }
+        fac_build<M>(F, J);
+        if (!F.ok) break;
+        const double dn = sqrt(fac_apply<M>(F, J, f, g, dx, dy));
+        double zn = 0.0;
+        for (int k = 0; k < M; k++) {
+            F.x[k] = cadd(F.x[k], dx[k]);
+            F.y[k] = cadd(F.y[k], dy[k]);
+            zn += cabs2(F.x[k]) + cabs2(F.y[k]);
+        }
+        if (!isfinite(dn) || !isfinite(zn)) {
+            finite = false;
+            break;
+        }
+        if (dn <= refine_eps * (1.0 + sqrt(zn))) break;
+    }
+    double beta = INFINITY, invF = INFINITY, res = INFINITY;
+    if (finite && xy_beta_invnorm<M>(F, J, beta, invF, res)) {
+        const double gam = invF * S.d2norm, alpha = beta * gam;
+        ep.alpha[e] = alpha;
+        ep.beta[e] = beta;
+        ep.gamma[e] = gam;
+        ep.resid[e] = res;
+        if (res <= tol_sol && alpha < alpha0) {
+            double im2 = 0.0;
+            for (int k = 0; k < M; k++) im2 += F.x[k].im * F.x[k].im + F.y[k].im * F.y[k].im;
+            if (sqrt(im2) > 2.0 * beta) {
+                cls = NPHC_END_NONREAL;
+            } else {
+                // real test at Re z
+                Fac64<M> G;
+                for (int k = 0; k < M; k++) {
+                    G.x[k] = cx<double>{F.x[k].re, 0.0};
+                    G.y[k] = cx<double>{F.y[k].re, 0.0};
+                }
+                double br, ir, rr;
+                if (xy_beta_invnorm<M>(G, J, br, ir, rr) && br * ir * S.d2norm < alpha0)
+                    cls = NPHC_END_REAL;
+                else
+                    cls = NPHC_END_UNDECIDED;
+            }
+        }
+    } else if (finite) {
+        ep.resid[e] = res;
+    }
+    for (int k = 0; k < M; k++) {
+        ep.z_re[k * cnt + e] = F.x[k].re;
+        ep.z_im[k * cnt + e] = F.x[k].im;
+        ep.z_re[(M + k) * cnt + e] = F.y[k].re;
+        ep.z_im[(M + k) * cnt + e] = F.y[k].im;
+    }
+    ep.cls[e] = cls;
+}
+
+template <int M>
+__global__ void __launch_bounds__(128)
+    xy_classify_kernel(const __grid_constant__ XYSys S, const EPView ep, double *theta,
+                       int32_t *index, double *energy, double *min_eig) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t cnt = ep.count;
+    if (e >= cnt) return;
+    if (ep.cls[e] != NPHC_END_REAL) {
+        index[e] = -1;
+        energy[e] = 0.0;
+        if (min_eig) min_eig[e] = 0.0;
+        for (int k = 0; k < M; k++) theta[k * cnt + e] = 0.0;
+        return;
+    }
+    const double *J = S.Jd;
+    constexpr int N = M + 1;
+    double th[N], c[N], s[N];
+    for (int k = 0; k < M; k++) {
+        const double x = ep.z_re[k * cnt + e], y = ep.z_re[(M + k) * cnt + e];
+        double a = atan2(y, x);
+        if (a <= -M_PI) a = M_PI;
+        th[k] = a;
+        sincos(a, &s[k], &c[k]);
+        theta[k * cnt + e] = a;
+    }
+    th[M] = 0.0;
+    c[M] = 1.0;
+    s[M] = 0.0;
+    // energy: cos(theta_i - theta_j) = c_i c_j + s_i s_j
+    double V = 0.0;
+    for (int i = 0; i < N; i++)
+        for (int j = i + 1; j < N; j++) V += J[i * NPHC_JSTRIDE + j] * (1.0 - (c[i] * c[j] + s[i] * s[j]));
+    double H[M][M];
+    for (int k = 0; k < M; k++)
+        for (int l = 0; l < M; l++) {
+            if (k == l) {
+                double d = 0.0;
+                for (int j = 0; j < N; j++)
+                    if (j != k) d += J[k * NPHC_JSTRIDE + j] * (c[k] * c[j] + s[k] * s[j]);
+                H[k][k] = d;
+            } else {
+                H[k][l] = -J[k * NPHC_JSTRIDE + l] * (c[k] * c[l] + s[k] * s[l]);
+            }
+        }
+    // cyclic Jacobi rotations until the off-diagonal part is negligible
+    for (int sweep = 0; sweep < 64; sweep++) {
+        double off = 0.0, tot = 0.0;
+        for (int p = 0; p < M; p++)
+            for (int q = 0; q < M; q++) {
+                tot += H[p][q] * H[p][q];
+                if (p != q) off += H[p][q] * H[p][q];
+            }
+        if (off <= 1e-30 * tot) break;
+        for (int p = 0; p < M - 1; p++)
+            for (int q = p + 1; q < M; q++) {
+                const double apq = H[p][q];
+                if (apq == 0.0) continue;
+                const double tq = (H[q][q] - H[p][p]) / (2.0 * apq);
+                const double tn = (tq >= 0.0 ? 1.0 : -1.0) / (fabs(tq) + sqrt(tq * tq + 1.0));
+                const double cs = rsqrt(tn * tn + 1.0), sn = tn * cs;
+                for (int k = 0; k < M; k++) {
+                    const double akp = H[k][p], akq = H[k][q];
+                    H[k][p] = cs * akp - sn * akq;
+                    H[k][q] = sn * akp + cs * akq;
+                }
+                for (int k = 0; k < M; k++) {
+                    const double apk = H[p][k], aqk = H[q][k];
+                    H[p][k] = cs * apk - sn * aqk;
+                    H[q][k] = sn * apk + cs * aqk;
+                }
+            }
+    }
+    int neg = 0;
+    double mn = INFINITY;
+    for (int k = 0; k < M; k++) {
+        if (H[k][k] < 0.0) neg++;
+        mn = fmin(mn, fabs(H[k][k]));
+    }
+    index[e] = neg;
+    energy[e] = V;
+    if (min_eig) min_eig[e] = mn;
+}

@@ -1,0 +1,68 @@
+// xy_inst.cu -- one ring size of one kernel family per compilation, so that the build
+// compiles the heavily unrolled kernels in parallel.  Compiled with
+//   -DNPHC_INST_M=<M>  (free sites, N = M + 1)
+//   -DNPHC_INST_KIND=0 (FP32 tracker), 1 (FP64 tracker) or 2 (FP64 endgame)
+#include "xy_dispatch.cuh"
+
+#if NPHC_INST_KIND == 0 || NPHC_INST_KIND == 1
+#include "xy_track.cuh"
+
+#if NPHC_INST_KIND == 0
+using RT = float;
+constexpr bool FFV = true;
+constexpr int BLK = NPHC_F32_BLOCK;
+#define NPHC_FN NPHC_CAT(launch_xy_track_f32_m, NPHC_INST_M)
+#else
+using RT = double;
+constexpr bool FFV = false;
+constexpr int BLK = NPHC_F64_BLOCK;
+#define NPHC_FN NPHC_CAT(launch_xy_track_f64_m, NPHC_INST_M)
+#endif
+
+cudaError_t NPHC_FN(const XYSys &sys, const XYCtl &ctl, const EPView &ep, const WorkList &wl,
+                    int grid, cudaStream_t st) {
+    constexpr int M = NPHC_INST_M;
+    const size_t smem = xy_track_smem_bytes(M, sizeof(RT), BLK);
+    auto k = xy_track_kernel<M, RT, FFV, BLK>;
+    static bool attr_set = false;   // once per process for this instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    if (grid <= 0) {   // persistent grid: every SM filled to its occupancy
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BLK, smem);
+        if (e != cudaSuccess) return e;
+        grid = sms * (per > 0 ? per : 1);
+    }
+    k<<<grid, BLK, smem, st>>>(sys, ctl, ep, wl);
+    return cudaGetLastError();
+}
+
+#else
+#include "xy_endgame.cuh"
+
+cudaError_t NPHC_CAT(launch_xy_refine_certify_m, NPHC_INST_M)(const XYSys &sys, double tol_sol,
+                                                             double refine_eps, int refine_iters,
+                                                             const EPView &ep, int64_t cap,
+                                                             const WorkList &wl, cudaStream_t st) {
+    if (cap <= 0) return cudaSuccess;
+    const int grid = (int)((cap + 127) / 128);
+    xy_refine_certify_kernel<NPHC_INST_M><<<grid, 128, 0, st>>>(sys, tol_sol, refine_eps,
+                                                               refine_iters, ep, wl);
+    return cudaGetLastError();
+}
+
+cudaError_t NPHC_CAT(launch_xy_classify_m, NPHC_INST_M)(const XYSys &sys, const EPView &ep,
+                                                       double *theta, int32_t *index,
+                                                       double *energy, double *min_eig,
+                                                       cudaStream_t st) {
+    if (ep.count <= 0) return cudaSuccess;
+    const int grid = (int)((ep.count + 127) / 128);
+    xy_classify_kernel<NPHC_INST_M><<<grid, 128, 0, st>>>(sys, ep, theta, index, energy, min_eig);
+    return cudaGetLastError();
+}
+#endif

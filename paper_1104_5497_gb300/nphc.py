@@ -1,0 +1,322 @@
+"""Python binding of libnphc (include/nphc.h): the same calls, argument marshalling only.
+
+Every step of the method runs in the CUDA library; PyTorch only provides device memory
+and streams.  There is no CPU fallback: loading fails loudly when the library is
+missing, and the compute calls raise when no CUDA device is present.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libnphc.so")
+
+NPHC_MIN_N, NPHC_MAX_N = 3, 13
+PREC_FP64, PREC_MIXED = 0, 1
+
+PATH_RUNNING, PATH_REACHED, PATH_DIVERGED, PATH_MIN_STEP, PATH_STEP_BUDGET, PATH_NONFINITE, \
+    PATH_HANDOFF = range(7)
+END_NONE, END_SINGULAR, END_REAL, END_NONREAL, END_UNDECIDED, END_DUPLICATE, END_FAILED = range(7)
+
+COUNT_NAMES = ["paths", "reached", "diverged", "failed", "real", "nonreal", "undecided",
+               "singular", "duplicate", "handoff", "retracked", "solves"]
+NCOUNTS = len(COUNT_NAMES) + NPHC_MAX_N - 1
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBUDGET", 5: "ESTATE"}
+
+
+class NphcError(RuntimeError):
+    def __init__(self, call: str, status: int, msg: str):
+        super().__init__(f"{call}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class nphc_options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int),
+                ("gamma_re", ctypes.c_double), ("gamma_im", ctypes.c_double),
+                ("tol_sol", ctypes.c_double), ("tol_real", ctypes.c_double),
+                ("h0", ctypes.c_double), ("h_max", ctypes.c_double), ("h_min", ctypes.c_double),
+                ("eps_fp32", ctypes.c_double), ("eps_fp64", ctypes.c_double),
+                ("trust", ctypes.c_double), ("r_div", ctypes.c_double),
+                ("r_div_fp32", ctypes.c_double), ("rho_div", ctypes.c_double),
+                ("max_newton_fp32", ctypes.c_int), ("max_newton_fp64", ctypes.c_int),
+                ("max_steps", ctypes.c_int), ("grow_after", ctypes.c_int),
+                ("refine_iters", ctypes.c_int), ("refine_eps", ctypes.c_double),
+                ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
+
+
+_P = ctypes.c_void_p
+
+
+class nphc_endpoints(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int64), ("path", _P), ("z_re", _P), ("z_im", _P),
+                ("t", _P), ("h", _P), ("status", _P), ("steps", _P), ("solves", _P),
+                ("newton", _P), ("cls", _P), ("alpha", _P), ("beta", _P), ("gamma", _P),
+                ("resid", _P)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libnphc.so (built by paper_1104_5497_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libnphc.so not built ({LIB_PATH}); run "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    L = ctypes.CDLL(LIB_PATH)
+    i32, i64, d, vp = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+    pd, pi64 = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int64)
+    pi32 = ctypes.POINTER(ctypes.c_int32)
+    sig = {
+        "nphc_options_default": [ctypes.POINTER(nphc_options)],
+        "nphc_xy_couplings": [i32, d, pd, d, pd],
+        "nphc_system_create_xy": [i32, d, pd, ctypes.POINTER(vp)],
+        "nphc_system_info": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), pi64],
+        "nphc_system_couplings": [vp, pd],
+        "nphc_workspace_size": [vp, i64, ctypes.POINTER(ctypes.c_size_t)],
+        "nphc_track": [vp, ctypes.POINTER(nphc_options), i32, ctypes.POINTER(nphc_endpoints),
+                       vp, vp, i32, vp, ctypes.c_size_t, vp],
+        "nphc_refine_certify": [vp, ctypes.POINTER(nphc_options), ctypes.POINTER(nphc_endpoints),
+                                vp, vp, vp],
+        "nphc_dedup": [vp, ctypes.POINTER(nphc_options), ctypes.POINTER(nphc_endpoints), vp, vp,
+                       vp, ctypes.c_size_t, vp],
+        "nphc_classify": [vp, ctypes.POINTER(nphc_endpoints), vp, vp, vp, vp, vp],
+        "nphc_result_create": [vp, ctypes.POINTER(vp)],
+        "nphc_solve_into": [vp, ctypes.POINTER(nphc_options), vp, vp],
+        "nphc_solve": [vp, ctypes.POINTER(nphc_options), vp, ctypes.POINTER(vp)],
+        "nphc_result_counts": [vp, pi64],
+        "nphc_result_copy_sps": [vp, i64, pd, pd, pi32, pd, pi64, pi64],
+        "nphc_result_copy_endpoints": [vp, i64, pd, pd, pi32, pi32, pi64],
+        "nphc_result_endpoints": [vp, ctypes.POINTER(nphc_endpoints)],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    L.nphc_system_destroy.argtypes = [vp]
+    L.nphc_system_destroy.restype = None
+    L.nphc_result_destroy.argtypes = [vp]
+    L.nphc_result_destroy.restype = None
+    L.nphc_last_error.argtypes = []
+    L.nphc_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(call: str, status: int):
+    if status != 0:
+        raise NphcError(call, status, lib().nphc_last_error().decode())
+
+
+def _pd(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _pi64(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _pi32(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+def options_default(**kw) -> nphc_options:
+    o = nphc_options()
+    _check("nphc_options_default", lib().nphc_options_default(ctypes.byref(o)))
+    for k, v in kw.items():
+        if k == "gamma":
+            o.gamma_re, o.gamma_im = float(np.real(v)), float(np.imag(v))
+        else:
+            setattr(o, k, v)
+    return o
+
+
+def xy_couplings(N: int, sigma: float, g: np.ndarray | None = None, eps: float = 0.1) -> np.ndarray:
+    J = np.zeros((N, N))
+    gg = None if g is None else np.ascontiguousarray(g, dtype=np.float64)
+    _check("nphc_xy_couplings", lib().nphc_xy_couplings(int(N), float(sigma),
+                                                       None if gg is None else _pd(gg),
+                                                       float(eps), _pd(J)))
+    return J
+
+
+class System:
+    """nphc_system: the polynomial system of one XY ring (host-side handle)."""
+
+    def __init__(self, N: int, sigma: float = 1.0, J: np.ndarray | None = None):
+        h = ctypes.c_void_p()
+        Jc = None if J is None else np.ascontiguousarray(J, dtype=np.float64)
+        _check("nphc_system_create_xy",
+               lib().nphc_system_create_xy(int(N), float(sigma), None if Jc is None else _pd(Jc),
+                                           ctypes.byref(h)))
+        self.handle = h
+        n = ctypes.c_int()
+        NN = ctypes.c_int()
+        P = ctypes.c_int64()
+        _check("nphc_system_info", lib().nphc_system_info(h, ctypes.byref(NN), ctypes.byref(n),
+                                                        ctypes.byref(P)))
+        self.N, self.n, self.npaths = NN.value, n.value, P.value
+        self.M = self.N - 1
+
+    def couplings(self) -> np.ndarray:
+        J = np.zeros((self.N, self.N))
+        _check("nphc_system_couplings", lib().nphc_system_couplings(self.handle, _pd(J)))
+        return J
+
+    def workspace_size(self, count: int) -> int:
+        b = ctypes.c_size_t()
+        _check("nphc_workspace_size", lib().nphc_workspace_size(self.handle, int(count), ctypes.byref(b)))
+        return b.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.nphc_system_destroy(self.handle)
+            self.handle = None
+
+
+class Result:
+    """nphc_result: device buffers for every path of a system."""
+
+    def __init__(self, system: System):
+        h = ctypes.c_void_p()
+        _check("nphc_result_create", lib().nphc_result_create(system.handle, ctypes.byref(h)))
+        self.handle = h
+        self.system = system
+
+    def counts(self) -> dict:
+        c = np.zeros(NCOUNTS, np.int64)
+        _check("nphc_result_counts", lib().nphc_result_counts(self.handle, _pi64(c)))
+        out = {k: int(c[i]) for i, k in enumerate(COUNT_NAMES)}
+        out["index_hist"] = [int(v) for v in c[len(COUNT_NAMES):len(COUNT_NAMES) + self.system.M]]
+        return out
+
+    def stationary_points(self) -> dict:
+        M = self.system.M
+        n = ctypes.c_int64()
+        _check("nphc_result_copy_sps", lib().nphc_result_copy_sps(self.handle, 0, None, None, None,
+                                                                  None, None, ctypes.byref(n)))
+        k = n.value
+        th, en, al = np.zeros((k, M)), np.zeros(k), np.zeros(k)
+        ix, pa = np.zeros(k, np.int32), np.zeros(k, np.int64)
+        _check("nphc_result_copy_sps", lib().nphc_result_copy_sps(self.handle, k, _pd(th), _pd(en),
+                                                                  _pi32(ix), _pd(al), _pi64(pa),
+                                                                  ctypes.byref(n)))
+        return dict(theta=th, energy=en, index=ix, alpha=al, path=pa)
+
+    def endpoints(self) -> dict:
+        s = self.system
+        n = ctypes.c_int64()
+        P = s.npaths
+        zr, zi = np.zeros((P, s.n)), np.zeros((P, s.n))
+        st, cl = np.zeros(P, np.int32), np.zeros(P, np.int32)
+        _check("nphc_result_copy_endpoints", lib().nphc_result_copy_endpoints(
+            self.handle, P, _pd(zr), _pd(zi), _pi32(st), _pi32(cl), ctypes.byref(n)))
+        return dict(z=zr + 1j * zi, status=st, cls=cl)
+
+    def device_endpoints(self) -> nphc_endpoints:
+        ep = nphc_endpoints()
+        _check("nphc_result_endpoints", lib().nphc_result_endpoints(self.handle, ctypes.byref(ep)))
+        return ep
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.nphc_result_destroy(self.handle)
+            self.handle = None
+
+
+def solve_into(system: System, opts: nphc_options, result: Result, stream=None) -> None:
+    """Asynchronous whole-method solve into an existing result (no allocation)."""
+    _check("nphc_solve_into", lib().nphc_solve_into(system.handle, ctypes.byref(opts),
+                                                   result.handle, _stream_ptr(stream)))
+
+
+def solve(system: System, opts: nphc_options, stream=None) -> Result:
+    """nphc_solve: allocate, solve, synchronise."""
+    h = ctypes.c_void_p()
+    _check("nphc_solve", lib().nphc_solve(system.handle, ctypes.byref(opts), _stream_ptr(stream),
+                                         ctypes.byref(h)))
+    r = Result.__new__(Result)
+    r.handle = h
+    r.system = system
+    return r
+
+
+# ------------------------------------------------------------ step-by-step --
+@dataclass
+class DeviceEndpoints:
+    """Caller-owned device endpoint arrays (torch tensors) for the step-by-step calls."""
+    count: int
+    n: int
+    tensors: dict
+
+    @classmethod
+    def empty(cls, n: int, paths, device="cuda"):
+        import torch
+        paths = torch.as_tensor(paths, dtype=torch.int64, device=device).contiguous()
+        c = int(paths.numel())
+        f64 = dict(dtype=torch.float64, device=device)
+        i32 = dict(dtype=torch.int32, device=device)
+        t = dict(path=paths, z_re=torch.zeros(n, c, **f64), z_im=torch.zeros(n, c, **f64),
+                 t=torch.zeros(c, **f64), h=torch.zeros(c, **f64), status=torch.zeros(c, **i32),
+                 steps=torch.zeros(c, **i32), solves=torch.zeros(c, **i32),
+                 newton=torch.zeros(c, **i32), cls=torch.zeros(c, **i32),
+                 alpha=torch.zeros(c, **f64), beta=torch.zeros(c, **f64),
+                 gamma=torch.zeros(c, **f64), resid=torch.zeros(c, **f64))
+        return cls(c, n, t)
+
+    def struct(self) -> nphc_endpoints:
+        ep = nphc_endpoints()
+        ep.count = self.count
+        for k, v in self.tensors.items():
+            setattr(ep, k, v.data_ptr())
+        return ep
+
+
+def track(system: System, opts: nphc_options, prec: int, ep: DeviceEndpoints, workspace,
+          list_=None, list_count=None, resume: bool = False, stream=None) -> None:
+    s = ep.struct()
+    _check("nphc_track", lib().nphc_track(
+        system.handle, ctypes.byref(opts), int(prec), ctypes.byref(s),
+        None if list_ is None else list_.data_ptr(),
+        None if list_count is None else list_count.data_ptr(), int(resume),
+        workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream_ptr(stream)))
+
+
+def refine_certify(system: System, opts: nphc_options, ep: DeviceEndpoints, list_=None,
+                   list_count=None, stream=None) -> None:
+    s = ep.struct()
+    _check("nphc_refine_certify", lib().nphc_refine_certify(
+        system.handle, ctypes.byref(opts), ctypes.byref(s),
+        None if list_ is None else list_.data_ptr(),
+        None if list_count is None else list_count.data_ptr(), _stream_ptr(stream)))
+
+
+def dedup(system: System, opts: nphc_options, ep: DeviceEndpoints, workspace, dup_list=None,
+          dup_count=None, stream=None) -> None:
+    s = ep.struct()
+    _check("nphc_dedup", lib().nphc_dedup(
+        system.handle, ctypes.byref(opts), ctypes.byref(s),
+        None if dup_list is None else dup_list.data_ptr(),
+        None if dup_count is None else dup_count.data_ptr(),
+        workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream_ptr(stream)))
+
+
+def classify(system: System, ep: DeviceEndpoints, theta, index, energy, min_abs_eig=None,
+             stream=None) -> None:
+    s = ep.struct()
+    _check("nphc_classify", lib().nphc_classify(
+        system.handle, ctypes.byref(s), theta.data_ptr(), index.data_ptr(), energy.data_ptr(),
+        None if min_abs_eig is None else min_abs_eig.data_ptr(), _stream_ptr(stream)))

@@ -1,0 +1,70 @@
+"""Helpers for the GPU parity tests: build/load the CUDA library once per session and
+compare its results with the oracle's."""
+from functools import lru_cache
+
+import numpy as np
+import pytest
+
+import oracle as O
+
+
+@lru_cache(maxsize=None)
+def nphc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1104_5497_gb300 import build
+    build.build()
+    import paper_1104_5497_gb300.nphc as N
+    N.lib()
+    return N
+
+
+@lru_cache(maxsize=None)
+def oracle_xy(N, sigma, gamma_re, gamma_im):
+    return O.solve_xy(N, sigma, complex(gamma_re, gamma_im))
+
+
+def torus_dist(a, b):
+    return np.abs(np.angle(np.exp(1j * (a - b)))).max(axis=-1)
+
+
+def certified_set(z, cls, classes):
+    return z[np.isin(cls, classes)]
+
+
+def assert_same_point_sets(za, zb, rel=1e-10):
+    """Every point of za has a partner in zb within rel (1 + |z|) and vice versa."""
+    assert len(za) == len(zb), (len(za), len(zb))
+    if len(za) == 0:
+        return
+    for A, Bs in ((za, zb), (zb, za)):
+        for z in A:
+            d = np.linalg.norm(Bs - z, axis=1)
+            assert d.min() <= rel * (1 + np.linalg.norm(z)), d.min()
+
+
+def compare_with_oracle(N, sigma, gamma, prec, ref=None):
+    """Solve on the GPU and check: certified real and non-real sets equal the oracle's
+    (within 1e-10 relative), the real SPs carry the same theta, index and energy."""
+    N_ = nphc()
+    system = N_.System(N, sigma)
+    res = N_.solve(system, N_.options_default(gamma=gamma, precision=prec))
+    ep = res.endpoints()
+    sps = res.stationary_points()
+    counts = res.counts()
+    if ref is None:
+        ref = oracle_xy(N, float(sigma), float(np.real(gamma)), float(np.imag(gamma)))
+    for cl_gpu, cl_or in ((N_.END_REAL, O.C_REAL), (N_.END_NONREAL, O.C_NONREAL)):
+        assert_same_point_sets(certified_set(ep["z"], ep["cls"], [cl_gpu]),
+                               certified_set(ref["z"], ref["cls"], [cl_or]))
+    ref_th = np.array([s["theta"] for s in ref["sps"]]).reshape(len(ref["sps"]), N - 1)
+    assert len(sps["theta"]) == len(ref_th)
+    for th, ix, en in zip(sps["theta"], sps["index"], sps["energy"]):
+        d = torus_dist(ref_th, th)
+        k = int(d.argmin())
+        assert d[k] < 1e-9
+        assert ref["sps"][k]["index"] == ix
+        assert abs(ref["sps"][k]["energy"] - en) < 1e-10
+    assert counts["duplicate"] == 0 or prec == N_.PREC_FP64
+    return res, counts, ref

@@ -1,0 +1,80 @@
+"""The C ABI without a GPU: the library builds, loads and exports every function that
+include/nphc.h declares; host-side argument checks and the couplings builder."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import brute_force as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def N_():
+    from paper_1104_5497_gb300 import build
+    build.build()
+    import paper_1104_5497_gb300.nphc as nphc
+    return nphc
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "nphc.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(nphc_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(N_):
+    names = declared_functions()
+    assert len(names) >= 20
+    L = N_.lib()
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_options_defaults(N_):
+    o = N_.options_default()
+    assert o.precision == N_.PREC_MIXED
+    assert o.tol_sol == 1e-10 and o.tol_real == 1e-7
+    assert abs(o.gamma_re ** 2 + o.gamma_im ** 2 - 1) < 1e-15
+
+
+@pytest.mark.parametrize("N,sigma", [(3, 0.75), (8, 1.5), (13, 1.0)])
+def test_couplings_builder(N_, N, sigma):
+    assert np.array_equal(N_.xy_couplings(N, sigma), B.ring_couplings(N, sigma))
+
+
+def test_disordered_couplings_builder(N_):
+    rng = np.random.default_rng(0)
+    g = rng.standard_normal((7, 7))
+    g = np.triu(g, 1) + np.triu(g, 1).T
+    J = N_.xy_couplings(7, 1.2, g, 0.1)
+    assert np.allclose(J, B.ring_couplings(7, 1.2, g, 0.1), rtol=1e-15, atol=0)
+
+
+def test_invalid_arguments_are_reported(N_):
+    for N in (2, 14):
+        with pytest.raises(N_.NphcError) as ei:
+            N_.System(N, 1.0)
+        assert ei.value.status == 1
+    J = N_.xy_couplings(5, 1.0)
+    J[0, 1] += 1e-3
+    with pytest.raises(N_.NphcError):
+        N_.System(5, 1.0, J)
+    J = N_.xy_couplings(5, 1.0)
+    J[2, 3] = J[3, 2] = np.nan
+    with pytest.raises(N_.NphcError):
+        N_.System(5, 1.0, J)
+    g = np.ones((5, 5))
+    g[0, 1] = 2.0
+    with pytest.raises(N_.NphcError):
+        N_.xy_couplings(5, 1.0, g, 0.1)
+
+
+@pytest.mark.parametrize("N", [3, 10, 13])
+def test_system_dimensions(N_, N):
+    s = N_.System(N, 1.0)
+    assert (s.N, s.n, s.npaths) == (N, 2 * (N - 1), 4 ** (N - 1))
+    assert np.array_equal(s.couplings(), B.ring_couplings(N, 1.0))
+    assert s.workspace_size(1000) < s.workspace_size(100000)
