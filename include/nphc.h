@@ -93,13 +93,16 @@ typedef struct nphc_options {
     double h0, h_max, h_min;   /* first, largest and smallest step in t: 0.01, 0.05, 1e-14 */
     double eps_fp32;           /* FP32 corrector: accept when ||dz|| <= eps (1 + ||z||), 1e-5 */
     double eps_fp64;           /* FP64 corrector tolerance, 1e-9 */
-    double trust;              /* reject when the first correction exceeds trust (1 + ||z||), 0.1 */
+    double trust;              /* FP64: reject when the first correction exceeds trust (1 + ||z||), 0.1 */
+    double trust_fp32;         /* FP32: the same bound on the prediction error, 2e-3 (no wider
+                                  than what the FP64 corrector's tolerance implies) */
     double r_div;              /* FP64 divergence radius on ||z||_inf, 1e5 */
     double r_div_fp32;         /* FP32 radius at which divergence is decided, 1e4 */
     double rho_div;            /* FP32 declares divergence above this growth exponent, 0.5 */
     int max_newton_fp32;       /* corrector iterations per FP32 step, 3 */
     int max_newton_fp64;       /* corrector iterations per FP64 step, 3 */
     int max_steps;             /* step attempts per path, 5000 */
+    int max_steps_fp32;        /* step attempts per path in the FP32 pass before hand-off, 400 */
     int grow_after;            /* consecutive accepted steps before h doubles, 3 */
     int refine_iters;          /* Newton refinement steps at t = 1, 8 */
     double refine_eps;         /* refinement stops when ||dz|| <= eps (1 + ||z||), 1e-14 */
@@ -212,8 +215,9 @@ enum {
     NPHC_COUNT_HANDOFF,        /* paths the FP32 tracker handed to FP64 */
     NPHC_COUNT_RETRACKED,      /* paths re-tracked in FP64 from t = 0 */
     NPHC_COUNT_SOLVES,         /* linear solves summed over all tracking calls */
-    NPHC_COUNT_INDEX0,         /* + i: real SPs of Hessian index i, i = 0 .. NPHC_MAX_N-2 */
-    NPHC_NCOUNTS = NPHC_COUNT_INDEX0 + NPHC_MAX_N - 1
+    NPHC_COUNT_LAUNCHES,       /* kernels the last nphc_solve_into launched (host count) */
+    NPHC_COUNT_INDEX0,         /* + i: real SPs of Hessian index i, i = 0 .. NPHC_MAX_N-1 */
+    NPHC_NCOUNTS = NPHC_COUNT_INDEX0 + NPHC_MAX_N
 };
 
 /* Allocates device buffers for every path of sys (the result keeps a reference to no

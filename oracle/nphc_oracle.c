@@ -495,7 +495,7 @@ static int beta_and_inv_norm(const qsys *S, const cplx *z, double *beta, double 
 }
 
 typedef struct {
-    double tol_sol;       /* Delta_sol: ||P(z)||_inf at the refined point */
+    double tol_sol;       /* Delta_sol: ||P(z)||_inf <= tol_sol * max(1, ||z||_inf^2) */
     double refine_eps;    /* Newton refinement stops when ||dz|| <= eps (1 + ||z||) */
     int refine_iters;     /* at most this many refinement steps */
     double alpha0;        /* alpha threshold, (13 - 3 sqrt 17) / 4 */
@@ -526,7 +526,11 @@ static int refine_certify_one(const qsys *S, double d2, const oracle_cert_opts *
     if (beta_and_inv_norm(S, z, &beta, &invF, w)) return OC_SINGULAR;
     double gam = invF * d2, alpha = beta * gam;
     *alpha_out = alpha; *beta_out = beta; *gam_out = gam;
-    if (!(res <= o->tol_sol) || !(alpha < o->alpha0)) return OC_SINGULAR;
+    /* the solution tolerance is applied relative to the size of the equations' terms:
+     * every equation is quadratic, so at ||z|| >> 1 its terms are ~||z||^2 and an absolute
+     * 1e-10 would sit below the rounding of their sum */
+    double zi = norminf(n, z), scale = zi > 1.0 ? zi * zi : 1.0;
+    if (!(res <= o->tol_sol * scale) || !(alpha < o->alpha0)) return OC_SINGULAR;
     /* real test: alpha at x = Re z, a real point of a real system, so that Newton's
      * iterates from x stay real and converge to a real solution */
     cplx *x = w->zs;

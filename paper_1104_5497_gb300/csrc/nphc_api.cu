@@ -41,23 +41,24 @@ int64_t table_size_for(int64_t count) {
     return t;
 }
 
-// Device scratch: [queue counters | dedup table | rep | minpath | gsize | amb | inlist]
+// Device scratch: [queue counters | tracker path state | dedup cell keys | cell list
+// heads | list links | flags].  The tracker state holds three vectors of 2M complex
+// doubles for each of NPHC_TRACK_MAX_THREADS threads (enough for either precision).
 struct WsLayout {
-    size_t queue, table, rep, minpath, gsize, amb, inlist, total;
+    size_t queue, state, keys, head, next, inlist, total;
     int64_t tsize;
 };
 
-WsLayout ws_layout(int64_t count) {
+WsLayout ws_layout(int M, int64_t count) {
     WsLayout L;
     L.tsize = table_size_for(count);
     size_t o = 0;
-    L.queue = o;   o += align256(64);
-    L.table = o;   o += align256(sizeof(int32_t) * L.tsize);
-    L.rep = o;     o += align256(sizeof(int32_t) * count);
-    L.minpath = o; o += align256(sizeof(int64_t) * count);
-    L.gsize = o;   o += align256(sizeof(int32_t) * count);
-    L.amb = o;     o += align256(sizeof(int32_t) * count);
-    L.inlist = o;  o += align256(sizeof(int32_t) * count);
+    L.queue = o;  o += align256(64);
+    L.state = o;  o += align256((size_t)3 * 2 * M * NPHC_TRACK_MAX_THREADS * 2 * sizeof(double));
+    L.keys = o;   o += align256(sizeof(unsigned long long) * L.tsize * DD_LEVELS);
+    L.head = o;   o += align256(sizeof(int32_t) * L.tsize * DD_LEVELS);
+    L.next = o;   o += align256(sizeof(int32_t) * count * DD_LEVELS);
+    L.inlist = o; o += align256(sizeof(int32_t) * count);
     L.total = o;
     return L;
 }
@@ -65,12 +66,10 @@ WsLayout ws_layout(int64_t count) {
 DedupScratch dedup_scratch(void *ws, const WsLayout &L) {
     char *b = static_cast<char *>(ws);
     DedupScratch w;
-    w.table = reinterpret_cast<int32_t *>(b + L.table);
+    w.keys = reinterpret_cast<unsigned long long *>(b + L.keys);
+    w.head = reinterpret_cast<int32_t *>(b + L.head);
     w.table_size = L.tsize;
-    w.rep = reinterpret_cast<int32_t *>(b + L.rep);
-    w.minpath = reinterpret_cast<long long *>(b + L.minpath);
-    w.gsize = reinterpret_cast<int32_t *>(b + L.gsize);
-    w.amb = reinterpret_cast<int32_t *>(b + L.amb);
+    w.next = reinterpret_cast<int32_t *>(b + L.next);
     w.inlist = reinterpret_cast<int32_t *>(b + L.inlist);
     return w;
 }
@@ -95,7 +94,7 @@ struct nphc_result {
     size_t bytes;
     nphc_endpoints ep;       // device arrays for all paths
     double *theta, *energy, *mineig;
-    int32_t *index, *flags, *list[3], *lcount, *real_list;
+    int32_t *index, *flags, *list[4], *lcount, *real_list;
     int64_t *counts;
     double *o_theta, *o_energy, *o_alpha;
     int32_t *o_index;
@@ -104,6 +103,7 @@ struct nphc_result {
     size_t ws_bytes;
     cudaStream_t stream;
     bool solved;
+    int64_t launches;        // kernels launched by the last solve (host count)
 };
 
 extern "C" {
@@ -124,12 +124,14 @@ nphc_status nphc_options_default(nphc_options *o) {
     o->eps_fp32 = 1e-5;
     o->eps_fp64 = 1e-9;
     o->trust = 0.1;
+    o->trust_fp32 = 2e-3;
     o->r_div = 1e5;
     o->r_div_fp32 = 1e4;
     o->rho_div = 0.5;
     o->max_newton_fp32 = 3;
     o->max_newton_fp64 = 3;
     o->max_steps = 5000;
+    o->max_steps_fp32 = 400;
     o->grow_after = 3;
     o->refine_iters = 8;
     o->refine_eps = 1e-14;
@@ -223,7 +225,7 @@ void nphc_system_destroy(nphc_system *S) { delete S; }
 
 nphc_status nphc_workspace_size(const nphc_system *S, int64_t count, size_t *bytes) {
     if (!S || !bytes || count < 0) return fail(NPHC_EINVAL, "invalid argument");
-    *bytes = ws_layout(count).total;
+    *bytes = ws_layout(S->M, count).total;
     return NPHC_OK;
 }
 
@@ -237,8 +239,9 @@ nphc_status check_opt(const nphc_options *o) {
     const double g2 = o->gamma_re * o->gamma_re + o->gamma_im * o->gamma_im;
     if (!(g2 > 0.0) || !std::isfinite(g2)) return fail(NPHC_EINVAL, "|gamma| = 0 or not finite");
     if (!(o->h0 > 0 && o->h_max >= o->h0 && o->h_min > 0 && o->eps_fp32 > 0 && o->eps_fp64 > 0 &&
-          o->trust > 0 && o->r_div > 0 && o->r_div_fp32 > 0 && o->max_newton_fp32 > 0 &&
-          o->max_newton_fp64 > 0 && o->max_steps > 0 && o->grow_after > 0 && o->refine_iters >= 0))
+          o->trust > 0 && o->trust_fp32 > 0 && o->r_div > 0 && o->r_div_fp32 > 0 && o->max_newton_fp32 > 0 &&
+          o->max_newton_fp64 > 0 && o->max_steps > 0 && o->max_steps_fp32 > 0 && o->grow_after > 0 &&
+          o->refine_iters >= 0))
         return fail(NPHC_EINVAL, "options out of range");
     return NPHC_OK;
 }
@@ -256,16 +259,17 @@ XYCtl make_ctl(const nphc_options *o, bool fp32, bool resume, bool accumulate) {
     c.hmax = o->h_max;
     c.hmin = o->h_min;
     c.eps = fp32 ? o->eps_fp32 : o->eps_fp64;
-    c.trust = o->trust;
+    c.trust = fp32 ? o->trust_fp32 : o->trust;
     c.rdiv = o->r_div;
     c.rdiv_soft = fp32 ? o->r_div_fp32 : o->r_div;
     c.rho_div = o->rho_div;
     c.max_newton = fp32 ? o->max_newton_fp32 : o->max_newton_fp64;
-    c.max_steps = o->max_steps;
+    c.max_steps = fp32 ? o->max_steps_fp32 : o->max_steps;
     c.grow_after = o->grow_after;
     c.handoff = fp32 ? 1 : 0;
     c.resume = resume ? 1 : 0;
     c.accumulate = accumulate ? 1 : 0;
+    c.sparse = 0;
     return c;
 }
 
@@ -294,11 +298,15 @@ nphc_status track_impl(const nphc_system *S, const nphc_options *o, nphc_precisi
                        bool resume, bool accumulate, void *ws, int queue_slot, cudaStream_t st) {
     const bool f32 = prec == NPHC_PREC_MIXED;
     const XYSys xs = sys_with_gamma(S, o);
-    const XYCtl ctl = make_ctl(o, f32, resume, accumulate);
+    XYCtl ctl = make_ctl(o, f32, resume, accumulate);
+    // short FP64 lists (hand-offs, re-tracks) run one path per warp, spread over every SM
+    ctl.sparse = (!f32 && list != nullptr) ? 1 : 0;
     WorkList wl;
     wl.list = list;
     wl.list_count = list_count;
     wl.queue = ws_queue(ws, queue_slot);
+    wl.state = static_cast<char *>(ws) + ws_layout(S->M, 0).state;
+    wl.state_threads = NPHC_TRACK_MAX_THREADS;
     NPHC_CK(cudaMemsetAsync(wl.queue, 0, sizeof(unsigned long long), st));
     int grid = 0;
     if (f32 && o->blocks_per_sm > 0) {
@@ -339,7 +347,7 @@ nphc_status nphc_track(const nphc_system *S, const nphc_options *o, nphc_precisi
     if ((s = check_opt(o)) != NPHC_OK) return s;
     if (prec != NPHC_PREC_FP64 && prec != NPHC_PREC_MIXED) return fail(NPHC_EINVAL, "precision");
     if ((list == nullptr) != (list_count == nullptr)) return fail(NPHC_EINVAL, "list without count");
-    if (!ws || ws_bytes < ws_layout(ep->count).total) return fail(NPHC_EINVAL, "workspace too small");
+    if (!ws || ws_bytes < ws_layout(S->M, ep->count).total) return fail(NPHC_EINVAL, "workspace too small");
     return track_impl(S, o, prec, ep, list, list_count, resume != 0, resume != 0, ws, 0,
                       (cudaStream_t)stream);
 }
@@ -355,6 +363,8 @@ nphc_status nphc_refine_certify(const nphc_system *S, const nphc_options *o,
     wl.list = list;
     wl.list_count = list_count;
     wl.queue = nullptr;
+    wl.state = nullptr;
+    wl.state_threads = 0;
     NPHC_CK(launch_xy_refine_certify(S->M, sys_with_gamma(S, o), o->tol_sol, o->refine_eps,
                                      o->refine_iters, view(ep), ep->count, wl, (cudaStream_t)stream));
     return NPHC_OK;
@@ -367,7 +377,7 @@ nphc_status nphc_dedup(const nphc_system *S, const nphc_options *o, const nphc_e
     if ((s = check_ep(S, ep, true)) != NPHC_OK) return s;
     (void)o;
     if ((dup_list == nullptr) != (dup_count == nullptr)) return fail(NPHC_EINVAL, "list without count");
-    const WsLayout L = ws_layout(ep->count);
+    const WsLayout L = ws_layout(S->M, ep->count);
     if (!ws || ws_bytes < L.total) return fail(NPHC_EINVAL, "workspace too small");
     NPHC_CK(launch_dedup(view(ep), S->n, kDedupDelta, dedup_scratch(ws, L), dup_list, dup_count,
                          (cudaStream_t)stream));
@@ -390,7 +400,7 @@ nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
     *out = nullptr;
     const int64_t P = S->npaths;
     const int n = S->n, M = S->M;
-    const WsLayout L = ws_layout(P);
+    const WsLayout L = ws_layout(M, P);
     // sub-allocation plan
     std::vector<size_t> sz = {
         sizeof(int64_t) * P,            // 0 path
@@ -416,14 +426,15 @@ nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
         sizeof(int32_t) * P,            // 20 list1
         sizeof(int32_t) * P,            // 21 list2
         sizeof(int32_t) * 8,            // 22 lcount
-        sizeof(int32_t) * P,            // 23 real_list
-        sizeof(int64_t) * NPHC_NCOUNTS, // 24 counts
-        sizeof(double) * M * P,         // 25 o_theta
-        sizeof(double) * P,             // 26 o_energy
-        sizeof(double) * P,             // 27 o_alpha
-        sizeof(int32_t) * P,            // 28 o_index
-        sizeof(int64_t) * P,            // 29 o_path
-        L.total};                       // 30 workspace
+        sizeof(int32_t) * P,            // 23 list3
+        sizeof(int32_t) * P,            // 24 real_list
+        sizeof(int64_t) * NPHC_NCOUNTS, // 25 counts
+        sizeof(double) * M * P,         // 26 o_theta
+        sizeof(double) * P,             // 27 o_energy
+        sizeof(double) * P,             // 28 o_alpha
+        sizeof(int32_t) * P,            // 29 o_index
+        sizeof(int64_t) * P,            // 30 o_path
+        L.total};                       // 31 workspace
     std::vector<size_t> off(sz.size());
     size_t tot = 0;
     for (size_t i = 0; i < sz.size(); i++) {
@@ -471,14 +482,15 @@ nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
     R->list[1] = (int32_t *)at(20);
     R->list[2] = (int32_t *)at(21);
     R->lcount = (int32_t *)at(22);
-    R->real_list = (int32_t *)at(23);
-    R->counts = (int64_t *)at(24);
-    R->o_theta = (double *)at(25);
-    R->o_energy = (double *)at(26);
-    R->o_alpha = (double *)at(27);
-    R->o_index = (int32_t *)at(28);
-    R->o_path = (int64_t *)at(29);
-    R->ws = at(30);
+    R->list[3] = (int32_t *)at(23);
+    R->real_list = (int32_t *)at(24);
+    R->counts = (int64_t *)at(25);
+    R->o_theta = (double *)at(26);
+    R->o_energy = (double *)at(27);
+    R->o_alpha = (double *)at(28);
+    R->o_index = (int32_t *)at(29);
+    R->o_path = (int64_t *)at(30);
+    R->ws = at(31);
     R->ws_bytes = L.total;
     R->stream = nullptr;
     R->solved = false;
@@ -503,13 +515,10 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
     const nphc_endpoints *ep = &R->ep;
     const EPView v = view(ep);
     const XYSys xs = sys_with_gamma(S, o);
-    const WsLayout L = ws_layout(R->P);
+    const WsLayout L = ws_layout(R->M, R->P);
     const DedupScratch dsc = dedup_scratch(R->ws, L);
-    WorkList all;
-    all.list = nullptr;
-    all.list_count = nullptr;
-    all.queue = nullptr;
     R->solved = false;
+    const int64_t launches0 = nphc_launch_counter(0);
     NPHC_CK(cudaMemsetAsync(R->flags, 0, sizeof(int32_t) * R->P, st));
     NPHC_CK(cudaMemsetAsync(R->lcount, 0, sizeof(int32_t) * 8, st));
     const bool mixed = o->precision == NPHC_PREC_MIXED;
@@ -521,16 +530,15 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
         NPHC_CK(launch_compact(v, PRED_HANDOFF, R->flags, R->list[0], R->lcount + 0, st));
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[0], R->lcount + 0, true, true, R->ws, 1, st)))
             return s;
+        NPHC_CK(launch_compact(v, PRED_REACHED, R->flags, R->list[3], R->lcount + 3, st));
+        WorkList l3 = {R->list[3], R->lcount + 3, nullptr, nullptr, 0};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
-                                         R->P, all, st));
+                                         R->P, l3, st));
         // FP64 re-track of FP32 endpoints that did not certify
         NPHC_CK(launch_compact(v, PRED_UNCERTIFIED_FP32, R->flags, R->list[1], R->lcount + 1, st));
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[1], R->lcount + 1, false, true, R->ws, 2, st)))
             return s;
-        WorkList l1;
-        l1.list = R->list[1];
-        l1.list_count = R->lcount + 1;
-        l1.queue = nullptr;
+        WorkList l1 = {R->list[1], R->lcount + 1, nullptr, nullptr, 0};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
                                          R->P, l1, st));
         // deduplicate; every path of a solution reached more than once is re-tracked in
@@ -539,24 +547,24 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
         NPHC_CK(launch_flag_list(R->list[2], R->lcount + 2, R->P, R->flags, FLAG_RETRACKED_DUP, st));
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[2], R->lcount + 2, false, true, R->ws, 3, st)))
             return s;
-        WorkList l2;
-        l2.list = R->list[2];
-        l2.list_count = R->lcount + 2;
-        l2.queue = nullptr;
+        WorkList l2 = {R->list[2], R->lcount + 2, nullptr, nullptr, 0};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
                                          R->P, l2, st));
         NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st));
     } else {
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, nullptr, nullptr, false, false, R->ws, 0, st)))
             return s;
+        NPHC_CK(launch_compact(v, PRED_REACHED, R->flags, R->list[3], R->lcount + 3, st));
+        WorkList l3 = {R->list[3], R->lcount + 3, nullptr, nullptr, 0};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
-                                         R->P, all, st));
+                                         R->P, l3, st));
         NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st));
     }
     NPHC_CK(launch_xy_classify(S->M, xs, v, R->theta, R->index, R->energy, R->mineig, st));
     NPHC_CK(launch_counts(v, R->flags, R->index, R->counts, st));
     R->stream = st;
     R->solved = true;
+    R->launches = nphc_launch_counter(0) - launches0;
     return NPHC_OK;
 }
 
@@ -583,6 +591,7 @@ nphc_status nphc_result_counts(const nphc_result *R, int64_t *counts) {
     if (!R->solved) return fail(NPHC_ESTATE, "no solve on this result");
     NPHC_CK(cudaStreamSynchronize(R->stream));
     NPHC_CK(cudaMemcpy(counts, R->counts, sizeof(int64_t) * NPHC_NCOUNTS, cudaMemcpyDeviceToHost));
+    counts[NPHC_COUNT_LAUNCHES] = R->launches;
     return NPHC_OK;
 }
 

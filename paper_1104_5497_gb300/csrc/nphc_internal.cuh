@@ -13,7 +13,7 @@
 
 // ------------------------------------------------------------------ complex --
 template <class R>
-struct cx {
+struct alignas(2 * sizeof(R)) cx {
     R re, im;
 };
 
@@ -109,6 +109,7 @@ struct XYCtl {                              // step control of one tracking call
     int handoff;                            // 1: stops become NPHC_PATH_HANDOFF (FP32 pass)
     int resume;                             // 1: continue from (z, t, h) of the entry
     int accumulate;                         // 1: add to the entry's step/solve counters
+    int sparse;                             // 1: one path per warp (lane 0 only)
 };
 
 struct EPView {                             // device endpoint arrays (see nphc_endpoints)
@@ -123,7 +124,13 @@ struct WorkList {                           // which entries a launch processes
     const int32_t *list;                    // NULL: all entries
     const int32_t *list_count;              // device count of list
     unsigned long long *queue;              // zeroed work counter (persistent kernels)
+    void *state;                            // tracker scratch: per-thread path state
+    int64_t state_threads;                  // threads the scratch holds state for
 };
+
+// Threads of a persistent tracker grid the tracker scratch is sized for (a grid never
+// launches more threads than this).
+#define NPHC_TRACK_MAX_THREADS 65536
 
 __device__ __forceinline__ int64_t worklist_size(const WorkList &w, int64_t count) {
     return w.list ? (int64_t)(*w.list_count) : count;
@@ -144,5 +151,7 @@ cudaError_t launch_xy_refine_certify(int M, const XYSys &sys, double tol_sol, do
 cudaError_t launch_xy_classify(int M, const XYSys &sys, const EPView &ep, double *theta,
                                int32_t *index, double *energy, double *min_eig,
                                cudaStream_t st);
+// Host-side count of kernel launches made by this library (for the result counters).
+int64_t nphc_launch_counter(int64_t add);
 int xy_track_f32_block(int M);
 int xy_track_f64_block(int M);

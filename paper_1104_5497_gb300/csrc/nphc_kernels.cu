@@ -2,6 +2,13 @@
 // compaction, deduplication of certified endpoints, and result counters.
 #include "nphc_kernels.cuh"
 
+#include <atomic>
+
+int64_t nphc_launch_counter(int64_t add) {
+    static std::atomic<int64_t> n{0};
+    return n.fetch_add(add) + add;
+}
+
 // ------------------------------------------------------------- compaction --
 __global__ void compact_kernel(const EPView ep, int pred, int32_t *flags, int32_t *list,
                                int32_t *count) {
@@ -14,6 +21,14 @@ __global__ void compact_kernel(const EPView ep, int pred, int32_t *flags, int32_
     } else if (pred == PRED_UNCERTIFIED_FP32) {
         take = ep.cls[e] == NPHC_END_SINGULAR && !(flags[e] & (FLAG_FP64_CONTINUED | FLAG_RETRACKED));
         if (take) flags[e] |= FLAG_RETRACKED;
+    } else if (pred == PRED_REACHED) {
+        // endpoints to refine; every other path gets its final class here
+        const int st = ep.status[e];
+        take = st == NPHC_PATH_REACHED;
+        if (!take) {
+            ep.cls[e] = st == NPHC_PATH_DIVERGED ? NPHC_END_NONE : NPHC_END_FAILED;
+            ep.alpha[e] = ep.beta[e] = ep.gamma[e] = ep.resid[e] = INFINITY;
+        }
     }
     if (take) list[atomicAdd(count, 1)] = (int32_t)e;
 }
@@ -27,16 +42,18 @@ __global__ void flag_list_kernel(const int32_t *list, const int32_t *count, int3
 }
 
 // ------------------------------------------------------------------ dedup --
-// Certified endpoints are rounded to a grid of pitch delta.  Two certified endpoints of
-// one solution lie within 2 (beta_a + beta_b) of each other (each is within 2 beta of
-// it), so when both betas are <= BETA_HASH and no coordinate lies within
-// BAND = 4 BETA_HASH (< BAND_FRAC delta) of a cell boundary, they fall in the same cell.
-// An endpoint that fails either condition is "ambiguous" and is compared with every
-// certified endpoint instead (rare: ~2 n BAND_FRAC of the endpoints).  Cells live in an
-// open-addressing table; inside a cell the alpha-theory test decides.
-
-#define BETA_HASH 1e-12
-#define BAND_FRAC 1e-5
+// Two certified endpoints of one solution lie within 2 (beta_a + beta_b) of each other
+// (each is within 2 beta of it).  Candidates are found through grids on four
+// coordinates (Re/Im of c_1 and of s_1) at DD_LEVELS pitches delta_L = delta_0 100^L.
+// Every hashed endpoint is listed under its cell at every level; an endpoint e looks up
+// level L(e), the finest with 4 beta_e <= DD_BAND delta_L, in its own cell plus, in
+// each coordinate within DD_BAND cells of a boundary, the neighbour across it.  A copy
+// o with beta_o <= beta_e lies within 4 beta_e of e, so e finds it; a copy with a larger
+// beta finds e at its own level.  Each match marks the higher path index a duplicate,
+// so the lowest path of every solution keeps its class.  The alpha-theory test decides
+// each candidate pair.  Endpoints whose beta exceeds the coarsest level are compared
+// with every certified endpoint instead.
+#define DD_BAND 0.05
 
 __device__ __forceinline__ bool is_certified(int c) {
     return c == NPHC_END_REAL || c == NPHC_END_NONREAL || c == NPHC_END_UNDECIDED;
@@ -49,30 +66,27 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
     return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ uint64_t cell_hash(const EPView &ep, int n, int64_t e, double inv_delta,
-                                              bool &amb) {
-    uint64_t hsh = 0x2545F4914F6CDD1Dull;
-    amb = false;
-    const int64_t cnt = ep.count;
-    for (int i = 0; i < n; i++) {
-        const double v[2] = {ep.z_re[i * cnt + e] * inv_delta, ep.z_im[i * cnt + e] * inv_delta};
-        for (int p = 0; p < 2; p++) {
-            const double r = rint(v[p]);
-            if (fabs(v[p] - r) > 0.5 - BAND_FRAC) amb = true;
-            hsh = mix64(hsh ^ (uint64_t)(long long)r);
-        }
-    }
-    return hsh;
+__device__ __forceinline__ double dd_pitch(double delta0, int level) {
+    double d = delta0;
+    for (int l = 0; l < level; l++) d *= 100.0;
+    return d;
 }
 
-__device__ __forceinline__ bool same_cell(const EPView &ep, int n, int64_t a, int64_t b,
-                                          double inv_delta) {
+// The four grid coordinates of entry e, in units of the pitch.
+__device__ __forceinline__ void dd_coords(const EPView &ep, int n, int64_t e, double inv_delta,
+                                          double (&v)[4]) {
     const int64_t cnt = ep.count;
-    for (int i = 0; i < n; i++) {
-        if (rint(ep.z_re[i * cnt + a] * inv_delta) != rint(ep.z_re[i * cnt + b] * inv_delta)) return false;
-        if (rint(ep.z_im[i * cnt + a] * inv_delta) != rint(ep.z_im[i * cnt + b] * inv_delta)) return false;
-    }
-    return true;
+    const int m = n / 2;
+    v[0] = ep.z_re[e] * inv_delta;
+    v[1] = ep.z_im[e] * inv_delta;
+    v[2] = ep.z_re[m * cnt + e] * inv_delta;
+    v[3] = ep.z_im[m * cnt + e] * inv_delta;
+}
+
+__device__ __forceinline__ uint64_t dd_cell_key(int level, const long long (&q)[4]) {
+    uint64_t h = 0x2545F4914F6CDD1Dull ^ (uint64_t)level;
+    for (int i = 0; i < 4; i++) h = mix64(h ^ (uint64_t)q[i]);
+    return h | 1ull;   // 0 marks an empty slot
 }
 
 // alpha-theory: the same solution when alpha < 0.03 and ||za - zb|| < 1 / (20 gamma) for
@@ -93,41 +107,37 @@ __device__ __forceinline__ bool same_solution(const EPView &ep, int n, int64_t a
     return sa || sb || !distinct;
 }
 
-__global__ void dedup_insert_kernel(const EPView ep, int n, double inv_delta, DedupScratch w) {
+// finest level at which e's copies with smaller beta are within the band; DD_LEVELS if none
+__device__ __forceinline__ int dd_level(double beta, double delta0) {
+    for (int L = 0; L < DD_LEVELS; L++)
+        if (4.0 * beta <= DD_BAND * dd_pitch(delta0, L)) return L;
+    return DD_LEVELS;
+}
+
+// phase 1: list every certified endpoint under its cell at every level
+__global__ void dedup_insert_kernel(const EPView ep, int n, double delta0, DedupScratch w) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ep.count) return;
-    w.rep[e] = -1;
+    for (int L = 0; L < DD_LEVELS; L++) w.next[L * ep.count + e] = -1;
     if (!is_certified(ep.cls[e])) return;
-    bool amb;
-    const uint64_t hsh = cell_hash(ep, n, e, inv_delta, amb);
-    if (amb || !(ep.beta[e] <= BETA_HASH)) {
-        w.amb[e] = 1;
-        return;
-    }
     const uint64_t mask = (uint64_t)w.table_size - 1;
-    uint64_t slot = hsh & mask;
-    int32_t rep = -1;
-    for (int64_t probe = 0; probe < w.table_size; probe++) {
-        int32_t cur = w.table[slot];
-        if (cur == -1) {
-            const int32_t prev = atomicCAS(&w.table[slot], -1, (int32_t)e);
-            if (prev == -1) {
-                rep = (int32_t)e;
+    for (int L = 0; L < DD_LEVELS; L++) {
+        double v[4];
+        long long q[4];
+        dd_coords(ep, n, e, 1.0 / dd_pitch(delta0, L), v);
+        for (int i = 0; i < 4; i++) q[i] = (long long)floor(v[i]);
+        const unsigned long long key = dd_cell_key(L, q);
+        unsigned long long *keys = w.keys + L * w.table_size;
+        int32_t *head = w.head + L * w.table_size;
+        uint64_t slot = key & mask;
+        for (int64_t probe = 0; probe < w.table_size; probe++) {
+            const unsigned long long cur = atomicCAS(&keys[slot], 0ull, key);
+            if (cur == 0ull || cur == key) {
+                w.next[L * ep.count + e] = atomicExch(&head[slot], (int32_t)e);
                 break;
             }
-            cur = prev;
+            slot = (slot + 1) & mask;
         }
-        if (same_cell(ep, n, cur, e, inv_delta) && same_solution(ep, n, cur, e)) {
-            rep = cur;
-            break;
-        }
-        slot = (slot + 1) & mask;
-    }
-    w.rep[e] = rep;
-    if (rep >= 0) {
-        atomicMin(reinterpret_cast<unsigned long long *>(&w.minpath[rep]),
-                  (unsigned long long)ep.path[e]);
-        atomicAdd(&w.gsize[rep], 1);
     }
 }
 
@@ -136,33 +146,73 @@ __device__ __forceinline__ void push_once(DedupScratch &w, int32_t *list, int32_
     if (atomicExch(&w.inlist[e], 1) == 0 && list) list[atomicAdd(count, 1)] = (int32_t)e;
 }
 
-__global__ void dedup_resolve_kernel(const EPView ep, DedupScratch w, int32_t *list,
-                                     int32_t *count) {
+__device__ __forceinline__ void dd_pair(const EPView &ep, DedupScratch &w, int32_t *list,
+                                        int32_t *count, int64_t e, int64_t o) {
+    if (ep.path[o] < ep.path[e])
+        ep.cls[e] = NPHC_END_DUPLICATE;
+    else
+        ep.cls[o] = NPHC_END_DUPLICATE;
+    push_once(w, list, count, e);
+    push_once(w, list, count, o);
+}
+
+// phase 2: compare with the endpoints of the own and the neighbouring cells at level L(e)
+__global__ void dedup_match_kernel(const EPView ep, int n, double delta0, DedupScratch w,
+                                   int32_t *list, int32_t *count) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ep.count) return;
-    const int32_t r = w.rep[e];
-    if (r < 0) return;
-    if (w.gsize[r] > 1) {
-        if ((unsigned long long)ep.path[e] != (unsigned long long)w.minpath[r])
-            ep.cls[e] = NPHC_END_DUPLICATE;
-        push_once(w, list, count, e);
+    if (e >= ep.count || !is_certified(ep.cls[e])) return;
+    const int L = dd_level(ep.beta[e], delta0);
+    if (L >= DD_LEVELS) return;   // phase 3
+    double v[4];
+    long long q0[4];
+    int dir[4];
+    dd_coords(ep, n, e, 1.0 / dd_pitch(delta0, L), v);
+    for (int i = 0; i < 4; i++) {
+        q0[i] = (long long)floor(v[i]);
+        const double f = v[i] - (double)q0[i];
+        dir[i] = f < DD_BAND ? -1 : (f > 1.0 - DD_BAND ? 1 : 0);
+    }
+    const uint64_t mask = (uint64_t)w.table_size - 1;
+    const unsigned long long *keys = w.keys + L * w.table_size;
+    const int32_t *head = w.head + L * w.table_size;
+    const int32_t *next = w.next + L * ep.count;
+    for (int combo = 0; combo < 16; combo++) {
+        long long q[4];
+        bool skip = false;
+        for (int i = 0; i < 4; i++) {
+            const int bit = (combo >> i) & 1;
+            if (bit && dir[i] == 0) skip = true;
+            q[i] = q0[i] + (bit ? dir[i] : 0);
+        }
+        if (skip) continue;
+        const unsigned long long key = dd_cell_key(L, q);
+        uint64_t slot = key & mask;
+        int32_t o = -1;
+        for (int64_t probe = 0; probe < w.table_size; probe++) {
+            const unsigned long long cur = keys[slot];
+            if (cur == 0ull) break;
+            if (cur == key) {
+                o = head[slot];
+                break;
+            }
+            slot = (slot + 1) & mask;
+        }
+        for (int64_t guard = 0; o >= 0 && guard < ep.count; guard++) {
+            if (o != e && same_solution(ep, n, e, o)) dd_pair(ep, w, list, count, e, o);
+            o = next[o];
+        }
     }
 }
 
-// Ambiguous endpoints: compared with every certified endpoint.
-__global__ void dedup_ambiguous_kernel(const EPView ep, int n, DedupScratch w, int32_t *list,
-                                       int32_t *count) {
+__global__ void dedup_unhashed_kernel(const EPView ep, int n, double delta0, DedupScratch w,
+                                      int32_t *list, int32_t *count) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ep.count || !w.amb[e]) return;
+    if (e >= ep.count || !is_certified(ep.cls[e]) || dd_level(ep.beta[e], delta0) < DD_LEVELS) return;
     for (int64_t j = 0; j < ep.count; j++) {
-        if (j == e || !is_certified(ep.cls[j])) continue;
-        if (!same_solution(ep, n, e, j)) continue;
-        if (ep.path[j] < ep.path[e])
-            ep.cls[e] = NPHC_END_DUPLICATE;
-        else
-            ep.cls[j] = NPHC_END_DUPLICATE;
-        push_once(w, list, count, e);
-        push_once(w, list, count, j);
+        if (j == e) continue;
+        const int cj = ep.cls[j];
+        if (!is_certified(cj) && cj != NPHC_END_DUPLICATE) continue;
+        if (same_solution(ep, n, e, j)) dd_pair(ep, w, list, count, e, j);
     }
 }
 
@@ -192,7 +242,7 @@ __global__ void counts_kernel(const EPView ep, const int32_t *flags, const int32
         atomicAdd(&loc[NPHC_COUNT_SOLVES], (unsigned long long)ep.solves[e]);
         if (c == NPHC_END_REAL && index) {
             const int ix = index[e];
-            if (ix >= 0 && ix < NPHC_MAX_N - 1) atomicAdd(&loc[NPHC_COUNT_INDEX0 + ix], 1ull);
+            if (ix >= 0 && ix < NPHC_MAX_N) atomicAdd(&loc[NPHC_COUNT_INDEX0 + ix], 1ull);
         }
     }
     __syncthreads();
@@ -234,6 +284,7 @@ cudaError_t launch_compact(const EPView &ep, int pred, int32_t *flags, int32_t *
                            int32_t *count, cudaStream_t st) {
     if (ep.count == 0) return cudaSuccess;
     compact_kernel<<<blocks_for(ep.count, 256), 256, 0, st>>>(ep, pred, flags, list, count);
+    nphc_launch_counter(1);
     return cudaGetLastError();
 }
 
@@ -241,6 +292,7 @@ cudaError_t launch_flag_list(const int32_t *list, const int32_t *count, int64_t 
                              int32_t *flags, int32_t bit, cudaStream_t st) {
     if (cap == 0) return cudaSuccess;
     flag_list_kernel<<<blocks_for(cap, 256), 256, 0, st>>>(list, count, flags, bit);
+    nphc_launch_counter(1);
     return cudaGetLastError();
 }
 
@@ -248,16 +300,18 @@ cudaError_t launch_dedup(const EPView &ep, int n, double delta, DedupScratch w, 
                          int32_t *count, cudaStream_t st) {
     if (ep.count == 0) return cudaSuccess;
     cudaError_t err;
-    if ((err = cudaMemsetAsync(w.table, 0xff, sizeof(int32_t) * w.table_size, st))) return err;
-    if ((err = cudaMemsetAsync(w.minpath, 0xff, sizeof(int64_t) * ep.count, st))) return err;
-    if ((err = cudaMemsetAsync(w.gsize, 0, sizeof(int32_t) * ep.count, st))) return err;
-    if ((err = cudaMemsetAsync(w.amb, 0, sizeof(int32_t) * ep.count, st))) return err;
+    const size_t slots = (size_t)DD_LEVELS * w.table_size;
+    if ((err = cudaMemsetAsync(w.keys, 0, sizeof(unsigned long long) * slots, st))) return err;
+    if ((err = cudaMemsetAsync(w.head, 0xff, sizeof(int32_t) * slots, st))) return err;
     if ((err = cudaMemsetAsync(w.inlist, 0, sizeof(int32_t) * ep.count, st))) return err;
     if (count && (err = cudaMemsetAsync(count, 0, sizeof(int32_t), st))) return err;
     const int g = blocks_for(ep.count, 256);
-    dedup_insert_kernel<<<g, 256, 0, st>>>(ep, n, 1.0 / delta, w);
-    dedup_resolve_kernel<<<g, 256, 0, st>>>(ep, w, list, count);
-    dedup_ambiguous_kernel<<<g, 256, 0, st>>>(ep, n, w, list, count);
+    dedup_insert_kernel<<<g, 256, 0, st>>>(ep, n, delta, w);
+    nphc_launch_counter(1);
+    dedup_match_kernel<<<g, 256, 0, st>>>(ep, n, delta, w, list, count);
+    nphc_launch_counter(1);
+    dedup_unhashed_kernel<<<g, 256, 0, st>>>(ep, n, delta, w, list, count);
+    nphc_launch_counter(1);
     return cudaGetLastError();
 }
 
@@ -266,6 +320,7 @@ cudaError_t launch_counts(const EPView &ep, const int32_t *flags, const int32_t 
     cudaError_t err = cudaMemsetAsync(counts, 0, sizeof(int64_t) * NPHC_NCOUNTS, st);
     if (err || ep.count == 0) return err;
     counts_kernel<<<blocks_for(ep.count, 256), 256, 0, st>>>(ep, flags, index, counts);
+    nphc_launch_counter(1);
     return cudaGetLastError();
 }
 
@@ -273,12 +328,14 @@ cudaError_t launch_real_list(const EPView &ep, int32_t *list, int32_t *count, cu
     cudaError_t err = cudaMemsetAsync(count, 0, sizeof(int32_t), st);
     if (err || ep.count == 0) return err;
     real_list_kernel<<<blocks_for(ep.count, 256), 256, 0, st>>>(ep, list, count);
+    nphc_launch_counter(1);
     return cudaGetLastError();
 }
 
 cudaError_t launch_iota(int64_t *path, int64_t n, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
     iota_kernel<<<blocks_for(n, 256), 256, 0, st>>>(path, n);
+    nphc_launch_counter(1);
     return cudaGetLastError();
 }
 
@@ -289,5 +346,6 @@ cudaError_t launch_gather_sps(const EPView &ep, int M, const int32_t *list, cons
     if (cap == 0) return cudaSuccess;
     gather_sps_kernel<<<blocks_for(cap, 256), 256, 0, st>>>(ep, M, list, count, theta, index, energy,
                                                           o_theta, o_index, o_energy, o_alpha, o_path);
+    nphc_launch_counter(1);
     return cudaGetLastError();
 }

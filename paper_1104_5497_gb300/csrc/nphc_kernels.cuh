@@ -3,18 +3,18 @@
 
 #include "nphc_internal.cuh"
 
-enum { PRED_HANDOFF = 1, PRED_UNCERTIFIED_FP32 = 2 };
+enum { PRED_HANDOFF = 1, PRED_UNCERTIFIED_FP32 = 2, PRED_REACHED = 3 };
 enum { FLAG_FP64_CONTINUED = 1, FLAG_RETRACKED = 2, FLAG_RETRACKED_DUP = 4 };
 
-// Device scratch of the deduplication (all arrays sized for the endpoint count, the
-// table a power of two >= 2 x count).
+#define DD_LEVELS 4   // grid pitches 1e-6, 1e-4, 1e-2, 1
+
+// Device scratch of the deduplication: per level, an open-addressing table of grid
+// cells (keys, list heads; a power of two >= 2 x count slots) and per-entry list links.
 struct DedupScratch {
-    int32_t *table;
+    unsigned long long *keys;
+    int32_t *head;
     int64_t table_size;
-    int32_t *rep;
-    long long *minpath;
-    int32_t *gsize;
-    int32_t *amb;
+    int32_t *next;
     int32_t *inlist;
 };
 

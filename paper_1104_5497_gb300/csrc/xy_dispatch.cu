@@ -32,5 +32,5 @@ cudaError_t launch_xy_classify(int M, const XYSys &sys, const EPView &ep, double
 #undef C
 }
 
-int xy_track_f32_block(int M) { (void)M; return NPHC_F32_BLOCK; }
-int xy_track_f64_block(int M) { (void)M; return NPHC_F64_BLOCK; }
+int xy_track_f32_block(int M) { (void)M; return NPHC_TRACK_BLOCK; }
+int xy_track_f64_block(int M) { (void)M; return NPHC_TRACK_BLOCK; }

@@ -6,16 +6,10 @@
 #define NPHC_CAT2(a, b) a##b
 #define NPHC_CAT(a, b) NPHC_CAT2(a, b)
 
-#define NPHC_F32_BLOCK 128
-#define NPHC_F64_BLOCK 64
+#define NPHC_TRACK_BLOCK 32   // one warp per block: per-thread shared memory, no block sync
 #define NPHC_M_MIN 2
 #define NPHC_M_MAX 12
 #define NPHC_FOR_EACH_M(X) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
-
-// Shared memory of the tracker: five per-thread vectors of 2M complex numbers.
-inline size_t xy_track_smem_bytes(int M, size_t real_bytes, int block) {
-    return (size_t)5 * 4 * M * block * real_bytes;
-}
 
 #define NPHC_DECL(MM)                                                                         \
     cudaError_t launch_xy_track_f32_m##MM(const XYSys &, const XYCtl &, const EPView &,     \

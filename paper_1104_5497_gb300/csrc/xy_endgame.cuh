@@ -243,7 +243,10 @@ __global__ void __launch_bounds__(128)
         ep.beta[e] = beta;
         ep.gamma[e] = gam;
         ep.resid[e] = res;
-        if (res <= tol_sol && alpha < alpha0) {
+        // Delta_sol relative to the size of the (quadratic) terms: max(1, ||z||_inf^2)
+        double zi = 0.0;
+        for (int k = 0; k < M; k++) zi = fmax(zi, fmax(sqrt(cabs2(F.x[k])), sqrt(cabs2(F.y[k]))));
+        if (res <= tol_sol * fmax(1.0, zi * zi) && alpha < alpha0) {
             double im2 = 0.0;
             for (int k = 0; k < M; k++) im2 += F.x[k].im * F.x[k].im + F.y[k].im * F.y[k].im;
             if (sqrt(im2) > 2.0 * beta) {
@@ -290,67 +293,70 @@ __global__ void __launch_bounds__(128)
     }
     const double *J = S.Jd;
     constexpr int N = M + 1;
-    double th[N], c[N], s[N];
+    double c[N], s[N];
+#pragma unroll 1
     for (int k = 0; k < M; k++) {
         const double x = ep.z_re[k * cnt + e], y = ep.z_re[(M + k) * cnt + e];
         double a = atan2(y, x);
         if (a <= -M_PI) a = M_PI;
-        th[k] = a;
         sincos(a, &s[k], &c[k]);
         theta[k * cnt + e] = a;
     }
-    th[M] = 0.0;
-    c[M] = 1.0;
+    c[M] = 1.0;   // theta_N = 0
     s[M] = 0.0;
-    // energy: cos(theta_i - theta_j) = c_i c_j + s_i s_j
+    // V = sum_{i<j} J_ij (1 - cos(theta_i - theta_j)), cos(a - b) = c_a c_b + s_a s_b
     double V = 0.0;
+#pragma unroll 1
     for (int i = 0; i < N; i++)
         for (int j = i + 1; j < N; j++) V += J[i * NPHC_JSTRIDE + j] * (1.0 - (c[i] * c[j] + s[i] * s[j]));
-    double H[M][M];
-    for (int k = 0; k < M; k++)
-        for (int l = 0; l < M; l++) {
-            if (k == l) {
-                double d = 0.0;
-                for (int j = 0; j < N; j++)
-                    if (j != k) d += J[k * NPHC_JSTRIDE + j] * (c[k] * c[j] + s[k] * s[j]);
-                H[k][k] = d;
-            } else {
-                H[k][l] = -J[k * NPHC_JSTRIDE + l] * (c[k] * c[l] + s[k] * s[l]);
-            }
-        }
+    // Hessian in theta_1..theta_M (row-major, flat)
+    double H[M * M];
+#pragma unroll 1
+    for (int k = 0; k < M; k++) {
+        double d = 0.0;
+        for (int j = 0; j < N; j++)
+            if (j != k) d += J[k * NPHC_JSTRIDE + j] * (c[k] * c[j] + s[k] * s[j]);
+        for (int l = 0; l < M; l++)
+            H[k * M + l] = (k == l) ? d : -J[k * NPHC_JSTRIDE + l] * (c[k] * c[l] + s[k] * s[l]);
+    }
     // cyclic Jacobi rotations until the off-diagonal part is negligible
+#pragma unroll 1
     for (int sweep = 0; sweep < 64; sweep++) {
         double off = 0.0, tot = 0.0;
-        for (int p = 0; p < M; p++)
-            for (int q = 0; q < M; q++) {
-                tot += H[p][q] * H[p][q];
-                if (p != q) off += H[p][q] * H[p][q];
-            }
+        for (int i = 0; i < M * M; i++) {
+            tot += H[i] * H[i];
+            if (i / M != i % M) off += H[i] * H[i];
+        }
         if (off <= 1e-30 * tot) break;
+#pragma unroll 1
         for (int p = 0; p < M - 1; p++)
+#pragma unroll 1
             for (int q = p + 1; q < M; q++) {
-                const double apq = H[p][q];
+                const double apq = H[p * M + q];
                 if (apq == 0.0) continue;
-                const double tq = (H[q][q] - H[p][p]) / (2.0 * apq);
+                const double tq = (H[q * M + q] - H[p * M + p]) / (2.0 * apq);
                 const double tn = (tq >= 0.0 ? 1.0 : -1.0) / (fabs(tq) + sqrt(tq * tq + 1.0));
-                const double cs = rsqrt(tn * tn + 1.0), sn = tn * cs;
-                for (int k = 0; k < M; k++) {
-                    const double akp = H[k][p], akq = H[k][q];
-                    H[k][p] = cs * akp - sn * akq;
-                    H[k][q] = sn * akp + cs * akq;
+                const double cs = 1.0 / sqrt(tn * tn + 1.0), sn = tn * cs;
+#pragma unroll 1
+                for (int k = 0; k < M; k++) {   // columns p and q
+                    const double akp = H[k * M + p], akq = H[k * M + q];
+                    H[k * M + p] = cs * akp - sn * akq;
+                    H[k * M + q] = sn * akp + cs * akq;
                 }
-                for (int k = 0; k < M; k++) {
-                    const double apk = H[p][k], aqk = H[q][k];
-                    H[p][k] = cs * apk - sn * aqk;
-                    H[q][k] = sn * apk + cs * aqk;
+#pragma unroll 1
+                for (int k = 0; k < M; k++) {   // rows p and q
+                    const double apk = H[p * M + k], aqk = H[q * M + k];
+                    H[p * M + k] = cs * apk - sn * aqk;
+                    H[q * M + k] = sn * apk + cs * aqk;
                 }
             }
     }
     int neg = 0;
     double mn = INFINITY;
     for (int k = 0; k < M; k++) {
-        if (H[k][k] < 0.0) neg++;
-        mn = fmin(mn, fabs(H[k][k]));
+        const double w = H[k * M + k];
+        if (w < 0.0) neg++;
+        mn = fmin(mn, fabs(w));
     }
     index[e] = neg;
     energy[e] = V;

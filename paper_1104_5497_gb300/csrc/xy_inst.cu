@@ -10,19 +10,19 @@
 #if NPHC_INST_KIND == 0
 using RT = float;
 constexpr bool FFV = true;
-constexpr int BLK = NPHC_F32_BLOCK;
+constexpr int BLK = NPHC_TRACK_BLOCK;
 #define NPHC_FN NPHC_CAT(launch_xy_track_f32_m, NPHC_INST_M)
 #else
 using RT = double;
 constexpr bool FFV = false;
-constexpr int BLK = NPHC_F64_BLOCK;
+constexpr int BLK = NPHC_TRACK_BLOCK;
 #define NPHC_FN NPHC_CAT(launch_xy_track_f64_m, NPHC_INST_M)
 #endif
 
 cudaError_t NPHC_FN(const XYSys &sys, const XYCtl &ctl, const EPView &ep, const WorkList &wl,
                     int grid, cudaStream_t st) {
     constexpr int M = NPHC_INST_M;
-    const size_t smem = xy_track_smem_bytes(M, sizeof(RT), BLK);
+    const size_t smem = xy_smem_per_thread<M, RT>() * BLK;
     auto k = xy_track_kernel<M, RT, FFV, BLK>;
     static bool attr_set = false;   // once per process for this instantiation
     if (!attr_set) {
@@ -30,15 +30,18 @@ cudaError_t NPHC_FN(const XYSys &sys, const XYCtl &ctl, const EPView &ep, const 
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    if (grid <= 0) {   // persistent grid: every SM filled to its occupancy
-        int dev = 0, sms = 0, per = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BLK, smem);
-        if (e != cudaSuccess) return e;
-        grid = sms * (per > 0 ? per : 1);
-    }
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BLK, smem);
+    if (e != cudaSuccess) return e;
+    const int full = sms * (per > 0 ? per : 1);   // persistent grid: every SM filled
+    if (grid <= 0 || grid > full) grid = full;
+    const int cap = (int)(wl.state_threads / BLK);  // the scratch holds state for this many
+    if (grid > cap) grid = cap;
+    if (grid <= 0) return cudaErrorInvalidValue;
     k<<<grid, BLK, smem, st>>>(sys, ctl, ep, wl);
+    nphc_launch_counter(1);
     return cudaGetLastError();
 }
 
@@ -53,6 +56,7 @@ cudaError_t NPHC_CAT(launch_xy_refine_certify_m, NPHC_INST_M)(const XYSys &sys, 
     const int grid = (int)((cap + 127) / 128);
     xy_refine_certify_kernel<NPHC_INST_M><<<grid, 128, 0, st>>>(sys, tol_sol, refine_eps,
                                                                refine_iters, ep, wl);
+    nphc_launch_counter(1);
     return cudaGetLastError();
 }
 
@@ -63,6 +67,7 @@ cudaError_t NPHC_CAT(launch_xy_classify_m, NPHC_INST_M)(const XYSys &sys, const 
     if (ep.count <= 0) return cudaSuccess;
     const int grid = (int)((ep.count + 127) / 128);
     xy_classify_kernel<NPHC_INST_M><<<grid, 128, 0, st>>>(sys, ep, theta, index, energy, min_eig);
+    nphc_launch_counter(1);
     return cudaGetLastError();
 }
 #endif

@@ -12,64 +12,111 @@
 // with (a^, b^) = (a_k, b_k) / |(a_k, b_k)|, turns that row into q_k = r_gk / |(a_k, b_k)|
 // and leaves an M x M complex system for s in the gradient rows:
 //   S_kj = A_kj b^_j - B_kj a^_j,   rhs_k = r_fk - sum_j (A_kj conj(a^_j) + B_kj conj(b^_j)) q_j,
-// where A = d(f rows)/dx and B = d(f rows)/dy of H.  S is solved by Householder QR
-// (unitary, so no pivot search and no data-dependent indexing: everything stays in
-// registers of one thread).  Cost ~ (8/3) M^3 + O(M^2 + M N) instead of (8/3) (2M)^3.
+// where A = d(f rows)/dx and B = d(f rows)/dy of H.  S is solved by Householder QR:
+// unitary (no pivot search, no growth) and data-independent in its control flow.
+// Cost ~ (8/3) M^3 + O(M^2 + M N) real flops instead of (8/3) (2M)^3 for the full system.
+//
+// Memory layout (one path per thread): the M x M matrix S of each thread lives in
+// shared memory, column-major, each complex entry interleaved across the threads of
+// the block (entry (i, c) of thread t at [(c M + i) BLOCK + t]: conflict-free 64-bit
+// accesses).  Householder step k keeps its reflector in registers and streams the
+// remaining columns through registers one at a time, so the code is a short loop per
+// step instead of a fully unrolled M^3 block (which would not fit the instruction
+// cache); the right-hand sides stay in registers throughout.
 #pragma once
 
 #include "nphc_internal.cuh"
 
 // One thread's vector of 2M complex unknowns in shared memory, interleaved across the
-// threads of the block (component e of thread tid at [e * BLOCK + tid]): conflict-free.
+// threads of the block (element i of thread t at [i * BLOCK + t]).
 template <class R, int BLOCK>
-struct TVec {
-    R *p;
-    __device__ __forceinline__ cx<R> get(int i) const { return cx<R>{p[(2 * i) * BLOCK], p[(2 * i + 1) * BLOCK]}; }
-    __device__ __forceinline__ void set(int i, cx<R> v) const {
-        p[(2 * i) * BLOCK] = v.re;
-        p[(2 * i + 1) * BLOCK] = v.im;
-    }
+struct SVec {
+    cx<R> *p;
+    __device__ __forceinline__ cx<R> get(int i) const { return p[i * BLOCK]; }
+    __device__ __forceinline__ void set(int i, cx<R> v) const { p[i * BLOCK] = v; }
 };
+
+// One thread's vector in global scratch (element i at [i * stride]); stride = threads in
+// the grid, so a warp's accesses are coalesced.
+template <class R>
+struct GVec {
+    cx<R> *p;
+    int64_t stride;
+    __device__ __forceinline__ cx<R> get(int i) const { return p[i * stride]; }
+    __device__ __forceinline__ void set(int i, cx<R> v) const { p[i * stride] = v; }
+};
+
+// One thread's M x M complex matrix in shared memory, column-major.
+template <int M, class R, int BLOCK>
+struct SMat {
+    cx<R> *p;
+    __device__ __forceinline__ cx<R> get(int i, int c) const { return p[(c * M + i) * BLOCK]; }
+    __device__ __forceinline__ void set(int i, int c, cx<R> v) const { p[(c * M + i) * BLOCK] = v; }
+};
+
+// Shared memory per thread: the matrix plus two vectors (evaluation point, solve output).
+template <int M, class R>
+constexpr size_t xy_smem_per_thread() { return sizeof(cx<R>) * (size_t)(M * M + 4 * M); }
 
 __device__ __forceinline__ void compiler_fence() { asm volatile("" ::: "memory"); }
 
-// -H_t(z) for gradient row k and constraint row k, H_t = P - gamma Q.
+// -H_t rows of site k (H_t = P - gamma Q) at the point (xk, yk) with u_k, w_k given.
+template <class R>
+__device__ __forceinline__ void minus_ht_rows(cx<R> xk, cx<R> yk, cx<R> u, cx<R> w, cx<R> gam,
+                                              cx<R> &rf, cx<R> &rg) {
+    const cx<R> f = csub(cmul(yk, u), cmul(xk, w));
+    const cx<R> x2 = cmul(xk, xk), y2 = cmul(yk, yk);
+    rf = csub(cmul(gam, cx<R>{x2.re - R(1), x2.im}), f);
+    rg = csub(cmul(gam, cx<R>{y2.re - R(1), y2.im}), cx<R>{x2.re + y2.re - R(1), x2.im + y2.im});
+}
+
+// -H_t constraint row only (needs no couplings).
+template <class R>
+__device__ __forceinline__ cx<R> minus_ht_g(cx<R> xk, cx<R> yk, cx<R> gam) {
+    const cx<R> x2 = cmul(xk, xk), y2 = cmul(yk, yk);
+    return csub(cmul(gam, cx<R>{y2.re - R(1), y2.im}), cx<R>{x2.re + y2.re - R(1), x2.im + y2.im});
+}
+
+// u_k = J_{k,N} + sum_l J_kl x_l and w_k = sum_l J_kl y_l (J_kk = 0, so the sum may run over
+// every l).  k may be a runtime index (the row of J is then read with a uniform offset).
 template <int M, class R>
-__device__ __forceinline__ void xy_minus_ht(const R *__restrict__ J, const cx<R> (&x)[M],
-                                            const cx<R> (&y)[M], int k, cx<R> gam, cx<R> &u,
-                                            cx<R> &w, cx<R> &rf, cx<R> &rg) {
-    u = cx<R>{J[k * NPHC_JSTRIDE + M], R(0)};
+__device__ __forceinline__ void xy_uw(const R *__restrict__ J, const cx<R> (&x)[M],
+                                      const cx<R> (&y)[M], int k, cx<R> &u, cx<R> &w) {
+    const R *Jk = J + k * NPHC_JSTRIDE;
+    u = cx<R>{Jk[M], R(0)};
     w = cx<R>{R(0), R(0)};
 #pragma unroll
     for (int l = 0; l < M; l++) {
-        if (l == k) continue;
-        const R Jl = J[k * NPHC_JSTRIDE + l];
+        const R Jl = Jk[l];
         u.re += Jl * x[l].re;
         u.im += Jl * x[l].im;
         w.re += Jl * y[l].re;
         w.im += Jl * y[l].im;
     }
-    const cx<R> f = csub(cmul(y[k], u), cmul(x[k], w));
-    const cx<R> x2 = cmul(x[k], x[k]), y2 = cmul(y[k], y[k]);
-    const cx<R> qx = cx<R>{x2.re - R(1), x2.im}, qy = cx<R>{y2.re - R(1), y2.im};
-    const cx<R> g = cx<R>{x2.re + y2.re - R(1), x2.im + y2.im};
-    rf = csub(cmul(gam, qx), f);
-    rg = csub(cmul(gam, qy), g);
 }
 
-// Solve H_z(z, te) d = r for NR right-hand sides.
-//   NR == 1: r = -H_t (predictor: d = dz/dt), written to out1.
-//   NR == 2: r1 = the residual vector in `res` (corrector: -H), written to out1;
-//            r2 = -H_t, written to out2.
-// Outputs are written only when wr.  Returns false when the system is singular or the
-// result is not finite.
-template <int M, class R, int NR, int BLOCK>
-__device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const TVec<R, BLOCK> &pt,
-                                         double te, cx<R> gam, const TVec<R, BLOCK> &res,
-                                         const TVec<R, BLOCK> &out1, const TVec<R, BLOCK> &out2,
-                                         bool wr) {
-    const R s = (R)te;
-    const R omt = (R)(1.0 - te);
+// Frame of constraint row j: (a^, b^) and 1 / |(a_j, b_j)|.
+template <class R>
+__device__ __forceinline__ void g_frame(cx<R> xj, cx<R> yj, R s, cx<R> sg, cx<R> &ah, cx<R> &bh,
+                                        R &iv) {
+    const cx<R> a = cscale(R(2) * s, xj);
+    const cx<R> bb = cscale(R(2), cmul(sg, yj));
+    iv = rsqrt_r(cabs2(a) + cabs2(bb));
+    ah = cscale(iv, a);
+    bh = cscale(iv, bb);
+}
+
+// Solve H_z(z, t) d = r at the point in `pt`, with t given as (s, omt) = (t, 1 - t).
+//   two_rhs == false: r = -H_t (predictor: d = dz/dt), written to out1.
+//   two_rhs == true:  r1 = the residual vector in `res` (corrector: -H), written to out1;
+//                     r2 = -H_t, written to out2.
+// two_rhs must be uniform across the warp.  Outputs are written only when wr.  Returns
+// false when the system is singular or the result is not finite.
+template <int M, class R, int BLOCK, class Out2>
+__device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, R, BLOCK> &A,
+                                         const SVec<R, BLOCK> &pt, R s, R omt, cx<R> gam,
+                                         bool two_rhs, const SVec<R, BLOCK> &res,
+                                         const SVec<R, BLOCK> &out1, const Out2 &out2, bool wr) {
     const cx<R> gomt = cscale(omt, gam);
     const cx<R> sg = cx<R>{s + gomt.re, gomt.im};   // t + gamma (1 - t)
 
@@ -79,62 +126,45 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const TVec<R, 
         x[k] = pt.get(k);
         y[k] = pt.get(M + k);
     }
+    cx<R> b0[M], b1[M];
+#pragma unroll
+    for (int k = 0; k < M; k++) b0[k] = b1[k] = cx<R>{R(0), R(0)};
 
-    cx<R> A[M][M];
-    cx<R> b[NR][M];
-#pragma unroll
-    for (int r = 0; r < NR; r++)
-#pragma unroll
-        for (int k = 0; k < M; k++) b[r][k] = cx<R>{R(0), R(0)};
-
-    // ---- build the Schur system column by column
-#pragma unroll
+    // ---- build S column by column (columns j in a loop; rows unrolled)
+#pragma unroll 1
     for (int j = 0; j < M; j++) {
+        const cx<R> xj = pt.get(j), yj = pt.get(M + j);
         cx<R> u, w, htf, htg;
-        xy_minus_ht<M, R>(J, x, y, j, gam, u, w, htf, htg);
-        cx<R> rf[NR], rg[NR];
-        if constexpr (NR == 1) {
-            rf[0] = htf;
-            rg[0] = htg;
-        } else {
-            rf[0] = res.get(j);
-            rg[0] = res.get(M + j);
-            rf[1] = htf;
-            rg[1] = htg;
-        }
-        // diagonal entries of the gradient rows
-        const cx<R> Ajj = cx<R>{-s * w.re + R(2) * (gomt.re * x[j].re - gomt.im * x[j].im),
-                                -s * w.im + R(2) * (gomt.re * x[j].im + gomt.im * x[j].re)};
+        xy_uw<M, R>(J, x, y, j, u, w);
+        minus_ht_rows<R>(xj, yj, u, w, gam, htf, htg);
+        const cx<R> rf0 = two_rhs ? res.get(j) : htf;
+        const cx<R> rg0 = two_rhs ? res.get(M + j) : htg;
+        // diagonal Jacobian entries of gradient row j
+        const cx<R> Ajj = cx<R>{-s * w.re + R(2) * (gomt.re * xj.re - gomt.im * xj.im),
+                                -s * w.im + R(2) * (gomt.re * xj.im + gomt.im * xj.re)};
         const cx<R> Bjj = cscale(s, u);
-        // frame of constraint row j
-        const cx<R> a = cscale(R(2) * s, x[j]);
-        const cx<R> bb = cscale(R(2), cmul(sg, y[j]));
-        const R iv = rsqrt_r(cabs2(a) + cabs2(bb));
-        const cx<R> ah = cscale(iv, a), bh = cscale(iv, bb);
+        cx<R> ah, bh;
+        R iv;
+        g_frame<R>(xj, yj, s, sg, ah, bh, iv);
+        const cx<R> q0 = cscale(iv, rg0), q1 = cscale(iv, htg);
+        const cx<R> px0 = cmulc(ah, q0), py0 = cmulc(bh, q0);
+        const cx<R> px1 = cmulc(ah, q1), py1 = cmulc(bh, q1);
+        // the diagonal's own contributions, added to row j below
+        const cx<R> d0 = csub(rf0, cadd(cmul(Ajj, px0), cmul(Bjj, py0)));
+        const cx<R> d1 = csub(htf, cadd(cmul(Ajj, px1), cmul(Bjj, py1)));
 #pragma unroll
         for (int k = 0; k < M; k++) {
+            // off-diagonal entries; J_jj = 0 makes the k == j term vanish
+            const R sJ = s * J[k * NPHC_JSTRIDE + j];
+            A.set(k, j, cscale(sJ, cadd(cmul(y[k], bh), cmul(x[k], ah))));
+            b0[k] = csub(b0[k], cscale(sJ, csub(cmul(y[k], px0), cmul(x[k], py0))));
+            if (two_rhs) b1[k] = csub(b1[k], cscale(sJ, csub(cmul(y[k], px1), cmul(x[k], py1))));
             if (k == j) {
-                A[k][j] = csub(cmul(Ajj, bh), cmul(Bjj, ah));
-            } else {
-                const R sJ = s * J[k * NPHC_JSTRIDE + j];
-                A[k][j] = cscale(sJ, cadd(cmul(y[k], bh), cmul(x[k], ah)));
+                b0[k] = cadd(b0[k], d0);
+                b1[k] = cadd(b1[k], d1);
             }
         }
-#pragma unroll
-        for (int r = 0; r < NR; r++) {
-            const cx<R> q = cscale(iv, rg[r]);
-            const cx<R> px = cmulc(ah, q), py = cmulc(bh, q);
-#pragma unroll
-            for (int k = 0; k < M; k++) {
-                if (k == j) {
-                    b[r][k] = csub(b[r][k], cadd(cmul(Ajj, px), cmul(Bjj, py)));
-                } else {
-                    const R sJ = s * J[k * NPHC_JSTRIDE + j];
-                    b[r][k] = csub(b[r][k], cscale(sJ, csub(cmul(y[k], px), cmul(x[k], py))));
-                }
-            }
-            b[r][j] = cadd(b[r][j], rf[r]);
-        }
+        A.set(j, j, csub(cmul(Ajj, bh), cmul(Bjj, ah)));
     }
 
     // ---- Householder QR: Q^H S = R (real diagonal), applied to the right-hand sides
@@ -142,10 +172,14 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const TVec<R, 
     bool ok = true;
 #pragma unroll
     for (int k = 0; k < M; k++) {
-        const cx<R> al = A[k][k];
+        cx<R> v[M];
         R xn2 = R(0);
 #pragma unroll
-        for (int i = k + 1; i < M; i++) xn2 += cabs2(A[i][k]);
+        for (int i = k + 1; i < M; i++) {
+            v[i] = A.get(i, k);
+            xn2 += cabs2(v[i]);
+        }
+        const cx<R> al = A.get(k, k);
         const R an = sqrt_r(cabs2(al) + xn2);
         ok = ok && (an > R(0));
         const R beta = al.re >= R(0) ? -an : an;
@@ -153,98 +187,107 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const TVec<R, 
         const cx<R> tauc = cx<R>{(beta - al.re) * ib, al.im * ib};   // conj(tau)
         const cx<R> sc = crecip(cx<R>{al.re - beta, al.im});
 #pragma unroll
-        for (int i = k + 1; i < M; i++) A[i][k] = cmul(A[i][k], sc);  // v_i (v_k = 1)
+        for (int i = k + 1; i < M; i++) v[i] = cmul(v[i], sc);   // reflector, v_k = 1
         dg[k] = beta;
+        // stream the trailing columns through registers
+#pragma unroll 1
+        for (int c = k + 1; c < M; c++) {
+            cx<R> col[M];
+            cx<R> wv = A.get(k, c);
+#pragma unroll
+            for (int i = k + 1; i < M; i++) {
+                col[i] = A.get(i, c);
+                wv = cadd(wv, cmulc(v[i], col[i]));
+            }
+            wv = cmul(tauc, wv);
+            A.set(k, c, csub(A.get(k, c), wv));
+#pragma unroll
+            for (int i = k + 1; i < M; i++) A.set(i, c, csub(col[i], cmul(v[i], wv)));
+        }
+        {
+            cx<R> wv = b0[k];
+#pragma unroll
+            for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(v[i], b0[i]));
+            wv = cmul(tauc, wv);
+            b0[k] = csub(b0[k], wv);
+#pragma unroll
+            for (int i = k + 1; i < M; i++) b0[i] = csub(b0[i], cmul(v[i], wv));
+        }
+        if (two_rhs) {
+            cx<R> wv = b1[k];
+#pragma unroll
+            for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(v[i], b1[i]));
+            wv = cmul(tauc, wv);
+            b1[k] = csub(b1[k], wv);
+#pragma unroll
+            for (int i = k + 1; i < M; i++) b1[i] = csub(b1[i], cmul(v[i], wv));
+        }
+    }
+    // ---- back substitution R s = Q^H b (in place)
+#pragma unroll
+    for (int k = M - 1; k >= 0; k--) {
+        cx<R> a0 = b0[k], a1 = b1[k];
 #pragma unroll
         for (int c = k + 1; c < M; c++) {
-            cx<R> wv = A[k][c];
-#pragma unroll
-            for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(A[i][k], A[i][c]));
-            wv = cmul(tauc, wv);
-            A[k][c] = csub(A[k][c], wv);
-#pragma unroll
-            for (int i = k + 1; i < M; i++) A[i][c] = csub(A[i][c], cmul(A[i][k], wv));
+            const cx<R> Rkc = A.get(k, c);
+            a0 = csub(a0, cmul(Rkc, b0[c]));
+            a1 = csub(a1, cmul(Rkc, b1[c]));
         }
-#pragma unroll
-        for (int r = 0; r < NR; r++) {
-            cx<R> wv = b[r][k];
-#pragma unroll
-            for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(A[i][k], b[r][i]));
-            wv = cmul(tauc, wv);
-            b[r][k] = csub(b[r][k], wv);
-#pragma unroll
-            for (int i = k + 1; i < M; i++) b[r][i] = csub(b[r][i], cmul(A[i][k], wv));
-        }
-    }
-    // back substitution R s = Q^H b (in place in b)
-#pragma unroll
-    for (int r = 0; r < NR; r++) {
-#pragma unroll
-        for (int k = M - 1; k >= 0; k--) {
-            cx<R> acc = b[r][k];
-#pragma unroll
-            for (int c = k + 1; c < M; c++) acc = csub(acc, cmul(A[k][c], b[r][c]));
-            b[r][k] = cscale(recip_r(dg[k]), acc);
-        }
+        const R ir = recip_r(dg[k]);
+        b0[k] = cscale(ir, a0);
+        b1[k] = cscale(ir, a1);
     }
 
-    // ---- back to (dx, dy): reload the point rather than keep it live through the QR
-    compiler_fence();
+    // ---- back to (dx, dy)
     R chk = R(0);
 #pragma unroll
     for (int j = 0; j < M; j++) {
         const cx<R> xj = pt.get(j), yj = pt.get(M + j);
-        const cx<R> a = cscale(R(2) * s, xj);
-        const cx<R> bb = cscale(R(2), cmul(sg, yj));
-        const R iv = rsqrt_r(cabs2(a) + cabs2(bb));
-        const cx<R> ah = cscale(iv, a), bh = cscale(iv, bb);
-        const cx<R> y2 = cmul(yj, yj), x2 = cmul(xj, xj);
-        const cx<R> htg = csub(cmul(gam, cx<R>{y2.re - R(1), y2.im}),
-                               cx<R>{x2.re + y2.re - R(1), x2.im + y2.im});
-#pragma unroll
-        for (int r = 0; r < NR; r++) {
-            const cx<R> rg = (NR == 2 && r == 0) ? res.get(M + j) : htg;
-            const cx<R> q = cscale(iv, rg);
-            const cx<R> dx = cadd(cmulc(ah, q), cmul(bh, b[r][j]));
-            const cx<R> dy = csub(cmulc(bh, q), cmul(ah, b[r][j]));
-            chk += cabs2(dx) + cabs2(dy);
+        cx<R> ah, bh;
+        R iv;
+        g_frame<R>(xj, yj, s, sg, ah, bh, iv);
+        const cx<R> htg = minus_ht_g<R>(xj, yj, gam);
+        const cx<R> q0 = cscale(iv, two_rhs ? res.get(M + j) : htg);
+        const cx<R> dx0 = cadd(cmulc(ah, q0), cmul(bh, b0[j]));
+        const cx<R> dy0 = csub(cmulc(bh, q0), cmul(ah, b0[j]));
+        chk += cabs2(dx0) + cabs2(dy0);
+        if (two_rhs) {
+            const cx<R> q1 = cscale(iv, htg);
+            const cx<R> dx1 = cadd(cmulc(ah, q1), cmul(bh, b1[j]));
+            const cx<R> dy1 = csub(cmulc(bh, q1), cmul(ah, b1[j]));
+            chk += cabs2(dx1) + cabs2(dy1);
             if (wr) {
-                const TVec<R, BLOCK> &o = (r == 0) ? out1 : out2;
-                o.set(j, dx);
-                o.set(M + j, dy);
+                out2.set(j, dx1);
+                out2.set(M + j, dy1);
             }
+        }
+        if (wr) {
+            out1.set(j, dx0);
+            out1.set(M + j, dy0);
         }
     }
     return ok && finite_r(chk);
 }
 
-// -H(z, te) in the working precision R (no compensation), written to out when wr.
+// -H(z, t) in the working precision R (no compensation), written to out when wr.
 template <int M, class R, int BLOCK>
-__device__ __forceinline__ void xy_residual_plain(const R *__restrict__ J, const TVec<R, BLOCK> &pt,
-                                                  double te, cx<R> gam,
-                                                  const TVec<R, BLOCK> &out, bool wr) {
-    const R s = (R)te;
-    const cx<R> gomt = cscale((R)(1.0 - te), gam);
+__device__ __forceinline__ void xy_residual_plain(const R *__restrict__ J, const SVec<R, BLOCK> &pt,
+                                                  R s, R omt, cx<R> gam,
+                                                  const SVec<R, BLOCK> &out, bool wr) {
+    const cx<R> gomt = cscale(omt, gam);
     cx<R> x[M], y[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
         x[k] = pt.get(k);
         y[k] = pt.get(M + k);
     }
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < M; k++) {
-        cx<R> u = cx<R>{J[k * NPHC_JSTRIDE + M], R(0)}, w = cx<R>{R(0), R(0)};
-#pragma unroll
-        for (int l = 0; l < M; l++) {
-            if (l == k) continue;
-            const R Jl = J[k * NPHC_JSTRIDE + l];
-            u.re += Jl * x[l].re;
-            u.im += Jl * x[l].im;
-            w.re += Jl * y[l].re;
-            w.im += Jl * y[l].im;
-        }
-        const cx<R> f = csub(cmul(y[k], u), cmul(x[k], w));
-        const cx<R> x2 = cmul(x[k], x[k]), y2 = cmul(y[k], y[k]);
+        const cx<R> xk = pt.get(k), yk = pt.get(M + k);
+        cx<R> u, w;
+        xy_uw<M, R>(J, x, y, k, u, w);
+        const cx<R> f = csub(cmul(yk, u), cmul(xk, w));
+        const cx<R> x2 = cmul(xk, xk), y2 = cmul(yk, yk);
         const cx<R> hf = cadd(cmul(gomt, cx<R>{x2.re - R(1), x2.im}), cscale(s, f));
         const cx<R> hg = cadd(cmul(gomt, cx<R>{y2.re - R(1), y2.im}),
                               cscale(s, cx<R>{x2.re + y2.re - R(1), x2.im + y2.im}));
@@ -255,18 +298,16 @@ __device__ __forceinline__ void xy_residual_plain(const R *__restrict__ J, const
     }
 }
 
-// -H(z, te) for an FP32 point, evaluated with compensated (float-float) sums and exact
+// -H(z, t) for an FP32 point, evaluated with compensated (float-float) sums and exact
 // products, then rounded once: the error is ~2^-48 of the terms instead of 2^-24, so a
 // Newton corrector driven by it converges to the FP32 rounding of the path point even
 // when H_z is far from well conditioned (mixed-precision iterative refinement).  The
 // coefficients J, gamma (1-t) and t enter as their FP32 values.
 template <int M, int BLOCK>
 __device__ __forceinline__ void xy_residual_ff(const float *__restrict__ J,
-                                               const TVec<float, BLOCK> &pt, double te,
-                                               cx<float> gam, const TVec<float, BLOCK> &out,
+                                               const SVec<float, BLOCK> &pt, float s, float omt,
+                                               cx<float> gam, const SVec<float, BLOCK> &out,
                                                bool wr) {
-    const float s = (float)te;
-    const float omt = (float)(1.0 - te);
     const cx<float> gomt = cx<float>{__fmul_rn(omt, gam.re), __fmul_rn(omt, gam.im)};
     cx<float> x[M], y[M];
 #pragma unroll
@@ -274,13 +315,14 @@ __device__ __forceinline__ void xy_residual_ff(const float *__restrict__ J,
         x[k] = pt.get(k);
         y[k] = pt.get(M + k);
     }
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < M; k++) {
-        ff ure = {J[k * NPHC_JSTRIDE + M], 0.f}, uim = {0.f, 0.f}, wre = {0.f, 0.f}, wim = {0.f, 0.f};
+        const cx<float> xk = pt.get(k), yk = pt.get(M + k);
+        const float *Jk = J + k * NPHC_JSTRIDE;
+        ff ure = {Jk[M], 0.f}, uim = {0.f, 0.f}, wre = {0.f, 0.f}, wim = {0.f, 0.f};
 #pragma unroll
-        for (int l = 0; l < M; l++) {
-            if (l == k) continue;
-            const float Jl = J[k * NPHC_JSTRIDE + l];
+        for (int l = 0; l < M; l++) {   // J_kk = 0 adds exact zeros
+            const float Jl = Jk[l];
             ff_acc(ure, Jl, x[l].re);
             ff_acc(uim, Jl, x[l].im);
             ff_acc(wre, Jl, y[l].re);
@@ -288,22 +330,22 @@ __device__ __forceinline__ void xy_residual_ff(const float *__restrict__ J,
         }
         // f = y u - x w
         ff fre = {0.f, 0.f}, fim = {0.f, 0.f};
-        ff_acc_ff(fre, y[k].re, ure);
-        ff_acc_ff(fre, -y[k].im, uim);
-        ff_acc_ff(fre, -x[k].re, wre);
-        ff_acc_ff(fre, x[k].im, wim);
-        ff_acc_ff(fim, y[k].re, uim);
-        ff_acc_ff(fim, y[k].im, ure);
-        ff_acc_ff(fim, -x[k].re, wim);
-        ff_acc_ff(fim, -x[k].im, wre);
-        // x^2 - 1, y^2 - 1 and c^2 + s^2 - 1, exactly as float-float
+        ff_acc_ff(fre, yk.re, ure);
+        ff_acc_ff(fre, -yk.im, uim);
+        ff_acc_ff(fre, -xk.re, wre);
+        ff_acc_ff(fre, xk.im, wim);
+        ff_acc_ff(fim, yk.re, uim);
+        ff_acc_ff(fim, yk.im, ure);
+        ff_acc_ff(fim, -xk.re, wim);
+        ff_acc_ff(fim, -xk.im, wre);
+        // x^2 - 1 and y^2 - 1 exactly as float-float
         ff qxr = {-1.f, 0.f}, qxi = {0.f, 0.f}, qyr = {-1.f, 0.f}, qyi = {0.f, 0.f};
-        ff_acc(qxr, x[k].re, x[k].re);
-        ff_acc(qxr, -x[k].im, x[k].im);
-        ff_acc(qxi, 2.f * x[k].re, x[k].im);
-        ff_acc(qyr, y[k].re, y[k].re);
-        ff_acc(qyr, -y[k].im, y[k].im);
-        ff_acc(qyi, 2.f * y[k].re, y[k].im);
+        ff_acc(qxr, xk.re, xk.re);
+        ff_acc(qxr, -xk.im, xk.im);
+        ff_acc(qxi, 2.f * xk.re, xk.im);
+        ff_acc(qyr, yk.re, yk.re);
+        ff_acc(qyr, -yk.im, yk.im);
+        ff_acc(qyi, 2.f * yk.re, yk.im);
         // H_f = gomt (x^2 - 1) + s f ;  H_g = gomt (y^2 - 1) + s (x^2 + y^2 - 1)
         ff hfr = {0.f, 0.f}, hfi = {0.f, 0.f}, hgr = {0.f, 0.f}, hgi = {0.f, 0.f};
         ff_acc_ff(hfr, gomt.re, qxr);

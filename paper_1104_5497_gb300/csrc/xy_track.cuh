@@ -5,12 +5,13 @@
 //
 // Layout: one path per thread; a persistent grid pulls paths from a device work
 // counter (warp-aggregated atomics) until the list is drained.  The warp runs its 32
-// paths in lockstep through the same phases -- three RK4 stage solves, then up to
-// max_newton corrector solves -- so the heavy solve is never divergent; lanes whose
-// path has finished take the next one at the step boundary.  Per-path state (point,
-// derivative, RK4 accumulator, evaluation point, solve output: five vectors of 2M
-// complex) lives in shared memory, interleaved by thread; the M x M Schur matrix of
-// each solve lives in registers (xy_solve.cuh).
+// paths in lockstep through the same phases of a step -- three RK4 stage solves, then
+// up to max_newton corrector solves -- in a loop with a single call site of the solve,
+// so the heavy solve is never divergent and its unrolled code is instantiated once
+// (instruction-cache resident); lanes whose path has finished take the next one at
+// the step boundary.  The M x M Schur matrix, the evaluation point and the solve
+// output of each path live in shared memory (xy_solve.cuh); the accepted point, its
+// derivative and the RK4 sum live in a global scratch (coalesced, L2-resident).
 //
 // Predictor: classical RK4 on dz/dt = -H_z^-1 H_t.  The derivative at the start of a
 // step is taken from the previous step's last corrector solve (second right-hand
@@ -25,8 +26,12 @@
 // FP32 pass (ctl.handoff = 1): a path whose ||z||_inf exceeds rdiv_soft is declared
 // diverged when its growth exponent d ln||z|| / d ln(1/(1-t)) over the last step
 // exceeds rho_div (paths at infinity grow like (1-t)^-rho); otherwise, and on a step
-// size underflow, ten consecutive rejects or the step budget, it is handed to FP64
-// (NPHC_PATH_HANDOFF) with its (z, t, h).
+// size underflow, ten consecutive rejects, a crawl near t = 1 (1 - t failing to halve
+// within CRAWL_STEPS accepted steps) or its own (smaller) attempt budget, it is handed
+// to FP64 (NPHC_PATH_HANDOFF) with its (z, t, h).  In FP64 a crawl ends the path
+// (NPHC_PATH_MIN_STEP).  The FP32 bound on the first correction (trust_fp32) keeps its
+// accepted steps no longer than the FP64 tolerance allows, so that it does not step
+// across a sharp turn of the path onto a neighbouring one.
 #pragma once
 
 #include "xy_solve.cuh"
@@ -42,18 +47,21 @@ struct JSel<double> {
     static __device__ __forceinline__ const double *get(const XYSys &S) { return S.Jd; }
 };
 
-template <int M, class R, int BLOCK>
-__device__ __forceinline__ R tvec_norm2(const TVec<R, BLOCK> &v) {
+#define CRAWL_ZONE 1e-3   // the crawl test applies once 1 - t < CRAWL_ZONE
+#define CRAWL_STEPS 32
+
+template <int M, class R, class V>
+__device__ __forceinline__ R vnorm2(const V &v) {
     R s = R(0);
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < 2 * M; i++) s += cabs2(v.get(i));
     return sqrt_r(s);
 }
 
-template <int M, class R, int BLOCK>
-__device__ __forceinline__ R tvec_norminf(const TVec<R, BLOCK> &v) {
+template <int M, class R, class V>
+__device__ __forceinline__ R vnorminf(const V &v) {
     R s = R(0);
-#pragma unroll
+#pragma unroll 1
     for (int i = 0; i < 2 * M; i++) s = fmax(s, sqrt_r(cabs2(v.get(i))));
     return s;
 }
@@ -62,22 +70,27 @@ template <int M, class R, bool FF, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     xy_track_kernel(const __grid_constant__ XYSys S, const __grid_constant__ XYCtl C,
                     const EPView ep, const WorkList wl) {
-    constexpr int NV = 4 * M;   // reals per vector
     extern __shared__ __align__(16) unsigned char smraw[];
-    R *sm = reinterpret_cast<R *>(smraw);
+    cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
     const int tid = threadIdx.x, lane = tid & 31;
-    const TVec<R, BLOCK> Z0{sm + 0 * NV * BLOCK + tid};   // accepted point
-    const TVec<R, BLOCK> K1{sm + 1 * NV * BLOCK + tid};   // dz/dt at Z0
-    const TVec<R, BLOCK> AC{sm + 2 * NV * BLOCK + tid};   // RK4 sum; next K1 during correction
-    const TVec<R, BLOCK> ZC{sm + 3 * NV * BLOCK + tid};   // evaluation point / Newton iterate
-    const TVec<R, BLOCK> W1{sm + 4 * NV * BLOCK + tid};   // solve output / residual
+    const SMat<M, R, BLOCK> A{sm + tid};
+    const SVec<R, BLOCK> ZC{sm + M * M * BLOCK + tid};           // evaluation point / iterate
+    const SVec<R, BLOCK> W1{sm + (M * M + 2 * M) * BLOCK + tid}; // solve output / residual
+    const int64_t gtid = (int64_t)blockIdx.x * BLOCK + tid;
+    const int64_t nth = wl.state_threads;
+    cx<R> *st = reinterpret_cast<cx<R> *>(wl.state);
+    const GVec<R> Z0{st + (0 * 2 * M) * nth + gtid, nth};       // accepted point
+    const GVec<R> K1{st + (1 * 2 * M) * nth + gtid, nth};       // dz/dt at Z0
+    const GVec<R> AC{st + (2 * 2 * M) * nth + gtid, nth};       // RK4 sum; next K1 in correction
     const R *J = JSel<R>::get(S);
     const cx<R> gam = cx<R>{(R)S.gre, (R)S.gim};
     const int64_t total = worklist_size(wl, ep.count);
     const int64_t cnt = ep.count;
 
-    int64_t e = -1;   // entry index; -1 idle, -2 list drained
+    int64_t e = (C.sparse && lane != 0) ? -2 : -1;   // entry index; -1 idle, -2 drained
     double t = 0.0, h = 0.0, hacc = 0.0, tprev = 0.0;
+    double tmark = 0.0;   // 1 - t recorded every CRAWL_STEPS accepted steps near t = 1
+    int since = 0;
     R zprev = R(1);
     int status = 0, run = 0, rejects = 0, attempts = 0, steps = 0, solves = 0, newton = 0;
     bool need_k1 = false;
@@ -95,17 +108,19 @@ __global__ void __launch_bounds__(BLOCK)
                 const int64_t i = (int64_t)base + __popc(need & ((1u << lane) - 1u));
                 if (i < total) {
                     e = worklist_entry(wl, i);
-                    const int64_t p = ep.path[e];
                     status = NPHC_PATH_RUNNING;
                     run = 0;
                     rejects = 0;
                     attempts = 0;
                     if (C.resume) {
-#pragma unroll
+#pragma unroll 1
                         for (int k = 0; k < 2 * M; k++)
                             Z0.set(k, cx<R>{(R)ep.z_re[k * cnt + e], (R)ep.z_im[k * cnt + e]});
                         t = ep.t[e];
-                        h = fmax(ep.h[e], C.hmin * 4.0);
+                        // restart with a step on the scale of 1 - t: the FP32 pass may have
+                        // been crawling with a far smaller one
+                        h = fmin(fmax(ep.h[e], 0.125 * (1.0 - t)), C.hmax);
+                        h = fmax(h, C.hmin * 4.0);
                         steps = ep.steps[e];
                         solves = ep.solves[e];
                         newton = ep.newton[e];
@@ -113,22 +128,25 @@ __global__ void __launch_bounds__(BLOCK)
                     } else {
                         // start point and its derivative: at t = 0, H_z = 2 gamma diag(z)
                         // and H_t = P(z), so dz_i/dt = -P_i(z) / (2 gamma z_i)
+                        const int64_t p = ep.path[e];
                         cx<R> x[M], y[M];
 #pragma unroll
                         for (int k = 0; k < M; k++) {
                             x[k] = cx<R>{((p >> k) & 1) ? R(-1) : R(1), R(0)};
                             y[k] = cx<R>{((p >> (M + k)) & 1) ? R(-1) : R(1), R(0)};
-                            Z0.set(k, x[k]);
-                            Z0.set(M + k, y[k]);
                         }
                         const cx<R> ig = crecip(gam);
-#pragma unroll
+#pragma unroll 1
                         for (int k = 0; k < M; k++) {
+                            const cx<R> xk = cx<R>{((p >> k) & 1) ? R(-1) : R(1), R(0)};
+                            const cx<R> yk = cx<R>{((p >> (M + k)) & 1) ? R(-1) : R(1), R(0)};
                             cx<R> u, w, rf, rg;
-                            xy_minus_ht<M, R>(J, x, y, k, gam, u, w, rf, rg);
-                            // rf = -H_t row = -P_k (Q_k = 0 at a start point)
-                            K1.set(k, cscale(R(0.5) * x[k].re, cmul(ig, rf)));
-                            K1.set(M + k, cscale(R(0.5) * y[k].re, cmul(ig, rg)));
+                            xy_uw<M, R>(J, x, y, k, u, w);
+                            minus_ht_rows<R>(xk, yk, u, w, gam, rf, rg);
+                            Z0.set(k, xk);
+                            Z0.set(M + k, yk);
+                            K1.set(k, cscale(R(0.5) * xk.re, cmul(ig, rf)));
+                            K1.set(M + k, cscale(R(0.5) * yk.re, cmul(ig, rg)));
                         }
                         t = 0.0;
                         h = C.h0;
@@ -139,7 +157,9 @@ __global__ void __launch_bounds__(BLOCK)
                     }
                     hacc = h;
                     tprev = t;
-                    zprev = tvec_norminf<M, R, BLOCK>(Z0);
+                    tmark = 1.0 - t;
+                    since = 0;
+                    zprev = vnorminf<M, R>(Z0);
                 } else {
                     e = -2;
                 }
@@ -148,99 +168,115 @@ __global__ void __launch_bounds__(BLOCK)
         if (__all_sync(0xffffffffu, e < 0)) break;
         const bool act = (e >= 0);
 
-        // ---- resumed paths need dz/dt at their current point
-        if (__any_sync(0xffffffffu, act && need_k1)) {
-            const bool w = act && need_k1;
-            if (w) {
-#pragma unroll
-                for (int k = 0; k < 2 * M; k++) ZC.set(k, Z0.get(k));
-            }
-            const bool okk = xy_solve<M, R, 1, BLOCK>(J, ZC, t, gam, W1, W1, W1, w);
-            if (w) {
-                solves++;
-#pragma unroll
-                for (int k = 0; k < 2 * M; k++) K1.set(k, W1.get(k));
-                need_k1 = false;
-                if (!okk) status = C.handoff ? NPHC_PATH_HANDOFF : NPHC_PATH_NONFINITE;
-            }
-        }
-        const bool go = act && status == NPHC_PATH_RUNNING;
-
-        // ---- RK4 predictor: stages 2..4 (stage 1 is K1)
+        // ---- one step: phase 0 = dz/dt at a resumed point (only when some lane needs
+        // it), phases 1..3 = RK4 stages 2..4, phases 4.. = Newton corrector iterations
         double hh = h, t1 = t + h;
         if (t1 >= 1.0) {
             t1 = 1.0;
             hh = 1.0 - t;
         }
         const R hr = (R)hh;
-        bool okp = true;
-        if (go) {
-#pragma unroll
-            for (int k = 0; k < 2 * M; k++) ZC.set(k, cadd(Z0.get(k), cscale(R(0.5) * hr, K1.get(k))));
-        }
-        okp &= xy_solve<M, R, 1, BLOCK>(J, ZC, t + 0.5 * hh, gam, W1, W1, W1, go);
-        if (go) {
-#pragma unroll
-            for (int k = 0; k < 2 * M; k++) {
-                const cx<R> d = W1.get(k);
-                AC.set(k, cadd(K1.get(k), cscale(R(2), d)));
-                ZC.set(k, cadd(Z0.get(k), cscale(R(0.5) * hr, d)));
+        bool go = act && !need_k1;
+        bool conv = false, bad = false;
+        R zpn = R(0);
+        const int ph0 = __any_sync(0xffffffffu, act && need_k1) ? 0 : 1;
+        const int nph = 4 + C.max_newton;
+#pragma unroll 1
+        for (int ph = ph0; ph < nph; ph++) {
+            const bool corr = ph >= 4;   // warp-uniform
+            if (corr && __all_sync(0xffffffffu, !go || conv || bad)) break;
+            // participating lanes and the evaluation time of this phase
+            bool w;
+            double te;
+            if (ph == 0) {
+                w = act && need_k1;
+                te = t;
+            } else if (!corr) {
+                w = go;
+                te = (ph == 3) ? t1 : t + 0.5 * hh;
+            } else {
+                w = go && !conv && !bad;
+                te = t1;
             }
-        }
-        okp &= xy_solve<M, R, 1, BLOCK>(J, ZC, t + 0.5 * hh, gam, W1, W1, W1, go);
-        if (go) {
-#pragma unroll
-            for (int k = 0; k < 2 * M; k++) {
-                const cx<R> d = W1.get(k);
-                AC.set(k, cadd(AC.get(k), cscale(R(2), d)));
-                ZC.set(k, cadd(Z0.get(k), cscale(hr, d)));
+            if (w && ph < 4) {
+                // evaluation point of the phase: z0, z0 + h/2 k1, z0 + h/2 k2, z0 + h k3
+                const R c = ph == 3 ? hr : R(0.5) * hr;
+#pragma unroll 1
+                for (int k = 0; k < 2 * M; k++) {
+                    if (ph == 0) {
+                        ZC.set(k, Z0.get(k));
+                    } else {
+                        const cx<R> d = ph == 1 ? K1.get(k) : W1.get(k);
+                        ZC.set(k, cadd(Z0.get(k), cscale(c, d)));
+                    }
+                }
             }
-        }
-        okp &= xy_solve<M, R, 1, BLOCK>(J, ZC, t1, gam, W1, W1, W1, go);
-        if (go) {
-            solves += 3;
-#pragma unroll
-            for (int k = 0; k < 2 * M; k++) {
-                const cx<R> acc = cadd(AC.get(k), W1.get(k));
-                ZC.set(k, cadd(Z0.get(k), cscale(hr / R(6), acc)));
+            const R tr = (R)te, omt = (R)(1.0 - te);
+            if (corr) {
+                if constexpr (FF)
+                    xy_residual_ff<M, BLOCK>(J, ZC, tr, omt, gam, W1, w);
+                else
+                    xy_residual_plain<M, R, BLOCK>(J, ZC, tr, omt, gam, W1, w);
             }
-        }
-
-        // ---- Newton corrector at t1
-        bool conv = false, bad = !go || !okp;
-        const R zpn = go ? tvec_norm2<M, R, BLOCK>(ZC) : R(0);
-        for (int it = 0; it < C.max_newton; it++) {
-            if (__all_sync(0xffffffffu, conv || bad)) break;
-            const bool w = !conv && !bad;
-            if constexpr (FF)
-                xy_residual_ff<M, BLOCK>(J, ZC, t1, gam, W1, w);
-            else
-                xy_residual_plain<M, R, BLOCK>(J, ZC, t1, gam, W1, w);
-            const bool oks = xy_solve<M, R, 2, BLOCK>(J, ZC, t1, gam, W1, W1, AC, w);
-            if (w) {
-                solves++;
+            const bool oks = xy_solve<M, R, BLOCK>(J, A, ZC, tr, omt, gam, corr, W1, W1, AC, w);
+            if (!w) continue;
+            solves++;
+            if (ph == 0) {
+#pragma unroll 1
+                for (int k = 0; k < 2 * M; k++) K1.set(k, W1.get(k));
+                need_k1 = false;
+                if (!oks) status = C.handoff ? NPHC_PATH_HANDOFF : NPHC_PATH_NONFINITE;
+            } else if (!corr) {
+                bad = bad || !oks;
+                if (ph == 1) {
+#pragma unroll 1
+                    for (int k = 0; k < 2 * M; k++) AC.set(k, cadd(K1.get(k), cscale(R(2), W1.get(k))));
+                } else if (ph == 2) {
+#pragma unroll 1
+                    for (int k = 0; k < 2 * M; k++) AC.set(k, cadd(AC.get(k), cscale(R(2), W1.get(k))));
+                } else {
+                    // predicted point z0 + h/6 (k1 + 2 k2 + 2 k3 + k4)
+                    R zz = R(0);
+#pragma unroll 1
+                    for (int k = 0; k < 2 * M; k++) {
+                        const cx<R> zp = cadd(Z0.get(k), cscale(hr / R(6), cadd(AC.get(k), W1.get(k))));
+                        ZC.set(k, zp);
+                        zz += cabs2(zp);
+                    }
+                    zpn = sqrt_r(zz);
+                }
+            } else {
                 newton++;
-                const R dn = tvec_norm2<M, R, BLOCK>(W1);
+                const R dn = vnorm2<M, R>(W1);
                 if (!oks || !finite_r(dn)) {
                     bad = true;
-                } else if (it == 0 && dn > (R)C.trust * (R(1) + zpn)) {
+                } else if (ph == 4 && dn > (R)C.trust * (R(1) + zpn)) {
                     bad = true;
                 } else {
-#pragma unroll
-                    for (int k = 0; k < 2 * M; k++) ZC.set(k, cadd(ZC.get(k), W1.get(k)));
-                    if (dn <= (R)C.eps * (R(1) + tvec_norm2<M, R, BLOCK>(ZC))) conv = true;
+                    R zz = R(0);
+#pragma unroll 1
+                    for (int k = 0; k < 2 * M; k++) {
+                        const cx<R> zn = cadd(ZC.get(k), W1.get(k));
+                        ZC.set(k, zn);
+                        zz += cabs2(zn);
+                    }
+                    if (dn <= (R)C.eps * (R(1) + sqrt_r(zz))) conv = true;
                 }
             }
         }
+        go = go && status == NPHC_PATH_RUNNING;
 
         // ---- accept or reject
         if (go) {
             attempts++;
             if (conv) {
-#pragma unroll
+                R zi = R(0);
+#pragma unroll 1
                 for (int k = 0; k < 2 * M; k++) {
-                    Z0.set(k, ZC.get(k));
+                    const cx<R> v = ZC.get(k);
+                    Z0.set(k, v);
                     K1.set(k, AC.get(k));
+                    zi = fmax(zi, sqrt_r(cabs2(v)));
                 }
                 t = t1;
                 steps++;
@@ -250,7 +286,6 @@ __global__ void __launch_bounds__(BLOCK)
                     run = 0;
                     h = fmin(2.0 * h, C.hmax);
                 }
-                const R zi = tvec_norminf<M, R, BLOCK>(Z0);
                 if (t >= 1.0) {
                     status = NPHC_PATH_REACHED;
                 } else if ((double)zi > C.rdiv) {
@@ -263,6 +298,20 @@ __global__ void __launch_bounds__(BLOCK)
                 }
                 zprev = zi;
                 tprev = t;
+                // crawl test near t = 1: 1 - t must at least halve every CRAWL_STEPS
+                // accepted steps (paths to nonsingular endpoints finish in a few steps;
+                // a crawl means a singular endpoint, infinity, or precision exhausted)
+                if (status == NPHC_PATH_RUNNING && 1.0 - t < CRAWL_ZONE) {
+                    if (++since >= CRAWL_STEPS) {
+                        if (1.0 - t > 0.5 * tmark)
+                            status = C.handoff ? NPHC_PATH_HANDOFF : NPHC_PATH_MIN_STEP;
+                        tmark = 1.0 - t;
+                        since = 0;
+                    }
+                } else {
+                    tmark = 1.0 - t;
+                    since = 0;
+                }
             } else {
                 run = 0;
                 rejects++;
@@ -276,7 +325,7 @@ __global__ void __launch_bounds__(BLOCK)
                 status = C.handoff ? NPHC_PATH_HANDOFF : NPHC_PATH_STEP_BUDGET;
         }
         if (act && status != NPHC_PATH_RUNNING) {
-#pragma unroll
+#pragma unroll 1
             for (int k = 0; k < 2 * M; k++) {
                 const cx<R> v = Z0.get(k);
                 ep.z_re[k * cnt + e] = (double)v.re;

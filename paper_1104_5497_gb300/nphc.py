@@ -23,8 +23,8 @@ PATH_RUNNING, PATH_REACHED, PATH_DIVERGED, PATH_MIN_STEP, PATH_STEP_BUDGET, PATH
 END_NONE, END_SINGULAR, END_REAL, END_NONREAL, END_UNDECIDED, END_DUPLICATE, END_FAILED = range(7)
 
 COUNT_NAMES = ["paths", "reached", "diverged", "failed", "real", "nonreal", "undecided",
-               "singular", "duplicate", "handoff", "retracked", "solves"]
-NCOUNTS = len(COUNT_NAMES) + NPHC_MAX_N - 1
+               "singular", "duplicate", "handoff", "retracked", "solves", "launches"]
+NCOUNTS = len(COUNT_NAMES) + NPHC_MAX_N
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBUDGET", 5: "ESTATE"}
 
 
@@ -40,10 +40,12 @@ class nphc_options(ctypes.Structure):
                 ("tol_sol", ctypes.c_double), ("tol_real", ctypes.c_double),
                 ("h0", ctypes.c_double), ("h_max", ctypes.c_double), ("h_min", ctypes.c_double),
                 ("eps_fp32", ctypes.c_double), ("eps_fp64", ctypes.c_double),
-                ("trust", ctypes.c_double), ("r_div", ctypes.c_double),
+                ("trust", ctypes.c_double), ("trust_fp32", ctypes.c_double),
+                ("r_div", ctypes.c_double),
                 ("r_div_fp32", ctypes.c_double), ("rho_div", ctypes.c_double),
                 ("max_newton_fp32", ctypes.c_int), ("max_newton_fp64", ctypes.c_int),
-                ("max_steps", ctypes.c_int), ("grow_after", ctypes.c_int),
+                ("max_steps", ctypes.c_int), ("max_steps_fp32", ctypes.c_int),
+                ("grow_after", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("refine_eps", ctypes.c_double),
                 ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
 
@@ -200,7 +202,7 @@ class Result:
         c = np.zeros(NCOUNTS, np.int64)
         _check("nphc_result_counts", lib().nphc_result_counts(self.handle, _pi64(c)))
         out = {k: int(c[i]) for i, k in enumerate(COUNT_NAMES)}
-        out["index_hist"] = [int(v) for v in c[len(COUNT_NAMES):len(COUNT_NAMES) + self.system.M]]
+        out["index_hist"] = [int(v) for v in c[len(COUNT_NAMES):len(COUNT_NAMES) + self.system.M + 1]]
         return out
 
     def stationary_points(self) -> dict:
