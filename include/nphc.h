@@ -96,13 +96,13 @@ typedef struct nphc_options {
     double trust;              /* FP64: reject when the first correction exceeds trust (1 + ||z||), 0.1 */
     double trust_fp32;         /* FP32: the same bound on the prediction error, 2e-3 (no wider
                                   than what the FP64 corrector's tolerance implies) */
-    double r_div;              /* FP64 divergence radius on ||z||_inf, 1e5 */
-    double r_div_fp32;         /* FP32 radius at which divergence is decided, 1e4 */
-    double rho_div;            /* FP32 declares divergence above this growth exponent, 0.5 */
+    double r_div;              /* divergence radius on ||z||_inf (both precisions), 1e4 */
     int max_newton_fp32;       /* corrector iterations per FP32 step, 3 */
     int max_newton_fp64;       /* corrector iterations per FP64 step, 3 */
     int max_steps;             /* step attempts per path, 5000 */
     int max_steps_fp32;        /* step attempts per path in the FP32 pass before hand-off, 400 */
+    int crawl_steps_fp32;      /* FP32 hands a path off when, once 1 - t < 1e-3, 1 - t fails to
+                                  halve within this many accepted steps, 32 (0: never) */
     int grow_after;            /* consecutive accepted steps before h doubles, 3 */
     int refine_iters;          /* Newton refinement steps at t = 1, 8 */
     double refine_eps;         /* refinement stops when ||dz|| <= eps (1 + ||z||), 1e-14 */

@@ -54,7 +54,7 @@ class CertOpts(ctypes.Structure):
 
 def default_track_opts(**kw) -> TrackOpts:
     """Step control of the oracle tracker (the paper gives none; see the design notes)."""
-    o = dict(h0=0.01, h_max=0.05, h_min=1e-14, eps_corr=1e-9, trust=0.1, r_div=1e5,
+    o = dict(h0=0.01, h_max=0.05, h_min=1e-14, eps_corr=1e-9, trust=0.1, r_div=1e4,
              max_newton=3, max_steps=5000, grow_after=3)
     o.update(kw)
     return TrackOpts(**o)
@@ -68,14 +68,15 @@ def default_cert_opts(**kw) -> CertOpts:
 
 
 def build(force: bool = False) -> str:
-    """Compile nphc_oracle.c into a shared library (gcc, -O2, IEEE semantics)."""
+    """Compile nphc_oracle.c into a shared library (gcc, -O2, IEEE semantics, no FMA
+    contraction so that the compensated sums stay exact)."""
     with _lock:
         if (not force and os.path.exists(_LIB)
                 and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
             return _LIB
         os.makedirs(_BUILD, exist_ok=True)
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-pthread",
+        subprocess.run(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-pthread",
                         "-o", tmp, _SRC, "-lm"], check=True)
         os.replace(tmp, _LIB)
         return _LIB
@@ -94,6 +95,7 @@ def lib():
                                    ctypes.c_double, ctypes.POINTER(TrackOpts), I64, I64,
                                    ctypes.c_int, D, D, I, I, D]
         L.oracle_sys_eval_jac.argtypes = [ctypes.c_int, ctypes.c_int, I, I, I, D, D, D, D, D, D, D, D]
+        L.oracle_sys_eval_acc.argtypes = [ctypes.c_int, ctypes.c_int, I, I, I, D, D, D, D, D, D]
         L.oracle_d2_norm.argtypes = [ctypes.c_int, ctypes.c_int, I, I, I, D, D]
         L.oracle_d2_norm.restype = ctypes.c_double
         L.oracle_refine_certify.argtypes = [ctypes.c_int, ctypes.c_int, I, I, I, D, D,
@@ -161,6 +163,15 @@ class Terms:
 
     def d2_norm(self) -> float:
         return lib().oracle_d2_norm(*self.args())
+
+    def eval_acc(self, z: np.ndarray) -> np.ndarray:
+        """P(z) with exact products and double-double sums, rounded once."""
+        n = self.n
+        z = np.asarray(z, dtype=complex)
+        zre, zim = np.ascontiguousarray(z.real), np.ascontiguousarray(z.imag)
+        pre, pim = np.zeros(n), np.zeros(n)
+        lib().oracle_sys_eval_acc(*self.args(), _d(zre), _d(zim), _d(pre), _d(pim))
+        return pre + 1j * pim
 
     def eval_jac(self, z: np.ndarray):
         """P(z) and DP(z) of the term list."""

@@ -22,8 +22,11 @@
  *     Homotopy Continuation Method");
  *   - a predictor-corrector path tracker from t=0 to t=1 (same section: "Euler's
  *     predictor and Newton's corrector"; the predictor here is classical RK4 on
- *     dz/dt = -H_z^-1 H_t, see the readings in the design notes);
- *   - refinement of endpoints by Newton's method on P to machine precision, the
+ *     dz/dt = -H_z^-1 H_t, the corrector evaluates H with compensated sums; a path whose
+ *     ||z||_inf exceeds the divergence radius is taken to go to infinity);
+ *   - refinement of endpoints by Newton's method on P to machine precision (P evaluated
+ *     with compensated double-double sums, so that the refinement and beta are limited
+ *     by the solution's conditioning and not by the rounding of ~||z||^2 terms), the
  *     solution tolerance Delta_sol and the real tolerance Delta_R (same section);
  *   - Smale alpha-theory certification (the alphaCertified step of the same section):
  *     beta = ||DP^-1 P||, gamma <= ||DP^-1|| * ||D^2 P / 2||, alpha = beta * gamma <
@@ -88,6 +91,60 @@ static void sys_eval(const qsys *S, const cplx *z, cplx *P) {
     }
 }
 
+/* P(z) with every product formed exactly and every sum carried in double-double
+ * (Knuth's two-sum, fma two-product), rounded once at the end.  Used where the value of
+ * P at a candidate solution is the quantity of interest (refinement, beta): at ||z|| >> 1
+ * the terms are ~||z||^2 and their plain double sum would be dominated by rounding. */
+typedef struct { double hi, lo; } dd;
+
+static dd dd_two_sum(double a, double b) {
+    double s = a + b, bb = s - a;
+    dd r = {s, (a - (s - bb)) + (b - bb)};
+    return r;
+}
+
+static dd dd_two_prod(double a, double b) {
+    double p = a * b;
+    dd r = {p, fma(a, b, -p)};
+    return r;
+}
+
+static dd dd_add(dd a, dd b) {
+    dd s = dd_two_sum(a.hi, b.hi);
+    double lo = s.lo + a.lo + b.lo, hi = s.hi + lo;
+    dd r = {hi, lo - (hi - s.hi)};
+    return r;
+}
+
+/* (a.hi + a.lo) * b */
+static dd dd_mul_d(dd a, double b) {
+    dd p = dd_two_prod(a.hi, b);
+    double lo = p.lo + a.lo * b, hi = p.hi + lo;
+    dd r = {hi, lo - (hi - p.hi)};
+    return r;
+}
+
+static void sys_eval_acc(const qsys *S, const cplx *z, cplx *P) {
+    int n = S->n;
+    dd *re = calloc(n, sizeof(dd)), *im = calloc(n, sizeof(dd));
+    for (int t = 0; t < S->nterms; t++) {
+        cplx wa = wvar(z, S->va[t]), wb = wvar(z, S->vb[t]);
+        /* wa * wb exactly: real = ar br - ai bi, imag = ar bi + ai br */
+        dd pr = dd_add(dd_two_prod(creal(wa), creal(wb)), dd_two_prod(-cimag(wa), cimag(wb)));
+        dd pi = dd_add(dd_two_prod(creal(wa), cimag(wb)), dd_two_prod(cimag(wa), creal(wb)));
+        /* times the coefficient c = cr + i ci */
+        double cr = S->cre[t], ci = S->cim[t];
+        dd tr = dd_add(dd_mul_d(pr, cr), dd_mul_d(pi, -ci));
+        dd ti = dd_add(dd_mul_d(pi, cr), dd_mul_d(pr, ci));
+        int e = S->eq[t];
+        re[e] = dd_add(re[e], tr);
+        im[e] = dd_add(im[e], ti);
+    }
+    for (int i = 0; i < n; i++) P[i] = (re[i].hi + re[i].lo) + I * (im[i].hi + im[i].lo);
+    free(re);
+    free(im);
+}
+
 /* DP(z), row-major n x n: d/dz_c of c*w(a)*w(b) = c*(delta_ac w(b) + delta_bc w(a)) */
 static void sys_jac(const qsys *S, const cplx *z, cplx *D) {
     int n = S->n;
@@ -113,6 +170,18 @@ void oracle_sys_eval_jac(int n, int nterms, const int *eq, const int *va, const 
     for (int i = 0; i < n; i++) { pre[i] = creal(P[i]); pim[i] = cimag(P[i]); }
     for (int i = 0; i < n * n; i++) { dre[i] = creal(D[i]); dim[i] = cimag(D[i]); }
     free(z); free(P); free(D);
+}
+
+/* Exported for the tests: P(z) with compensated sums. */
+void oracle_sys_eval_acc(int n, int nterms, const int *eq, const int *va, const int *vb,
+                         const double *cre, const double *cim, const double *zre,
+                         const double *zim, double *pre, double *pim) {
+    qsys S = {n, nterms, eq, va, vb, cre, cim};
+    cplx *z = malloc(sizeof(cplx) * n), *P = malloc(sizeof(cplx) * n);
+    for (int i = 0; i < n; i++) z[i] = zre[i] + I * zim[i];
+    sys_eval_acc(&S, z, P);
+    for (int i = 0; i < n; i++) { pre[i] = creal(P[i]); pim[i] = cimag(P[i]); }
+    free(z); free(P);
 }
 
 /* ---------------------------------------------------------------- LU (textbook) -- */
@@ -326,12 +395,31 @@ static int dzdt(const qsys *S, cplx gamma, const cplx *z, double t, work *w, cpl
     return 0;
 }
 
+/* H(z, t) = gamma (1-t) (z^2 - 1) + t P(z) with compensated sums (exact products,
+ * double-double accumulation, one rounding), for the corrector: near a point where the
+ * terms of H are much larger than H itself (large ||z||) a plain double evaluation would
+ * stall Newton's method at the rounding of the terms rather than at the solution. */
+static void hom_eval_acc(const qsys *S, cplx gamma, const cplx *z, double t, cplx *Hout, cplx *P) {
+    int n = S->n;
+    sys_eval_acc(S, z, P);   /* P to double, then t P: one product, compensated below */
+    double gr = creal(gamma) * (1.0 - t), gi = cimag(gamma) * (1.0 - t);
+    for (int i = 0; i < n; i++) {
+        double xr = creal(z[i]), xi = cimag(z[i]);
+        /* q = z^2 - 1 exactly */
+        dd qr = dd_add(dd_add(dd_two_prod(xr, xr), dd_two_prod(-xi, xi)), (dd){-1.0, 0.0});
+        dd qi = dd_two_prod(2.0 * xr, xi);
+        /* gamma (1-t) q + t P */
+        dd hr = dd_add(dd_add(dd_mul_d(qr, gr), dd_mul_d(qi, -gi)), dd_two_prod(t, creal(P[i])));
+        dd hi = dd_add(dd_add(dd_mul_d(qi, gr), dd_mul_d(qr, gi)), dd_two_prod(t, cimag(P[i])));
+        Hout[i] = (hr.hi + hr.lo) + I * (hi.hi + hi.lo);
+    }
+}
+
 /* One Newton step on H(., t): z += -H_z^-1 H.  Writes ||dz||_2 to *dn. */
 static int newton_hom(const qsys *S, cplx gamma, cplx *z, double t, work *w, double *dn) {
     int n = S->n;
-    sys_eval(S, z, w->P);
-    for (int i = 0; i < n; i++)
-        w->b[i] = -(gamma * (1.0 - t) * (z[i] * z[i] - 1.0) + t * w->P[i]);
+    hom_eval_acc(S, gamma, z, t, w->b, w->P);
+    for (int i = 0; i < n; i++) w->b[i] = -w->b[i];
     hom_jac(S, gamma, z, t, w);
     if (lu_factor(n, w->A, w->piv)) return 1;
     lu_apply(n, w->A, w->piv, w->b);
@@ -480,7 +568,7 @@ static int beta_and_inv_norm(const qsys *S, const cplx *z, double *beta, double 
     int n = S->n;
     sys_jac(S, z, w->A);
     if (lu_factor(n, w->A, w->piv)) return 1;
-    sys_eval(S, z, w->b);
+    sys_eval_acc(S, z, w->b);
     lu_apply(n, w->A, w->piv, w->b);
     *beta = norm2(n, w->b);
     double s = 0;
@@ -509,17 +597,17 @@ static int refine_certify_one(const qsys *S, double d2, const oracle_cert_opts *
     int n = S->n;
     *alpha_out = INFINITY; *beta_out = INFINITY; *gam_out = INFINITY; *res_out = INFINITY;
     *alpha_re_out = INFINITY;
-    /* Newton on P at t = 1 */
+    /* Newton on P at t = 1, P evaluated with compensated sums */
     for (int it = 0; it < o->refine_iters; it++) {
         sys_jac(S, z, w->A);
         if (lu_factor(n, w->A, w->piv)) break;
-        sys_eval(S, z, w->b);
+        sys_eval_acc(S, z, w->b);
         lu_apply(n, w->A, w->piv, w->b);
         for (int i = 0; i < n; i++) z[i] -= w->b[i];
         if (!all_finite(n, z)) return OC_SINGULAR;
         if (norm2(n, w->b) <= o->refine_eps * (1.0 + norm2(n, z))) break;
     }
-    sys_eval(S, z, w->P);
+    sys_eval_acc(S, z, w->P);
     double res = norminf(n, w->P);
     *res_out = res;
     double beta, invF;

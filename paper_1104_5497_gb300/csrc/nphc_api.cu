@@ -125,13 +125,12 @@ nphc_status nphc_options_default(nphc_options *o) {
     o->eps_fp64 = 1e-9;
     o->trust = 0.1;
     o->trust_fp32 = 2e-3;
-    o->r_div = 1e5;
-    o->r_div_fp32 = 1e4;
-    o->rho_div = 0.5;
+    o->r_div = 1e4;
     o->max_newton_fp32 = 3;
     o->max_newton_fp64 = 3;
     o->max_steps = 5000;
     o->max_steps_fp32 = 400;
+    o->crawl_steps_fp32 = 32;
     o->grow_after = 3;
     o->refine_iters = 8;
     o->refine_eps = 1e-14;
@@ -239,8 +238,8 @@ nphc_status check_opt(const nphc_options *o) {
     const double g2 = o->gamma_re * o->gamma_re + o->gamma_im * o->gamma_im;
     if (!(g2 > 0.0) || !std::isfinite(g2)) return fail(NPHC_EINVAL, "|gamma| = 0 or not finite");
     if (!(o->h0 > 0 && o->h_max >= o->h0 && o->h_min > 0 && o->eps_fp32 > 0 && o->eps_fp64 > 0 &&
-          o->trust > 0 && o->trust_fp32 > 0 && o->r_div > 0 && o->r_div_fp32 > 0 && o->max_newton_fp32 > 0 &&
-          o->max_newton_fp64 > 0 && o->max_steps > 0 && o->max_steps_fp32 > 0 && o->grow_after > 0 &&
+          o->trust > 0 && o->trust_fp32 > 0 && o->r_div > 0 && o->max_newton_fp32 > 0 &&
+          o->max_newton_fp64 > 0 && o->max_steps > 0 && o->max_steps_fp32 > 0 && o->crawl_steps_fp32 >= 0 && o->grow_after > 0 &&
           o->refine_iters >= 0))
         return fail(NPHC_EINVAL, "options out of range");
     return NPHC_OK;
@@ -261,8 +260,6 @@ XYCtl make_ctl(const nphc_options *o, bool fp32, bool resume, bool accumulate) {
     c.eps = fp32 ? o->eps_fp32 : o->eps_fp64;
     c.trust = fp32 ? o->trust_fp32 : o->trust;
     c.rdiv = o->r_div;
-    c.rdiv_soft = fp32 ? o->r_div_fp32 : o->r_div;
-    c.rho_div = o->rho_div;
     c.max_newton = fp32 ? o->max_newton_fp32 : o->max_newton_fp64;
     c.max_steps = fp32 ? o->max_steps_fp32 : o->max_steps;
     c.grow_after = o->grow_after;
@@ -270,6 +267,7 @@ XYCtl make_ctl(const nphc_options *o, bool fp32, bool resume, bool accumulate) {
     c.resume = resume ? 1 : 0;
     c.accumulate = accumulate ? 1 : 0;
     c.sparse = 0;
+    c.crawl_steps = fp32 ? o->crawl_steps_fp32 : 0;
     return c;
 }
 
@@ -366,7 +364,7 @@ nphc_status nphc_refine_certify(const nphc_system *S, const nphc_options *o,
     wl.state = nullptr;
     wl.state_threads = 0;
     NPHC_CK(launch_xy_refine_certify(S->M, sys_with_gamma(S, o), o->tol_sol, o->refine_eps,
-                                     o->refine_iters, view(ep), ep->count, wl, (cudaStream_t)stream));
+                                     o->refine_iters, view(ep), ep->count, wl, 0, (cudaStream_t)stream));
     return NPHC_OK;
 }
 
@@ -526,21 +524,26 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
         // FP32 pass over every path
         if ((s = track_impl(S, o, NPHC_PREC_MIXED, ep, nullptr, nullptr, false, false, R->ws, 0, st)))
             return s;
-        // FP64 continuation of the paths the FP32 pass handed off
+        // hand-offs: refinement at t = 1 straight from the hand-off point (certified ones
+        // are done), then FP64 continuation of the others
         NPHC_CK(launch_compact(v, PRED_HANDOFF, R->flags, R->list[0], R->lcount + 0, st));
-        if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[0], R->lcount + 0, true, true, R->ws, 1, st)))
+        WorkList l0 = {R->list[0], R->lcount + 0, nullptr, nullptr, 0};
+        NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
+                                         R->P, l0, 1, st));
+        NPHC_CK(launch_compact(v, PRED_HANDOFF, R->flags, R->list[0], R->lcount + 5, st));
+        if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[0], R->lcount + 5, true, true, R->ws, 1, st)))
             return s;
         NPHC_CK(launch_compact(v, PRED_REACHED, R->flags, R->list[3], R->lcount + 3, st));
         WorkList l3 = {R->list[3], R->lcount + 3, nullptr, nullptr, 0};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
-                                         R->P, l3, st));
+                                         R->P, l3, 0, st));
         // FP64 re-track of FP32 endpoints that did not certify
         NPHC_CK(launch_compact(v, PRED_UNCERTIFIED_FP32, R->flags, R->list[1], R->lcount + 1, st));
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[1], R->lcount + 1, false, true, R->ws, 2, st)))
             return s;
         WorkList l1 = {R->list[1], R->lcount + 1, nullptr, nullptr, 0};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
-                                         R->P, l1, st));
+                                         R->P, l1, 0, st));
         // deduplicate; every path of a solution reached more than once is re-tracked in
         // FP64 and the endpoints are deduplicated again
         NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, R->list[2], R->lcount + 2, st));
@@ -549,7 +552,7 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
             return s;
         WorkList l2 = {R->list[2], R->lcount + 2, nullptr, nullptr, 0};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
-                                         R->P, l2, st));
+                                         R->P, l2, 0, st));
         NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st));
     } else {
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, nullptr, nullptr, false, false, R->ws, 0, st)))
@@ -557,7 +560,7 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
         NPHC_CK(launch_compact(v, PRED_REACHED, R->flags, R->list[3], R->lcount + 3, st));
         WorkList l3 = {R->list[3], R->lcount + 3, nullptr, nullptr, 0};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
-                                         R->P, l3, st));
+                                         R->P, l3, 0, st));
         NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st));
     }
     NPHC_CK(launch_xy_classify(S->M, xs, v, R->theta, R->index, R->energy, R->mineig, st));
@@ -680,3 +683,4 @@ void nphc_result_destroy(nphc_result *R) {
 }
 
 }  // extern "C"
+

@@ -53,41 +53,66 @@ __device__ __forceinline__ cx<R> crecip(cx<R> a) {
 template <class R>
 __device__ __forceinline__ bool finite_r(R v) { return isfinite(v); }
 
-// ------------------------------------------------------ float-float sums --
-// Error-free transformations (Knuth's two-sum, FMA two-product) with round-to-
-// nearest intrinsics, so the compiler cannot contract or reassociate them.
-struct ff {
-    float hi, lo;
+// ---------------------------------------------- compensated (two-word) sums --
+// Error-free transformations (Knuth's two-sum, FMA two-product) with round-to-nearest
+// intrinsics, so that the compiler can neither contract nor reassociate them.  R is
+// float (float-float accumulation for the FP32 corrector) or double (double-double for
+// the FP64 corrector).
+template <class R>
+struct EFT;
+template <>
+struct EFT<float> {
+    static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+    static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+    static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+    static __device__ __forceinline__ float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+};
+template <>
+struct EFT<double> {
+    static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+    static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+    static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+    static __device__ __forceinline__ double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
 };
 
-__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
-    p = __fmul_rn(a, b);
-    e = __fmaf_rn(a, b, -p);
+template <class R>
+struct ext {   // hi + lo, |lo| ~ ulp(hi)
+    R hi, lo;
+};
+
+template <class R>
+__device__ __forceinline__ void two_prod(R a, R b, R &p, R &e) {
+    p = EFT<R>::mul(a, b);
+    e = EFT<R>::fma(a, b, -p);
 }
 
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+template <class R>
+__device__ __forceinline__ void two_sum(R a, R b, R &s, R &e) {
+    s = EFT<R>::add(a, b);
+    const R bb = EFT<R>::sub(s, a);
+    e = EFT<R>::add(EFT<R>::sub(a, EFT<R>::sub(s, bb)), EFT<R>::sub(b, bb));
 }
 
-// acc += a * b with a, b floats; the rounding errors of the product and of the sum
-// are collected in acc.lo (compensated dot product).
-__device__ __forceinline__ void ff_acc(ff &acc, float a, float b) {
-    float p, e, s, e2;
+// acc += a * b; the rounding errors of the product and of the sum are collected in
+// acc.lo (compensated dot product)
+template <class R>
+__device__ __forceinline__ void ext_acc(ext<R> &acc, R a, R b) {
+    R p, e, s, e2;
     two_prod(a, b, p, e);
     two_sum(acc.hi, p, s, e2);
     acc.hi = s;
-    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, e2));
+    acc.lo = EFT<R>::add(acc.lo, EFT<R>::add(e, e2));
 }
 
 // acc += a * (b.hi + b.lo)
-__device__ __forceinline__ void ff_acc_ff(ff &acc, float a, ff b) {
-    ff_acc(acc, a, b.hi);
-    acc.lo = __fmaf_rn(a, b.lo, acc.lo);
+template <class R>
+__device__ __forceinline__ void ext_acc_ext(ext<R> &acc, R a, ext<R> b) {
+    ext_acc(acc, a, b.hi);
+    acc.lo = EFT<R>::fma(a, b.lo, acc.lo);
 }
 
-__device__ __forceinline__ float ff_val(ff a) { return __fadd_rn(a.hi, a.lo); }
+template <class R>
+__device__ __forceinline__ R ext_val(ext<R> a) { return EFT<R>::add(a.hi, a.lo); }
 
 // ------------------------------------------------------ launch arguments --
 // Couplings and homotopy constants of one XY ring, passed by value so that the
@@ -102,14 +127,14 @@ struct XYSys {
 
 struct XYCtl {                              // step control of one tracking call
     double h0, hmax, hmin, eps, trust;
-    double rdiv;                            // divergence radius (final)
-    double rdiv_soft;                       // FP32: radius where the growth test decides
-    double rho_div;                         // FP32: growth exponent meaning divergence
+    double rdiv;                            // divergence radius on ||z||_inf
     int max_newton, max_steps, grow_after;
     int handoff;                            // 1: stops become NPHC_PATH_HANDOFF (FP32 pass)
     int resume;                             // 1: continue from (z, t, h) of the entry
     int accumulate;                         // 1: add to the entry's step/solve counters
     int sparse;                             // 1: one path per warp (lane 0 only)
+    int crawl_steps;                        // near t = 1, 1 - t must halve within this many
+                                            // accepted steps (0: no crawl test)
 };
 
 struct EPView {                             // device endpoint arrays (see nphc_endpoints)
@@ -147,7 +172,7 @@ cudaError_t launch_xy_track_f64(int M, const XYSys &sys, const XYCtl &ctl, const
                                 const WorkList &wl, int block, int grid, cudaStream_t st);
 cudaError_t launch_xy_refine_certify(int M, const XYSys &sys, double tol_sol, double refine_eps,
                                      int refine_iters, const EPView &ep, int64_t cap,
-                                     const WorkList &wl, cudaStream_t st);
+                                     const WorkList &wl, int shortcut, cudaStream_t st);
 cudaError_t launch_xy_classify(int M, const XYSys &sys, const EPView &ep, double *theta,
                                int32_t *index, double *energy, double *min_eig,
                                cudaStream_t st);

@@ -19,8 +19,8 @@ cudaError_t launch_xy_track_f64(int M, const XYSys &sys, const XYCtl &ctl, const
 
 cudaError_t launch_xy_refine_certify(int M, const XYSys &sys, double tol_sol, double refine_eps,
                                      int refine_iters, const EPView &ep, int64_t cap,
-                                     const WorkList &wl, cudaStream_t st) {
-#define C(MM) case MM: return launch_xy_refine_certify_m##MM(sys, tol_sol, refine_eps, refine_iters, ep, cap, wl, st);
+                                     const WorkList &wl, int shortcut, cudaStream_t st) {
+#define C(MM) case MM: return launch_xy_refine_certify_m##MM(sys, tol_sol, refine_eps, refine_iters, ep, cap, wl, shortcut, st);
     switch (M) { NPHC_FOR_EACH_M(C) default: return cudaErrorInvalidValue; }
 #undef C
 }

@@ -18,7 +18,7 @@
                                           const WorkList &, int, cudaStream_t);              \
     cudaError_t launch_xy_refine_certify_m##MM(const XYSys &, double, double, int,          \
                                                const EPView &, int64_t, const WorkList &,   \
-                                               cudaStream_t);                               \
+                                               int, cudaStream_t);                          \
     cudaError_t launch_xy_classify_m##MM(const XYSys &, const EPView &, double *, int32_t *, \
                                          double *, double *, cudaStream_t);
 NPHC_FOR_EACH_M(NPHC_DECL)

@@ -1,6 +1,7 @@
 // xy_endgame.cuh -- FP64 work at t = 1 on the endpoints of the XY ring:
 //   refinement: Newton's method on P to machine precision (section "Numerical Polynomial
-//     Homotopy Continuation Method": refinement "up to the machine precision");
+//     Homotopy Continuation Method": refinement "up to the machine precision"), with P
+//     evaluated by exact products and double-double sums (xy_eval_p_acc);
 //   the solution tolerance Delta_sol on ||P(z)||_inf;
 //   alpha-theory certification (the alphaCertified step of the same section):
 //     beta = ||DP^-1 P||_2, gamma <= ||DP^-1||_F ||D^2 P / 2|| (P is quadratic, so
@@ -51,6 +52,65 @@ __device__ void xy_eval_p(const double *__restrict__ J, const cx<double> (&x)[M]
         f[k] = csub(cmul(y[k], u), cmul(x[k], w));
         const cx<double> x2 = cmul(x[k], x[k]), y2 = cmul(y[k], y[k]);
         g[k] = cx<double>{x2.re + y2.re - 1.0, x2.im + y2.im};
+    }
+}
+
+// P(z) with exact products and double-double sums, rounded once: at ||z|| >> 1 the
+// terms of P are ~||z||^2 and a plain double sum is dominated by rounding, which would
+// limit the refinement and inflate beta (hence alpha) of large-norm solutions.
+struct dd {
+    double hi, lo;
+};
+
+__device__ __forceinline__ dd dd_two_prod(double a, double b) {
+    const double p = __dmul_rn(a, b);
+    return dd{p, __fma_rn(a, b, -p)};
+}
+
+__device__ __forceinline__ dd dd_add(dd a, dd b) {
+    const double s = __dadd_rn(a.hi, b.hi);
+    const double bb = __dsub_rn(s, a.hi);
+    const double e = __dadd_rn(__dsub_rn(a.hi, __dsub_rn(s, bb)), __dsub_rn(b.hi, bb));
+    const double lo = __dadd_rn(e, __dadd_rn(a.lo, b.lo));
+    const double hi = __dadd_rn(s, lo);
+    return dd{hi, __dsub_rn(lo, __dsub_rn(hi, s))};
+}
+
+// a * b with a double-double, b double
+__device__ __forceinline__ dd dd_mul_d(dd a, double b) {
+    const dd p = dd_two_prod(a.hi, b);
+    const double lo = __fma_rn(a.lo, b, p.lo);
+    const double hi = __dadd_rn(p.hi, lo);
+    return dd{hi, __dsub_rn(lo, __dsub_rn(hi, p.hi))};
+}
+
+__device__ __forceinline__ double dd_val(dd a) { return __dadd_rn(a.hi, a.lo); }
+
+template <int M>
+__device__ void xy_eval_p_acc(const double *__restrict__ J, const cx<double> (&x)[M],
+                              const cx<double> (&y)[M], cx<double> (&f)[M], cx<double> (&g)[M]) {
+#pragma unroll 1
+    for (int k = 0; k < M; k++) {
+        const double *Jk = J + k * NPHC_JSTRIDE;
+        dd ur = {Jk[M], 0.0}, ui = {0.0, 0.0}, wr = {0.0, 0.0}, wi = {0.0, 0.0};
+        for (int l = 0; l < M; l++) {   // J_kk = 0 adds exact zeros
+            ur = dd_add(ur, dd_two_prod(Jk[l], x[l].re));
+            ui = dd_add(ui, dd_two_prod(Jk[l], x[l].im));
+            wr = dd_add(wr, dd_two_prod(Jk[l], y[l].re));
+            wi = dd_add(wi, dd_two_prod(Jk[l], y[l].im));
+        }
+        // f = y u - x w
+        dd fr = dd_add(dd_add(dd_mul_d(ur, y[k].re), dd_mul_d(ui, -y[k].im)),
+                       dd_add(dd_mul_d(wr, -x[k].re), dd_mul_d(wi, x[k].im)));
+        dd fi = dd_add(dd_add(dd_mul_d(ui, y[k].re), dd_mul_d(ur, y[k].im)),
+                       dd_add(dd_mul_d(wi, -x[k].re), dd_mul_d(wr, -x[k].im)));
+        // g = c^2 + s^2 - 1
+        dd gr = dd_add(dd_add(dd_two_prod(x[k].re, x[k].re), dd_two_prod(-x[k].im, x[k].im)),
+                       dd_add(dd_two_prod(y[k].re, y[k].re), dd_two_prod(-y[k].im, y[k].im)));
+        gr = dd_add(gr, dd{-1.0, 0.0});
+        dd gi = dd_add(dd_two_prod(2.0 * x[k].re, x[k].im), dd_two_prod(2.0 * y[k].re, y[k].im));
+        f[k] = cx<double>{dd_val(fr), dd_val(fi)};
+        g[k] = cx<double>{dd_val(gr), dd_val(gi)};
     }
 }
 
@@ -158,7 +218,7 @@ template <int M>
 __device__ bool xy_beta_invnorm(Fac64<M> &F, const double *__restrict__ J, double &beta,
                                 double &invF, double &res) {
     cx<double> f[M], g[M], dx[M], dy[M];
-    xy_eval_p<M>(J, F.x, F.y, f, g);
+    xy_eval_p_acc<M>(J, F.x, F.y, f, g);
     res = 0.0;
     for (int k = 0; k < M; k++) {
         res = fmax(res, sqrt(cabs2(f[k])));
@@ -182,27 +242,37 @@ __device__ bool xy_beta_invnorm(Fac64<M> &F, const double *__restrict__ J, doubl
     return isfinite(beta) && isfinite(invF);
 }
 
+// shortcut = 1: entries handed off by the FP32 pass close to t = 1 are refined at t = 1
+// directly (Newton on P from the hand-off point: for a path to a nonsingular solution xi,
+// z(t) = xi + (1 - t) z'(1) + ..., so the point is already in xi's Newton basin).  The
+// first Newton correction must stay below SHORTCUT_TRUST (1 + ||z||); an entry that
+// certifies becomes NPHC_PATH_REACHED, any other entry is left untouched.
+#define SHORTCUT_TRUST 1e-2
+
 template <int M>
 __global__ void __launch_bounds__(128)
     xy_refine_certify_kernel(const __grid_constant__ XYSys S, double tol_sol, double refine_eps,
-                             int refine_iters, const EPView ep, const WorkList wl) {
+                             int refine_iters, const EPView ep, const WorkList wl, int shortcut) {
     const int64_t total = worklist_size(wl, ep.count);
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
     const int64_t e = worklist_entry(wl, i);
     const int64_t cnt = ep.count;
     const int st = ep.status[e];
-    ep.alpha[e] = INFINITY;
-    ep.beta[e] = INFINITY;
-    ep.gamma[e] = INFINITY;
-    ep.resid[e] = INFINITY;
-    if (st == NPHC_PATH_DIVERGED) {
-        ep.cls[e] = NPHC_END_NONE;
-        return;
-    }
-    if (st != NPHC_PATH_REACHED) {
-        ep.cls[e] = NPHC_END_FAILED;
-        return;
+    const bool sc = shortcut && st == NPHC_PATH_HANDOFF;
+    if (!sc) {
+        ep.alpha[e] = INFINITY;
+        ep.beta[e] = INFINITY;
+        ep.gamma[e] = INFINITY;
+        ep.resid[e] = INFINITY;
+        if (st == NPHC_PATH_DIVERGED) {
+            ep.cls[e] = NPHC_END_NONE;
+            return;
+        }
+        if (st != NPHC_PATH_REACHED) {
+            ep.cls[e] = NPHC_END_FAILED;
+            return;
+        }
     }
     const double *J = S.Jd;
     const double alpha0 = (13.0 - 3.0 * sqrt(17.0)) / 4.0;
@@ -216,7 +286,7 @@ __global__ void __launch_bounds__(128)
     // Newton refinement on P
     for (int it = 0; it < refine_iters; it++) {
         cx<double> f[M], g[M], dx[M], dy[M];
-        xy_eval_p<M>(J, F.x, F.y, f, g);
+        xy_eval_p_acc<M>(J, F.x, F.y, f, g);
         for (int k = 0; k < M; k++) {
             f[k] = cx<double>{-f[k].re, -f[k].im};
             g[k] = cx<double>{-g[k].re, -g[k].im};
@@ -224,6 +294,11 @@ __global__ void __launch_bounds__(128)
         fac_build<M>(F, J);
         if (!F.ok) break;
         const double dn = sqrt(fac_apply<M>(F, J, f, g, dx, dy));
+        if (sc && it == 0) {
+            double z0 = 0.0;
+            for (int k = 0; k < M; k++) z0 += cabs2(F.x[k]) + cabs2(F.y[k]);
+            if (!(dn <= SHORTCUT_TRUST * (1.0 + sqrt(z0)))) return;   // not in a basin: untouched
+        }
         double zn = 0.0;
         for (int k = 0; k < M; k++) {
             F.x[k] = cadd(F.x[k], dx[k]);
@@ -267,6 +342,11 @@ __global__ void __launch_bounds__(128)
         }
     } else if (finite) {
         ep.resid[e] = res;
+    }
+    if (sc) {
+        if (cls != NPHC_END_REAL && cls != NPHC_END_NONREAL && cls != NPHC_END_UNDECIDED) return;
+        ep.status[e] = NPHC_PATH_REACHED;
+        ep.t[e] = 1.0;
     }
     for (int k = 0; k < M; k++) {
         ep.z_re[k * cnt + e] = F.x[k].re;

@@ -9,12 +9,10 @@
 
 #if NPHC_INST_KIND == 0
 using RT = float;
-constexpr bool FFV = true;
 constexpr int BLK = NPHC_TRACK_BLOCK;
 #define NPHC_FN NPHC_CAT(launch_xy_track_f32_m, NPHC_INST_M)
 #else
 using RT = double;
-constexpr bool FFV = false;
 constexpr int BLK = NPHC_TRACK_BLOCK;
 #define NPHC_FN NPHC_CAT(launch_xy_track_f64_m, NPHC_INST_M)
 #endif
@@ -23,7 +21,7 @@ cudaError_t NPHC_FN(const XYSys &sys, const XYCtl &ctl, const EPView &ep, const 
                     int grid, cudaStream_t st) {
     constexpr int M = NPHC_INST_M;
     const size_t smem = xy_smem_per_thread<M, RT>() * BLK;
-    auto k = xy_track_kernel<M, RT, FFV, BLK>;
+    auto k = xy_track_kernel<M, RT, BLK>;
     static bool attr_set = false;   // once per process for this instantiation
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -51,11 +49,12 @@ cudaError_t NPHC_FN(const XYSys &sys, const XYCtl &ctl, const EPView &ep, const 
 cudaError_t NPHC_CAT(launch_xy_refine_certify_m, NPHC_INST_M)(const XYSys &sys, double tol_sol,
                                                              double refine_eps, int refine_iters,
                                                              const EPView &ep, int64_t cap,
-                                                             const WorkList &wl, cudaStream_t st) {
+                                                             const WorkList &wl, int shortcut,
+                                                             cudaStream_t st) {
     if (cap <= 0) return cudaSuccess;
     const int grid = (int)((cap + 127) / 128);
     xy_refine_certify_kernel<NPHC_INST_M><<<grid, 128, 0, st>>>(sys, tol_sol, refine_eps,
-                                                               refine_iters, ep, wl);
+                                                               refine_iters, ep, wl, shortcut);
     nphc_launch_counter(1);
     return cudaGetLastError();
 }

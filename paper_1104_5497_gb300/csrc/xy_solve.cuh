@@ -298,74 +298,76 @@ __device__ __forceinline__ void xy_residual_plain(const R *__restrict__ J, const
     }
 }
 
-// -H(z, t) for an FP32 point, evaluated with compensated (float-float) sums and exact
-// products, then rounded once: the error is ~2^-48 of the terms instead of 2^-24, so a
-// Newton corrector driven by it converges to the FP32 rounding of the path point even
-// when H_z is far from well conditioned (mixed-precision iterative refinement).  The
-// coefficients J, gamma (1-t) and t enter as their FP32 values.
-template <int M, int BLOCK>
-__device__ __forceinline__ void xy_residual_ff(const float *__restrict__ J,
-                                               const SVec<float, BLOCK> &pt, float s, float omt,
-                                               cx<float> gam, const SVec<float, BLOCK> &out,
-                                               bool wr) {
-    const cx<float> gomt = cx<float>{__fmul_rn(omt, gam.re), __fmul_rn(omt, gam.im)};
-    cx<float> x[M], y[M];
+// -H(z, t) evaluated with compensated sums (float-float for FP32, double-double for
+// FP64) and exact products, then rounded once: the error is ~u^2 of the terms instead of
+// u, so a Newton corrector driven by it converges to the rounding of the path point
+// even when H_z is far from well conditioned (mixed-precision iterative refinement; at
+// large ||z|| the terms of H are ~||z||^2 while H itself is near zero).  The coefficients
+// J, gamma (1-t) and t enter as their values in R.
+template <int M, class R, int BLOCK>
+__device__ __forceinline__ void xy_residual_comp(const R *__restrict__ J,
+                                                 const SVec<R, BLOCK> &pt, R s, R omt,
+                                                 cx<R> gam, const SVec<R, BLOCK> &out, bool wr) {
+    using E = EFT<R>;
+    const cx<R> gomt = cx<R>{E::mul(omt, gam.re), E::mul(omt, gam.im)};
+    cx<R> x[M], y[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
         x[k] = pt.get(k);
         y[k] = pt.get(M + k);
     }
+    const ext<R> zero = {R(0), R(0)};
 #pragma unroll 1
     for (int k = 0; k < M; k++) {
-        const cx<float> xk = pt.get(k), yk = pt.get(M + k);
-        const float *Jk = J + k * NPHC_JSTRIDE;
-        ff ure = {Jk[M], 0.f}, uim = {0.f, 0.f}, wre = {0.f, 0.f}, wim = {0.f, 0.f};
+        const cx<R> xk = pt.get(k), yk = pt.get(M + k);
+        const R *Jk = J + k * NPHC_JSTRIDE;
+        ext<R> ure = {Jk[M], R(0)}, uim = zero, wre = zero, wim = zero;
 #pragma unroll
         for (int l = 0; l < M; l++) {   // J_kk = 0 adds exact zeros
-            const float Jl = Jk[l];
-            ff_acc(ure, Jl, x[l].re);
-            ff_acc(uim, Jl, x[l].im);
-            ff_acc(wre, Jl, y[l].re);
-            ff_acc(wim, Jl, y[l].im);
+            const R Jl = Jk[l];
+            ext_acc(ure, Jl, x[l].re);
+            ext_acc(uim, Jl, x[l].im);
+            ext_acc(wre, Jl, y[l].re);
+            ext_acc(wim, Jl, y[l].im);
         }
         // f = y u - x w
-        ff fre = {0.f, 0.f}, fim = {0.f, 0.f};
-        ff_acc_ff(fre, yk.re, ure);
-        ff_acc_ff(fre, -yk.im, uim);
-        ff_acc_ff(fre, -xk.re, wre);
-        ff_acc_ff(fre, xk.im, wim);
-        ff_acc_ff(fim, yk.re, uim);
-        ff_acc_ff(fim, yk.im, ure);
-        ff_acc_ff(fim, -xk.re, wim);
-        ff_acc_ff(fim, -xk.im, wre);
-        // x^2 - 1 and y^2 - 1 exactly as float-float
-        ff qxr = {-1.f, 0.f}, qxi = {0.f, 0.f}, qyr = {-1.f, 0.f}, qyi = {0.f, 0.f};
-        ff_acc(qxr, xk.re, xk.re);
-        ff_acc(qxr, -xk.im, xk.im);
-        ff_acc(qxi, 2.f * xk.re, xk.im);
-        ff_acc(qyr, yk.re, yk.re);
-        ff_acc(qyr, -yk.im, yk.im);
-        ff_acc(qyi, 2.f * yk.re, yk.im);
+        ext<R> fre = zero, fim = zero;
+        ext_acc_ext(fre, yk.re, ure);
+        ext_acc_ext(fre, -yk.im, uim);
+        ext_acc_ext(fre, -xk.re, wre);
+        ext_acc_ext(fre, xk.im, wim);
+        ext_acc_ext(fim, yk.re, uim);
+        ext_acc_ext(fim, yk.im, ure);
+        ext_acc_ext(fim, -xk.re, wim);
+        ext_acc_ext(fim, -xk.im, wre);
+        // x^2 - 1 and y^2 - 1 exactly as two-word numbers
+        ext<R> qxr = {R(-1), R(0)}, qxi = zero, qyr = {R(-1), R(0)}, qyi = zero;
+        ext_acc(qxr, xk.re, xk.re);
+        ext_acc(qxr, -xk.im, xk.im);
+        ext_acc(qxi, R(2) * xk.re, xk.im);
+        ext_acc(qyr, yk.re, yk.re);
+        ext_acc(qyr, -yk.im, yk.im);
+        ext_acc(qyi, R(2) * yk.re, yk.im);
         // H_f = gomt (x^2 - 1) + s f ;  H_g = gomt (y^2 - 1) + s (x^2 + y^2 - 1)
-        ff hfr = {0.f, 0.f}, hfi = {0.f, 0.f}, hgr = {0.f, 0.f}, hgi = {0.f, 0.f};
-        ff_acc_ff(hfr, gomt.re, qxr);
-        ff_acc_ff(hfr, -gomt.im, qxi);
-        ff_acc_ff(hfr, s, fre);
-        ff_acc_ff(hfi, gomt.re, qxi);
-        ff_acc_ff(hfi, gomt.im, qxr);
-        ff_acc_ff(hfi, s, fim);
-        ff_acc_ff(hgr, gomt.re, qyr);
-        ff_acc_ff(hgr, -gomt.im, qyi);
-        ff_acc_ff(hgr, s, qxr);
-        ff_acc_ff(hgr, s, qyr);
-        ff_acc(hgr, s, 1.f);       // x^2 + y^2 - 1 = (x^2 - 1) + (y^2 - 1) + 1
-        ff_acc_ff(hgi, gomt.re, qyi);
-        ff_acc_ff(hgi, gomt.im, qyr);
-        ff_acc_ff(hgi, s, qxi);
-        ff_acc_ff(hgi, s, qyi);
+        ext<R> hfr = zero, hfi = zero, hgr = zero, hgi = zero;
+        ext_acc_ext(hfr, gomt.re, qxr);
+        ext_acc_ext(hfr, -gomt.im, qxi);
+        ext_acc_ext(hfr, s, fre);
+        ext_acc_ext(hfi, gomt.re, qxi);
+        ext_acc_ext(hfi, gomt.im, qxr);
+        ext_acc_ext(hfi, s, fim);
+        ext_acc_ext(hgr, gomt.re, qyr);
+        ext_acc_ext(hgr, -gomt.im, qyi);
+        ext_acc_ext(hgr, s, qxr);
+        ext_acc_ext(hgr, s, qyr);
+        ext_acc(hgr, s, R(1));       // x^2 + y^2 - 1 = (x^2 - 1) + (y^2 - 1) + 1
+        ext_acc_ext(hgi, gomt.re, qyi);
+        ext_acc_ext(hgi, gomt.im, qyr);
+        ext_acc_ext(hgi, s, qxi);
+        ext_acc_ext(hgi, s, qyi);
         if (wr) {
-            out.set(k, cx<float>{-ff_val(hfr), -ff_val(hfi)});
-            out.set(M + k, cx<float>{-ff_val(hgr), -ff_val(hgi)});
+            out.set(k, cx<R>{-ext_val(hfr), -ext_val(hfi)});
+            out.set(M + k, cx<R>{-ext_val(hgr), -ext_val(hgi)});
         }
     }
 }

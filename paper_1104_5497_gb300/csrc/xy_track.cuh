@@ -17,19 +17,21 @@
 // step is taken from the previous step's last corrector solve (second right-hand
 // side, same factorisation), and at t = 0 it is known in closed form
 // (H_z = 2 gamma diag(z), H_t = P(z)), so each step costs 3 stage solves.
-// Corrector: Newton at t + h; in FP32 its residual is evaluated with compensated sums
-// (xy_residual_ff), in FP64 directly.  A step is accepted when ||dz|| <= eps (1 + ||z||)
+// Corrector: Newton at t + h, its residual evaluated with compensated sums
+// (xy_residual_comp: float-float in FP32, double-double in FP64).  A step is accepted when ||dz|| <= eps (1 + ||z||)
 // within max_newton iterations, and rejected when the first correction exceeds
 // trust (1 + ||z||).  Step size doubles after grow_after consecutive accepts and halves
 // on a reject; the final step lands exactly on t = 1.
 //
-// FP32 pass (ctl.handoff = 1): a path whose ||z||_inf exceeds rdiv_soft is declared
-// diverged when its growth exponent d ln||z|| / d ln(1/(1-t)) over the last step
-// exceeds rho_div (paths at infinity grow like (1-t)^-rho); otherwise, and on a step
-// size underflow, ten consecutive rejects, a crawl near t = 1 (1 - t failing to halve
-// within CRAWL_STEPS accepted steps) or its own (smaller) attempt budget, it is handed
-// to FP64 (NPHC_PATH_HANDOFF) with its (z, t, h).  In FP64 a crawl ends the path
-// (NPHC_PATH_MIN_STEP).  The FP32 bound on the first correction (trust_fp32) keeps its
+// A path whose ||z||_inf exceeds rdiv is taken to go to infinity, in either precision
+// (the same radius as the oracle's: genuinely finite solutions near that scale are
+// approached with the same power-law growth as paths to infinity, so no growth test
+// can separate them before t = 1).
+// FP32 pass (ctl.handoff = 1): on a step size underflow, ten consecutive rejects, a
+// crawl near t = 1 (1 - t failing to halve
+// within crawl_steps accepted steps) or its own (smaller) attempt budget, it is handed
+// to FP64 (NPHC_PATH_HANDOFF) with its (z, t, h).  FP64 tracks like the oracle: no crawl
+// test, the same step budget and minimum step.  The FP32 bound on the first correction (trust_fp32) keeps its
 // accepted steps no longer than the FP64 tolerance allows, so that it does not step
 // across a sharp turn of the path onto a neighbouring one.
 #pragma once
@@ -48,7 +50,7 @@ struct JSel<double> {
 };
 
 #define CRAWL_ZONE 1e-3   // the crawl test applies once 1 - t < CRAWL_ZONE
-#define CRAWL_STEPS 32
+#define NEAR_END 1e-5     // FP32 radius crossings with 1 - t below this go to FP64
 
 template <int M, class R, class V>
 __device__ __forceinline__ R vnorm2(const V &v) {
@@ -66,7 +68,7 @@ __device__ __forceinline__ R vnorminf(const V &v) {
     return s;
 }
 
-template <int M, class R, bool FF, int BLOCK>
+template <int M, class R, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     xy_track_kernel(const __grid_constant__ XYSys S, const __grid_constant__ XYCtl C,
                     const EPView ep, const WorkList wl) {
@@ -87,11 +89,12 @@ __global__ void __launch_bounds__(BLOCK)
     const int64_t total = worklist_size(wl, ep.count);
     const int64_t cnt = ep.count;
 
-    int64_t e = (C.sparse && lane != 0) ? -2 : -1;   // entry index; -1 idle, -2 drained
-    double t = 0.0, h = 0.0, hacc = 0.0, tprev = 0.0;
+    // short lists run one path per warp (lane 0), spread over every SM
+    const bool sparse = C.sparse && total <= (int64_t)gridDim.x * (BLOCK / 32) * 2;
+    int64_t e = (sparse && lane != 0) ? -2 : -1;   // entry index; -1 idle, -2 drained
+    double t = 0.0, h = 0.0, hacc = 0.0;
     double tmark = 0.0;   // 1 - t recorded every CRAWL_STEPS accepted steps near t = 1
     int since = 0;
-    R zprev = R(1);
     int status = 0, run = 0, rejects = 0, attempts = 0, steps = 0, solves = 0, newton = 0;
     bool need_k1 = false;
 
@@ -156,10 +159,8 @@ __global__ void __launch_bounds__(BLOCK)
                         need_k1 = false;
                     }
                     hacc = h;
-                    tprev = t;
                     tmark = 1.0 - t;
                     since = 0;
-                    zprev = vnorminf<M, R>(Z0);
                 } else {
                     e = -2;
                 }
@@ -168,8 +169,10 @@ __global__ void __launch_bounds__(BLOCK)
         if (__all_sync(0xffffffffu, e < 0)) break;
         const bool act = (e >= 0);
 
-        // ---- one step: phase 0 = dz/dt at a resumed point (only when some lane needs
-        // it), phases 1..3 = RK4 stages 2..4, phases 4.. = Newton corrector iterations
+        // ---- one step: phase 0 = a resumed point is first pulled onto this precision's
+        // path (one Newton correction at the same t) and its dz/dt taken from the same
+        // solve (only when some lane needs it), phases 1..3 = RK4 stages 2..4, phases
+        // 4.. = Newton corrector iterations at t + h
         double hh = h, t1 = t + h;
         if (t1 >= 1.0) {
             t1 = 1.0;
@@ -183,8 +186,8 @@ __global__ void __launch_bounds__(BLOCK)
         const int nph = 4 + C.max_newton;
 #pragma unroll 1
         for (int ph = ph0; ph < nph; ph++) {
-            const bool corr = ph >= 4;   // warp-uniform
-            if (corr && __all_sync(0xffffffffu, !go || conv || bad)) break;
+            const bool corr = ph >= 4 || ph == 0;   // warp-uniform: residual + two solutions
+            if (ph >= 4 && __all_sync(0xffffffffu, !go || conv || bad)) break;
             // participating lanes and the evaluation time of this phase
             bool w;
             double te;
@@ -212,18 +215,18 @@ __global__ void __launch_bounds__(BLOCK)
                 }
             }
             const R tr = (R)te, omt = (R)(1.0 - te);
-            if (corr) {
-                if constexpr (FF)
-                    xy_residual_ff<M, BLOCK>(J, ZC, tr, omt, gam, W1, w);
-                else
-                    xy_residual_plain<M, R, BLOCK>(J, ZC, tr, omt, gam, W1, w);
-            }
+            if (corr) xy_residual_comp<M, R, BLOCK>(J, ZC, tr, omt, gam, W1, w);
             const bool oks = xy_solve<M, R, BLOCK>(J, A, ZC, tr, omt, gam, corr, W1, W1, AC, w);
             if (!w) continue;
             solves++;
             if (ph == 0) {
+                // z0 += Newton correction at t; dz/dt from the second right-hand side
 #pragma unroll 1
-                for (int k = 0; k < 2 * M; k++) K1.set(k, W1.get(k));
+                for (int k = 0; k < 2 * M; k++) {
+                    Z0.set(k, cadd(ZC.get(k), W1.get(k)));
+                    K1.set(k, AC.get(k));
+                }
+                newton++;
                 need_k1 = false;
                 if (!oks) status = C.handoff ? NPHC_PATH_HANDOFF : NPHC_PATH_NONFINITE;
             } else if (!corr) {
@@ -286,23 +289,18 @@ __global__ void __launch_bounds__(BLOCK)
                     run = 0;
                     h = fmin(2.0 * h, C.hmax);
                 }
-                if (t >= 1.0) {
+                if ((double)zi > C.rdiv)
+                    // FP32 leaves crossings close to t = 1 to FP64: a path to a finite
+                    // solution just inside the radius can overshoot it in FP32
+                    status = (C.handoff && 1.0 - t < NEAR_END) ? NPHC_PATH_HANDOFF
+                                                               : NPHC_PATH_DIVERGED;
+                else if (t >= 1.0)
                     status = NPHC_PATH_REACHED;
-                } else if ((double)zi > C.rdiv) {
-                    status = NPHC_PATH_DIVERGED;
-                } else if (C.handoff && (double)zi > C.rdiv_soft) {
-                    double rho = 0.0;
-                    if (tprev < t && zprev > R(0))
-                        rho = log((double)zi / (double)zprev) / log((1.0 - tprev) / (1.0 - t));
-                    status = rho > C.rho_div ? NPHC_PATH_DIVERGED : NPHC_PATH_HANDOFF;
-                }
-                zprev = zi;
-                tprev = t;
                 // crawl test near t = 1: 1 - t must at least halve every CRAWL_STEPS
                 // accepted steps (paths to nonsingular endpoints finish in a few steps;
                 // a crawl means a singular endpoint, infinity, or precision exhausted)
-                if (status == NPHC_PATH_RUNNING && 1.0 - t < CRAWL_ZONE) {
-                    if (++since >= CRAWL_STEPS) {
+                if (status == NPHC_PATH_RUNNING && C.crawl_steps > 0 && 1.0 - t < CRAWL_ZONE) {
+                    if (++since >= C.crawl_steps) {
                         if (1.0 - t > 0.5 * tmark)
                             status = C.handoff ? NPHC_PATH_HANDOFF : NPHC_PATH_MIN_STEP;
                         tmark = 1.0 - t;

@@ -42,9 +42,9 @@ class nphc_options(ctypes.Structure):
                 ("eps_fp32", ctypes.c_double), ("eps_fp64", ctypes.c_double),
                 ("trust", ctypes.c_double), ("trust_fp32", ctypes.c_double),
                 ("r_div", ctypes.c_double),
-                ("r_div_fp32", ctypes.c_double), ("rho_div", ctypes.c_double),
                 ("max_newton_fp32", ctypes.c_int), ("max_newton_fp64", ctypes.c_int),
                 ("max_steps", ctypes.c_int), ("max_steps_fp32", ctypes.c_int),
+                ("crawl_steps_fp32", ctypes.c_int),
                 ("grow_after", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("refine_eps", ctypes.c_double),
                 ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
