@@ -198,6 +198,32 @@ nphc_status nphc_dedup(const nphc_system *sys, const nphc_options *opt, const np
                        int32_t *dup_list, int32_t *dup_count, void *workspace,
                        size_t workspace_bytes, void *stream);
 
+/* Largest endpoint count nphc_dedup_noalloc accepts. */
+#define NPHC_DEDUP_NOALLOC_MAX 65536
+
+/* nphc_dedup without a workspace, for callers that cannot allocate device memory: a
+ * plugin or embedded solver inside a host program whose device memory all belongs to
+ * that program's own pool, or a caller that cannot afford cudaMalloc / cudaFree because
+ * they may synchronise the device and stall other streams.  The paper has no
+ * counterpart; this is an interface convenience.
+ *   Arguments, outputs and results are those of nphc_dedup (same flags, same dup_list
+ * and dup_count) for ep->count <= NPHC_DEDUP_NOALLOC_MAX (every path of a ring up to
+ * N = 9, or the reached endpoints of N = 10).  The scratch is one fixed device array
+ * inside the library (about 7.3 MB, part of the library's device image, present in every
+ * context that loads it); the call allocates nothing and calls no allocating routine.
+ *   The first call on a device (with that device current) looks up the array's device
+ * address and caches it; make that first call before any stream capture.
+ *   Every call on a device shares the one array and leaves its contents behind; each
+ * call clears the parts that must start at zero before use.  Calls whose work overlaps
+ * on the GPU (other streams, other host threads) race on the array and give wrong
+ * results: order them on one stream or synchronise between them.
+ *   NPHC_EINVAL when ep->count > NPHC_DEDUP_NOALLOC_MAX (with a message naming the
+ * limit), for the argument errors of nphc_dedup, or for a device ordinal >= 64;
+ * NPHC_ECUDA when the address lookup or a launch fails. */
+nphc_status nphc_dedup_noalloc(const nphc_system *sys, const nphc_options *opt,
+                               const nphc_endpoints *ep, int32_t *dup_list, int32_t *dup_count,
+                               void *stream);
+
 /* For every entry with cls == NPHC_END_REAL: theta_k = atan2(s_k, c_k) in (-pi, pi]
  * (theta: device [(N-1) * count], SoA), the Hessian of V in theta_1..theta_{N-1}, its
  * index (device int32 [count]: number of negative eigenvalues), its smallest |eigenvalue|

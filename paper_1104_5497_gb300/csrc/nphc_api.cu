@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -684,3 +685,84 @@ void nphc_result_destroy(nphc_result *R) {
 
 }  // extern "C"
 
+// ------------------------------------------------- allocation-free dedup --
+// nphc_dedup_noalloc: the deduplication of nphc_dedup with its scratch in a fixed
+// device array of this file instead of a caller workspace.  The array is sized for
+// NPHC_DEDUP_NOALLOC_MAX entries with the same table layout as the workspace path:
+// per level a power-of-two cell table of 2 x NPHC_DEDUP_NOALLOC_MAX slots (keys, list
+// heads), per-entry list links and flags.
+namespace {
+
+constexpr int64_t kNoallocTable = 2 * (int64_t)NPHC_DEDUP_NOALLOC_MAX;
+static_assert((kNoallocTable & (kNoallocTable - 1)) == 0 && kNoallocTable >= 1024,
+              "the cell table must be a power of two of at least 1024 slots");
+constexpr size_t noalloc_align(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t kNoallocBytes =
+    noalloc_align(sizeof(unsigned long long) * kNoallocTable * DD_LEVELS) +
+    noalloc_align(sizeof(int32_t) * kNoallocTable * DD_LEVELS) +
+    noalloc_align(sizeof(int32_t) * (size_t)NPHC_DEDUP_NOALLOC_MAX * DD_LEVELS) +
+    noalloc_align(sizeof(int32_t) * (size_t)NPHC_DEDUP_NOALLOC_MAX);
+
+static __device__ __align__(256) unsigned char g_dedup_noalloc_scratch[kNoallocBytes];
+
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[kNoallocMaxDevices] = {};
+
+// Device address of the array on the current device, looked up once per device.
+nphc_status noalloc_scratch(void **out) {
+    int dev = -1;
+    NPHC_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoallocMaxDevices) return fail(NPHC_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        NPHC_CK(cudaGetSymbolAddress(&p, g_dedup_noalloc_scratch));
+        if (!p) return fail(NPHC_ECUDA, "cudaGetSymbolAddress returned NULL");
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return NPHC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nphc_status nphc_dedup_noalloc(const nphc_system *S, const nphc_options *o,
+                               const nphc_endpoints *ep, int32_t *dup_list, int32_t *dup_count,
+                               void *stream) {
+    nphc_status s;
+    if ((s = check_ep(S, ep, true)) != NPHC_OK) return s;
+    (void)o;
+    if ((dup_list == nullptr) != (dup_count == nullptr)) return fail(NPHC_EINVAL, "list without count");
+    if (ep->count > NPHC_DEDUP_NOALLOC_MAX)
+        return fail(NPHC_EINVAL, "nphc_dedup_noalloc: " + std::to_string(ep->count) +
+                                     " entries exceed NPHC_DEDUP_NOALLOC_MAX (" +
+                                     std::to_string(NPHC_DEDUP_NOALLOC_MAX) +
+                                     "); use nphc_dedup with a workspace");
+    void *base = nullptr;
+    if ((s = noalloc_scratch(&base)) != NPHC_OK) return s;
+    if (ep->count == 0) return NPHC_OK;
+    // Same layout as the workspace path for this count, so both paths hash alike.
+    const int64_t tsize = table_size_for(ep->count);
+    char *b = static_cast<char *>(base);
+    size_t off = 0;
+    DedupScratch w;
+    w.keys = reinterpret_cast<unsigned long long *>(b + off);
+    off += align256(sizeof(unsigned long long) * tsize * DD_LEVELS);
+    w.head = reinterpret_cast<int32_t *>(b + off);
+    off += align256(sizeof(int32_t) * tsize * DD_LEVELS);
+    w.next = reinterpret_cast<int32_t *>(b + off);
+    off += align256(sizeof(int32_t) * ep->count * DD_LEVELS);
+    w.inlist = reinterpret_cast<int32_t *>(b + off);
+    off += align256(sizeof(int32_t) * ep->count);
+    w.table_size = tsize;
+    if (tsize > kNoallocTable || off > kNoallocBytes) return fail(NPHC_EINVAL, "scratch layout overflow");
+    // launch_dedup clears the cell keys, list heads, flags and *dup_count itself with
+    // cudaMemsetAsync on `stream`; the list links are written before they are read.
+    NPHC_CK(launch_dedup(view(ep), S->n, kDedupDelta, w, dup_list, dup_count, (cudaStream_t)stream));
+    return NPHC_OK;
+}
+
+}  // extern "C"

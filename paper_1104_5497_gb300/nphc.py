@@ -88,6 +88,8 @@ def lib():
                                 vp, vp, vp],
         "nphc_dedup": [vp, ctypes.POINTER(nphc_options), ctypes.POINTER(nphc_endpoints), vp, vp,
                        vp, ctypes.c_size_t, vp],
+        "nphc_dedup_noalloc": [vp, ctypes.POINTER(nphc_options), ctypes.POINTER(nphc_endpoints),
+                               vp, vp, vp],
         "nphc_classify": [vp, ctypes.POINTER(nphc_endpoints), vp, vp, vp, vp, vp],
         "nphc_result_create": [vp, ctypes.POINTER(vp)],
         "nphc_solve_into": [vp, ctypes.POINTER(nphc_options), vp, vp],
@@ -314,6 +316,19 @@ def dedup(system: System, opts: nphc_options, ep: DeviceEndpoints, workspace, du
         None if dup_list is None else dup_list.data_ptr(),
         None if dup_count is None else dup_count.data_ptr(),
         workspace.data_ptr(), workspace.numel() * workspace.element_size(), _stream_ptr(stream)))
+
+
+DEDUP_NOALLOC_MAX = 65536   # NPHC_DEDUP_NOALLOC_MAX
+
+
+def dedup_noalloc(system: System, opts: nphc_options, ep: DeviceEndpoints, dup_list=None,
+                  dup_count=None, stream=None) -> None:
+    """nphc_dedup_noalloc: dedup with the library's fixed scratch array (no workspace)."""
+    s = ep.struct()
+    _check("nphc_dedup_noalloc", lib().nphc_dedup_noalloc(
+        system.handle, ctypes.byref(opts), ctypes.byref(s),
+        None if dup_list is None else dup_list.data_ptr(),
+        None if dup_count is None else dup_count.data_ptr(), _stream_ptr(stream)))
 
 
 def classify(system: System, ep: DeviceEndpoints, theta, index, energy, min_abs_eig=None,
