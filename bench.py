@@ -247,6 +247,14 @@ def run_mine(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     counts = res.counts()
+    if args.profile:
+        # profiler captures: the solve loop only, no bench line
+        if rank == 0:
+            print(json.dumps({"profile": True, "ms_per_step": ms, "steps": args.steps,
+                              "warmup": args.warmup, "counts": counts}), flush=True)
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     launches = counts["launches"] * args.steps
     value = world * P / (ms / 1e3)
 
@@ -354,6 +362,8 @@ def main():
     ap.add_argument("--cpu-paths", type=int, default=8192, help="oracle sample for cpu_baseline")
     ap.add_argument("--ref-paths", type=int, default=2048, help="oracle sample per reference step")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--profile", action="store_true",
+                    help="run only the timed solve loop (for profiler captures); no bench line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
