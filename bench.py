@@ -48,6 +48,22 @@ def env_rank():
             int(os.environ.get("WORLD_SIZE", 1)))
 
 
+def max_over_ranks(x: float, world: int, device="cuda") -> float:
+    """The largest x over all ranks (the slowest replica's time); x itself at world 1."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(paths_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job paths/s: every rank solves its own replica of the workload."""
+    return world * paths_per_rank / seconds
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle-reason samples during the timed region."""
 
@@ -241,11 +257,7 @@ def run_mine(args):
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
         barrier()
-    ms = float(np.mean(times))
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(float(np.mean(times)), world)
     counts = res.counts()
     if args.profile:
         # profiler captures: the solve loop only, no bench line
@@ -256,7 +268,7 @@ def run_mine(args):
             torch.distributed.destroy_process_group()
         return
     launches = counts["launches"] * args.steps
-    value = world * P / (ms / 1e3)
+    value = replica_value(P, world, ms / 1e3)
 
     # ---- the dominant kernel alone: FP32 tracker, CUDA events on the launching stream
     ep = nphc.DeviceEndpoints.empty(2 * M, np.arange(P))
@@ -311,11 +323,7 @@ def run_mine(args):
         if k >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
         d2h = sum(v.nbytes for v in sps.values()) + 8 * nphc.NCOUNTS
-    e2e_s = float(np.mean(e2e_t))
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(float(np.mean(e2e_t)), world)
 
     # ---- CPU oracle on a sample of the same workload (rank 0, N = 1 only)
     cpu = None
@@ -336,7 +344,7 @@ def run_mine(args):
                                                       and counts["index_hist"] == c64["index_hist"])},
                 "plain_fp64": {"value": P / (ms64 / 1e3), "unit": "paths/s", "ms_per_step": ms64,
                                "speedup_mixed_over_fp64": ms64 / ms},
-                "e2e": {"value": world * P / e2e_s, "unit": "paths/s",
+                "e2e": {"value": replica_value(P, world, e2e_s), "unit": "paths/s",
                         "h2d_bytes_per_step": int(J_host.nbytes), "d2h_bytes_per_step": int(d2h)},
                 "roofline": {"bound": "alu", "kernel": "xy_track_kernel<9,float> (FP32 tracker)",
                              "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",

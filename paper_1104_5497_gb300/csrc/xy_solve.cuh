@@ -16,13 +16,16 @@
 // unitary (no pivot search, no growth) and data-independent in its control flow.
 // Cost ~ (8/3) M^3 + O(M^2 + M N) real flops instead of (8/3) (2M)^3 for the full system.
 //
-// Memory layout (one path per thread): the M x M matrix S of each thread lives in
-// shared memory, column-major, each complex entry interleaved across the threads of
-// the block (entry (i, c) of thread t at [(c M + i) BLOCK + t]: conflict-free 64-bit
-// accesses).  Householder step k keeps its reflector in registers and streams the
-// remaining columns through registers one at a time, so the code is a short loop per
-// step instead of a fully unrolled M^3 block (which would not fit the instruction
-// cache); the right-hand sides stay in registers throughout.
+// Memory layout (one path per thread): the augmented M x (M + 2) matrix [S | b0 | b1]
+// of each thread lives in shared memory, column-major, each complex entry interleaved
+// across the threads of the block (entry (i, c) of thread t at [(c M + i) BLOCK + t]:
+// conflict-free 64-bit accesses).  The Householder step k is a runtime loop: its
+// reflector sits in registers, and the remaining columns, right-hand sides included,
+// stream through registers one at a time in a loop of fixed length M that leaves early
+// (k is the same for every thread of a warp, so the exit is uniform).  The QR, the back
+// substitution and the recovery thus each exist once in the code: unrolled over k they
+// outgrow the instruction cache from M ~ 8 on, and the kernel stalls on instruction
+// fetch.
 #pragma once
 
 #include "nphc_internal.cuh"
@@ -54,9 +57,10 @@ struct SMat {
     __device__ __forceinline__ void set(int i, int c, cx<R> v) const { p[(c * M + i) * BLOCK] = v; }
 };
 
-// Shared memory per thread: the matrix plus two vectors (evaluation point, solve output).
+// Shared memory per thread: the augmented matrix plus two vectors (evaluation point,
+// solve output).
 template <int M, class R>
-constexpr size_t xy_smem_per_thread() { return sizeof(cx<R>) * (size_t)(M * M + 4 * M); }
+constexpr size_t xy_smem_per_thread() { return sizeof(cx<R>) * (size_t)(M * (M + 2) + 4 * M); }
 
 __device__ __forceinline__ void compiler_fence() { asm volatile("" ::: "memory"); }
 
@@ -167,19 +171,30 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
         A.set(j, j, csub(cmul(Ajj, bh), cmul(Bjj, ah)));
     }
 
-    // ---- Householder QR: Q^H S = R (real diagonal), applied to the right-hand sides
-    R dg[M];
-    bool ok = true;
+    // right-hand sides into columns M and M + 1
 #pragma unroll
     for (int k = 0; k < M; k++) {
+        A.set(k, M, b0[k]);
+        if (two_rhs) A.set(k, M + 1, b1[k]);
+    }
+
+    // ---- Householder QR: Q^H [S | b] = [R | Q^H b], R with a real diagonal (stored as
+    // (beta, 0) on the diagonal of S)
+    const int ncol = two_rhs ? M + 2 : M + 1;
+    bool ok = true;
+#pragma unroll 1
+    for (int k = 0; k < M; k++) {
+        const int n = M - k;   // active rows k .. M-1, relative index i = 0 .. n-1
+        const SMat<M, R, BLOCK> Ak{A.p + k * BLOCK};   // Ak.get(i, c) = S(k + i, c)
         cx<R> v[M];
         R xn2 = R(0);
 #pragma unroll
-        for (int i = k + 1; i < M; i++) {
-            v[i] = A.get(i, k);
+        for (int i = 1; i < M; i++) {
+            if (i >= n) break;
+            v[i] = Ak.get(i, k);
             xn2 += cabs2(v[i]);
         }
-        const cx<R> al = A.get(k, k);
+        const cx<R> al = Ak.get(0, k);
         const R an = sqrt_r(cabs2(al) + xn2);
         ok = ok && (an > R(0));
         const R beta = al.re >= R(0) ? -an : an;
@@ -187,60 +202,55 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
         const cx<R> tauc = cx<R>{(beta - al.re) * ib, al.im * ib};   // conj(tau)
         const cx<R> sc = crecip(cx<R>{al.re - beta, al.im});
 #pragma unroll
-        for (int i = k + 1; i < M; i++) v[i] = cmul(v[i], sc);   // reflector, v_k = 1
-        dg[k] = beta;
-        // stream the trailing columns through registers
+        for (int i = 1; i < M; i++) {
+            if (i >= n) break;
+            v[i] = cmul(v[i], sc);   // reflector (1, v_1, .., v_{n-1})
+        }
+        Ak.set(0, k, cx<R>{beta, R(0)});
 #pragma unroll 1
-        for (int c = k + 1; c < M; c++) {
+        for (int c = k + 1; c < ncol; c++) {
             cx<R> col[M];
-            cx<R> wv = A.get(k, c);
+            col[0] = Ak.get(0, c);
+            cx<R> wv = col[0];
 #pragma unroll
-            for (int i = k + 1; i < M; i++) {
-                col[i] = A.get(i, c);
+            for (int i = 1; i < M; i++) {
+                if (i >= n) break;
+                col[i] = Ak.get(i, c);
                 wv = cadd(wv, cmulc(v[i], col[i]));
             }
             wv = cmul(tauc, wv);
-            A.set(k, c, csub(A.get(k, c), wv));
+            Ak.set(0, c, csub(col[0], wv));
 #pragma unroll
-            for (int i = k + 1; i < M; i++) A.set(i, c, csub(col[i], cmul(v[i], wv)));
-        }
-        {
-            cx<R> wv = b0[k];
-#pragma unroll
-            for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(v[i], b0[i]));
-            wv = cmul(tauc, wv);
-            b0[k] = csub(b0[k], wv);
-#pragma unroll
-            for (int i = k + 1; i < M; i++) b0[i] = csub(b0[i], cmul(v[i], wv));
-        }
-        if (two_rhs) {
-            cx<R> wv = b1[k];
-#pragma unroll
-            for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(v[i], b1[i]));
-            wv = cmul(tauc, wv);
-            b1[k] = csub(b1[k], wv);
-#pragma unroll
-            for (int i = k + 1; i < M; i++) b1[i] = csub(b1[i], cmul(v[i], wv));
+            for (int i = 1; i < M; i++) {
+                if (i >= n) break;
+                Ak.set(i, c, csub(col[i], cmul(v[i], wv)));
+            }
         }
     }
-    // ---- back substitution R s = Q^H b (in place)
-#pragma unroll
+
+    // ---- back substitution R s = Q^H b, column by column, in place in columns M, M + 1
+#pragma unroll 1
     for (int k = M - 1; k >= 0; k--) {
-        cx<R> a0 = b0[k], a1 = b1[k];
-#pragma unroll
-        for (int c = k + 1; c < M; c++) {
-            const cx<R> Rkc = A.get(k, c);
-            a0 = csub(a0, cmul(Rkc, b0[c]));
-            a1 = csub(a1, cmul(Rkc, b1[c]));
+        const R ir = recip_r(A.get(k, k).re);
+        const cx<R> s0 = cscale(ir, A.get(k, M));
+        A.set(k, M, s0);
+        cx<R> s1 = cx<R>{R(0), R(0)};
+        if (two_rhs) {
+            s1 = cscale(ir, A.get(k, M + 1));
+            A.set(k, M + 1, s1);
         }
-        const R ir = recip_r(dg[k]);
-        b0[k] = cscale(ir, a0);
-        b1[k] = cscale(ir, a1);
+#pragma unroll
+        for (int i = 0; i < M - 1; i++) {
+            if (i >= k) break;
+            const cx<R> Rik = A.get(i, k);
+            A.set(i, M, csub(A.get(i, M), cmul(Rik, s0)));
+            if (two_rhs) A.set(i, M + 1, csub(A.get(i, M + 1), cmul(Rik, s1)));
+        }
     }
 
     // ---- back to (dx, dy)
     R chk = R(0);
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < M; j++) {
         const cx<R> xj = pt.get(j), yj = pt.get(M + j);
         cx<R> ah, bh;
@@ -248,13 +258,15 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
         g_frame<R>(xj, yj, s, sg, ah, bh, iv);
         const cx<R> htg = minus_ht_g<R>(xj, yj, gam);
         const cx<R> q0 = cscale(iv, two_rhs ? res.get(M + j) : htg);
-        const cx<R> dx0 = cadd(cmulc(ah, q0), cmul(bh, b0[j]));
-        const cx<R> dy0 = csub(cmulc(bh, q0), cmul(ah, b0[j]));
+        const cx<R> s0 = A.get(j, M);
+        const cx<R> dx0 = cadd(cmulc(ah, q0), cmul(bh, s0));
+        const cx<R> dy0 = csub(cmulc(bh, q0), cmul(ah, s0));
         chk += cabs2(dx0) + cabs2(dy0);
         if (two_rhs) {
             const cx<R> q1 = cscale(iv, htg);
-            const cx<R> dx1 = cadd(cmulc(ah, q1), cmul(bh, b1[j]));
-            const cx<R> dy1 = csub(cmulc(bh, q1), cmul(ah, b1[j]));
+            const cx<R> s1 = A.get(j, M + 1);
+            const cx<R> dx1 = cadd(cmulc(ah, q1), cmul(bh, s1));
+            const cx<R> dy1 = csub(cmulc(bh, q1), cmul(ah, s1));
             chk += cabs2(dx1) + cabs2(dy1);
             if (wr) {
                 out2.set(j, dx1);

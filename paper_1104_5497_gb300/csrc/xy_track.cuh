@@ -50,7 +50,8 @@ struct JSel<double> {
 };
 
 #define CRAWL_ZONE 1e-3   // the crawl test applies once 1 - t < CRAWL_ZONE
-#define NEAR_END 1e-5     // FP32 radius crossings with 1 - t below this go to FP64
+#define NEAR_END 1e-5     // FP32 radius crossings with 1 - t below this ...
+#define RDIV_BAND 1e-3    // ... and ||z||_inf within rdiv (1 + RDIV_BAND) go to FP64
 
 template <int M, class R, class V>
 __device__ __forceinline__ R vnorm2(const V &v) {
@@ -76,8 +77,8 @@ __global__ void __launch_bounds__(BLOCK)
     cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
     const int tid = threadIdx.x, lane = tid & 31;
     const SMat<M, R, BLOCK> A{sm + tid};
-    const SVec<R, BLOCK> ZC{sm + M * M * BLOCK + tid};           // evaluation point / iterate
-    const SVec<R, BLOCK> W1{sm + (M * M + 2 * M) * BLOCK + tid}; // solve output / residual
+    const SVec<R, BLOCK> ZC{sm + M * (M + 2) * BLOCK + tid};           // evaluation point / iterate
+    const SVec<R, BLOCK> W1{sm + (M * (M + 2) + 2 * M) * BLOCK + tid}; // solve output / residual
     const int64_t gtid = (int64_t)blockIdx.x * BLOCK + tid;
     const int64_t nth = wl.state_threads;
     cx<R> *st = reinterpret_cast<cx<R> *>(wl.state);
@@ -290,10 +291,13 @@ __global__ void __launch_bounds__(BLOCK)
                     h = fmin(2.0 * h, C.hmax);
                 }
                 if ((double)zi > C.rdiv)
-                    // FP32 leaves crossings close to t = 1 to FP64: a path to a finite
-                    // solution just inside the radius can overshoot it in FP32
-                    status = (C.handoff && 1.0 - t < NEAR_END) ? NPHC_PATH_HANDOFF
-                                                               : NPHC_PATH_DIVERGED;
+                    // An FP32 point is accurate to ~eps relative, so a crossing by more
+                    // than RDIV_BAND is one in FP64 too; FP32 leaves only the marginal
+                    // crossings close to t = 1 to FP64
+                    status = (C.handoff && 1.0 - t < NEAR_END &&
+                              (double)zi <= C.rdiv * (1.0 + RDIV_BAND))
+                                 ? NPHC_PATH_HANDOFF
+                                 : NPHC_PATH_DIVERGED;
                 else if (t >= 1.0)
                     status = NPHC_PATH_REACHED;
                 // crawl test near t = 1: 1 - t must at least halve every CRAWL_STEPS
