@@ -1,7 +1,8 @@
 // xy_endgame.cuh -- FP64 work at t = 1 on the endpoints of the XY ring:
-//   refinement: Newton's method on P to machine precision (section "Numerical Polynomial
-//     Homotopy Continuation Method": refinement "up to the machine precision"), with P
-//     evaluated by exact products and double-double sums (xy_eval_p_acc);
+//   refinement: Newton's method on P to full double precision (section "Numerical
+//     Polynomial Homotopy Continuation Method" refines every endpoint to machine
+//     precision before certifying it), with P evaluated by exact products and
+//     double-double sums (eg_minus_p);
 //   the solution tolerance Delta_sol on ||P(z)||_inf;
 //   alpha-theory certification (the alphaCertified step of the same section):
 //     beta = ||DP^-1 P||_2, gamma <= ||DP^-1||_F ||D^2 P / 2|| (P is quadratic, so
@@ -14,46 +15,60 @@
 //     V = sum_{i<j} J_ij (1 - cos(theta_i - theta_j)) in theta_1..theta_M, its number of
 //     negative eigenvalues (cyclic Jacobi), and V.
 //
-// The linear solves reuse the structure of xy_solve.cuh at t = 1 (a unitary frame per
-// constraint row, an M x M Schur system factored once by Householder QR) but keep the
-// factorisation in local memory so that it can be applied to many right-hand sides:
-// ||DP^-1||_F^2 = sum_i ||DP^-1 e_i||^2 needs 2M of them.
+// Linear algebra at t = 1 (the structure of xy_solve.cuh): in the unitary per-site frame
+// W, (dx_j, dy_j) = conj(a^_j, b^_j) q_j + (b^_j, -a^_j) s_j, the Jacobian becomes
+//   DP W = [[C, S], [D, 0]],   D = diag(nu_j), nu_j = |(a_j, b_j)| = 1 / iv_j,
+//   C_kj = A_kj conj(a^_j) + B_kj conj(b^_j),  S_kj = A_kj b^_j - B_kj a^_j,
+// (A, B: derivatives of the gradient rows in c and s) with inverse
+//   [[0, D^-1], [S^-1, -S^-1 C D^-1]],
+// so a solve costs one M x M system, and, W being unitary,
+//   ||DP^-1||_F^2 = sum_j iv_j^2 + ||S^-1||_F^2 + ||S^-1 C D^-1||_F^2
+// needs only 2M triangular solves after one Householder QR of S (stored: R above the
+// diagonal with a real diagonal, the reflectors below, conj(tau) aside).
+//
+// Storage: one endpoint per thread, everything in shared memory, interleaved across the
+// 32 threads of a block (element i of a thread's array at [i * 32 + lane]), so that the
+// rolled loops index it at run time without local memory.
 #pragma once
 
 #include "nphc_internal.cuh"
 
-template <int M>
-struct Fac64 {
-    cx<double> A[M][M];   // R above the diagonal, Householder vectors below
-    cx<double> tauc[M];   // conj(tau) of each reflector
-    double dg[M];         // real diagonal of R
-    cx<double> ah[M], bh[M];
-    double iv[M];
-    cx<double> Ad[M], Bd[M];   // diagonal Jacobian entries of the gradient rows
-    cx<double> x[M], y[M];
-    bool ok;
+#define EG_BLOCK 32
+
+// One thread's array of complex doubles in shared memory.
+struct EGVec {
+    cx<double> *p;
+    __device__ __forceinline__ cx<double> get(int i) const { return p[i * EG_BLOCK]; }
+    __device__ __forceinline__ void set(int i, cx<double> v) const { p[i * EG_BLOCK] = v; }
 };
 
-// P(z) (t = 1): gradient rows f_k and constraint rows g_k.
+// Per-thread working set of the endgame (complex doubles, in this order).
 template <int M>
-__device__ void xy_eval_p(const double *__restrict__ J, const cx<double> (&x)[M],
-                          const cx<double> (&y)[M], cx<double> (&f)[M], cx<double> (&g)[M]) {
-#pragma unroll 1
-    for (int k = 0; k < M; k++) {
-        cx<double> u = cx<double>{J[k * NPHC_JSTRIDE + M], 0.0}, w = cx<double>{0.0, 0.0};
-        for (int l = 0; l < M; l++) {
-            if (l == k) continue;
-            const double Jl = J[k * NPHC_JSTRIDE + l];
-            u.re += Jl * x[l].re;
-            u.im += Jl * x[l].im;
-            w.re += Jl * y[l].re;
-            w.im += Jl * y[l].im;
-        }
-        f[k] = csub(cmul(y[k], u), cmul(x[k], w));
-        const cx<double> x2 = cmul(x[k], x[k]), y2 = cmul(y[k], y[k]);
-        g[k] = cx<double>{x2.re + y2.re - 1.0, x2.im + y2.im};
-    }
-}
+struct EGLayout {
+    static constexpr int S = 0;                 // M x M, column-major: entry (i, c) at c M + i
+    static constexpr int TQ = S + M * M;        // conj(tau) of the reflectors
+    static constexpr int AH = TQ + M;           // frame a^
+    static constexpr int BH = AH + M;           // frame b^
+    static constexpr int IV = BH + M;           // iv (real part)
+    static constexpr int AD = IV + M;           // d f_j / d c_j
+    static constexpr int BD = AD + M;           // d f_j / d s_j
+    static constexpr int X = BD + M;            // c_1..c_M
+    static constexpr int Y = X + M;             // s_1..s_M
+    static constexpr int R = Y + M;             // right-hand side / residual, 2M
+    static constexpr int D = R + 2 * M;         // solution, 2M
+    static constexpr int TOTAL = D + 2 * M;
+};
+
+template <int M>
+constexpr size_t eg_smem_per_thread() { return sizeof(cx<double>) * (size_t)EGLayout<M>::TOTAL; }
+
+template <int M>
+struct EG {
+    cx<double> *base;
+    __device__ __forceinline__ EGVec v(int off) const { return EGVec{base + off * EG_BLOCK}; }
+    __device__ __forceinline__ cx<double> S(int i, int c) const { return base[(c * M + i) * EG_BLOCK]; }
+    __device__ __forceinline__ void setS(int i, int c, cx<double> a) const { base[(c * M + i) * EG_BLOCK] = a; }
+};
 
 // P(z) with exact products and double-double sums, rounded once: at ||z|| >> 1 the
 // terms of P are ~||z||^2 and a plain double sum is dominated by rounding, which would
@@ -86,159 +101,210 @@ __device__ __forceinline__ dd dd_mul_d(dd a, double b) {
 
 __device__ __forceinline__ double dd_val(dd a) { return __dadd_rn(a.hi, a.lo); }
 
+// -P(z) into R, with exact products and double-double sums; returns ||P||_inf.
 template <int M>
-__device__ void xy_eval_p_acc(const double *__restrict__ J, const cx<double> (&x)[M],
-                              const cx<double> (&y)[M], cx<double> (&f)[M], cx<double> (&g)[M]) {
+__device__ double eg_minus_p(const EG<M> &G, const double *__restrict__ J) {
+    const EGVec X = G.v(EGLayout<M>::X), Y = G.v(EGLayout<M>::Y), R = G.v(EGLayout<M>::R);
+    double res = 0.0;
 #pragma unroll 1
     for (int k = 0; k < M; k++) {
         const double *Jk = J + k * NPHC_JSTRIDE;
         dd ur = {Jk[M], 0.0}, ui = {0.0, 0.0}, wr = {0.0, 0.0}, wi = {0.0, 0.0};
+#pragma unroll 1
         for (int l = 0; l < M; l++) {   // J_kk = 0 adds exact zeros
-            ur = dd_add(ur, dd_two_prod(Jk[l], x[l].re));
-            ui = dd_add(ui, dd_two_prod(Jk[l], x[l].im));
-            wr = dd_add(wr, dd_two_prod(Jk[l], y[l].re));
-            wi = dd_add(wi, dd_two_prod(Jk[l], y[l].im));
+            const cx<double> xl = X.get(l), yl = Y.get(l);
+            ur = dd_add(ur, dd_two_prod(Jk[l], xl.re));
+            ui = dd_add(ui, dd_two_prod(Jk[l], xl.im));
+            wr = dd_add(wr, dd_two_prod(Jk[l], yl.re));
+            wi = dd_add(wi, dd_two_prod(Jk[l], yl.im));
         }
+        const cx<double> xk = X.get(k), yk = Y.get(k);
         // f = y u - x w
-        dd fr = dd_add(dd_add(dd_mul_d(ur, y[k].re), dd_mul_d(ui, -y[k].im)),
-                       dd_add(dd_mul_d(wr, -x[k].re), dd_mul_d(wi, x[k].im)));
-        dd fi = dd_add(dd_add(dd_mul_d(ui, y[k].re), dd_mul_d(ur, y[k].im)),
-                       dd_add(dd_mul_d(wi, -x[k].re), dd_mul_d(wr, -x[k].im)));
+        const dd fr = dd_add(dd_add(dd_mul_d(ur, yk.re), dd_mul_d(ui, -yk.im)),
+                             dd_add(dd_mul_d(wr, -xk.re), dd_mul_d(wi, xk.im)));
+        const dd fi = dd_add(dd_add(dd_mul_d(ui, yk.re), dd_mul_d(ur, yk.im)),
+                             dd_add(dd_mul_d(wi, -xk.re), dd_mul_d(wr, -xk.im)));
         // g = c^2 + s^2 - 1
-        dd gr = dd_add(dd_add(dd_two_prod(x[k].re, x[k].re), dd_two_prod(-x[k].im, x[k].im)),
-                       dd_add(dd_two_prod(y[k].re, y[k].re), dd_two_prod(-y[k].im, y[k].im)));
+        dd gr = dd_add(dd_add(dd_two_prod(xk.re, xk.re), dd_two_prod(-xk.im, xk.im)),
+                       dd_add(dd_two_prod(yk.re, yk.re), dd_two_prod(-yk.im, yk.im)));
         gr = dd_add(gr, dd{-1.0, 0.0});
-        dd gi = dd_add(dd_two_prod(2.0 * x[k].re, x[k].im), dd_two_prod(2.0 * y[k].re, y[k].im));
-        f[k] = cx<double>{dd_val(fr), dd_val(fi)};
-        g[k] = cx<double>{dd_val(gr), dd_val(gi)};
+        const dd gi = dd_add(dd_two_prod(2.0 * xk.re, xk.im), dd_two_prod(2.0 * yk.re, yk.im));
+        const cx<double> f = cx<double>{dd_val(fr), dd_val(fi)};
+        const cx<double> g = cx<double>{dd_val(gr), dd_val(gi)};
+        res = fmax(res, fmax(sqrt(cabs2(f)), sqrt(cabs2(g))));
+        R.set(k, cx<double>{-f.re, -f.im});
+        R.set(M + k, cx<double>{-g.re, -g.im});
     }
+    return res;
 }
 
-// Factor DP(z) (t = 1).
+// Frames, diagonal Jacobian entries and the Householder QR of S at the point (X, Y).
+// Returns false when S is singular.
 template <int M>
-__device__ void fac_build(Fac64<M> &F, const double *__restrict__ J) {
+__device__ bool eg_factor(const EG<M> &G, const double *__restrict__ J) {
+    using L = EGLayout<M>;
+    const EGVec X = G.v(L::X), Y = G.v(L::Y), AH = G.v(L::AH), BH = G.v(L::BH), IV = G.v(L::IV),
+                AD = G.v(L::AD), BD = G.v(L::BD), TQ = G.v(L::TQ);
 #pragma unroll 1
     for (int j = 0; j < M; j++) {
-        cx<double> u = cx<double>{J[j * NPHC_JSTRIDE + M], 0.0}, w = cx<double>{0.0, 0.0};
+        const double *Jj = J + j * NPHC_JSTRIDE;
+        cx<double> u = cx<double>{Jj[M], 0.0}, w = cx<double>{0.0, 0.0};
+#pragma unroll 1
         for (int l = 0; l < M; l++) {
-            if (l == j) continue;
-            const double Jl = J[j * NPHC_JSTRIDE + l];
-            u.re += Jl * F.x[l].re;
-            u.im += Jl * F.x[l].im;
-            w.re += Jl * F.y[l].re;
-            w.im += Jl * F.y[l].im;
+            const cx<double> xl = X.get(l), yl = Y.get(l);
+            u.re += Jj[l] * xl.re;
+            u.im += Jj[l] * xl.im;
+            w.re += Jj[l] * yl.re;
+            w.im += Jj[l] * yl.im;
         }
-        F.Ad[j] = cx<double>{-w.re, -w.im};   // d f_j / d c_j
-        F.Bd[j] = u;                          // d f_j / d s_j
-        const cx<double> a = cscale(2.0, F.x[j]), b = cscale(2.0, F.y[j]);
+        AD.set(j, cx<double>{-w.re, -w.im});
+        BD.set(j, u);
+        const cx<double> a = cscale(2.0, X.get(j)), b = cscale(2.0, Y.get(j));
         const double iv = rsqrt(cabs2(a) + cabs2(b));
-        F.iv[j] = iv;
-        F.ah[j] = cscale(iv, a);
-        F.bh[j] = cscale(iv, b);
+        IV.set(j, cx<double>{iv, 0.0});
+        AH.set(j, cscale(iv, a));
+        BH.set(j, cscale(iv, b));
     }
 #pragma unroll 1
-    for (int j = 0; j < M; j++)
+    for (int j = 0; j < M; j++) {
+        const cx<double> ah = AH.get(j), bh = BH.get(j);
+#pragma unroll 1
         for (int k = 0; k < M; k++) {
+            cx<double> e;
             if (k == j)
-                F.A[k][j] = csub(cmul(F.Ad[j], F.bh[j]), cmul(F.Bd[j], F.ah[j]));
+                e = csub(cmul(AD.get(j), bh), cmul(BD.get(j), ah));
             else
-                F.A[k][j] = cscale(J[k * NPHC_JSTRIDE + j],
-                                   cadd(cmul(F.y[k], F.bh[j]), cmul(F.x[k], F.ah[j])));
+                e = cscale(J[k * NPHC_JSTRIDE + j], cadd(cmul(Y.get(k), bh), cmul(X.get(k), ah)));
+            G.setS(k, j, e);
         }
-    F.ok = true;
+    }
+    bool ok = true;
 #pragma unroll 1
     for (int k = 0; k < M; k++) {
-        const cx<double> al = F.A[k][k];
+        const cx<double> al = G.S(k, k);
         double xn2 = 0.0;
-        for (int i = k + 1; i < M; i++) xn2 += cabs2(F.A[i][k]);
+#pragma unroll 1
+        for (int i = k + 1; i < M; i++) xn2 += cabs2(G.S(i, k));
         const double an = sqrt(cabs2(al) + xn2);
-        F.ok = F.ok && an > 0.0;
+        ok = ok && an > 0.0;
         const double beta = al.re >= 0.0 ? -an : an;
-        F.tauc[k] = cx<double>{(beta - al.re) / beta, al.im / beta};
+        const cx<double> tauc = cx<double>{(beta - al.re) / beta, al.im / beta};
         const cx<double> sc = crecip(cx<double>{al.re - beta, al.im});
-        for (int i = k + 1; i < M; i++) F.A[i][k] = cmul(F.A[i][k], sc);
-        F.dg[k] = beta;
+#pragma unroll 1
+        for (int i = k + 1; i < M; i++) G.setS(i, k, cmul(G.S(i, k), sc));
+        G.setS(k, k, cx<double>{beta, 0.0});
+        TQ.set(k, tauc);
+#pragma unroll 1
         for (int c = k + 1; c < M; c++) {
-            cx<double> wv = F.A[k][c];
-            for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(F.A[i][k], F.A[i][c]));
-            wv = cmul(F.tauc[k], wv);
-            F.A[k][c] = csub(F.A[k][c], wv);
-            for (int i = k + 1; i < M; i++) F.A[i][c] = csub(F.A[i][c], cmul(F.A[i][k], wv));
+            cx<double> wv = G.S(k, c);
+#pragma unroll 1
+            for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(G.S(i, k), G.S(i, c)));
+            wv = cmul(tauc, wv);
+            G.setS(k, c, csub(G.S(k, c), wv));
+#pragma unroll 1
+            for (int i = k + 1; i < M; i++) G.setS(i, c, csub(G.S(i, c), cmul(G.S(i, k), wv)));
         }
     }
+    return ok;
 }
 
-// d = DP^-1 r for r = (rf, rg); returns ||d||_2^2.
+// b <- R^-1 Q^H b (b: M entries of a per-thread array); returns ||b||^2 afterwards.
 template <int M>
-__device__ double fac_apply(const Fac64<M> &F, const double *__restrict__ J,
-                            const cx<double> (&rf)[M], const cx<double> (&rg)[M],
-                            cx<double> (&dx)[M], cx<double> (&dy)[M]) {
-    cx<double> q[M], b[M];
-#pragma unroll 1
-    for (int j = 0; j < M; j++) q[j] = cscale(F.iv[j], rg[j]);
+__device__ double eg_schur_solve(const EG<M> &G, const EGVec &b) {
+    const EGVec TQ = G.v(EGLayout<M>::TQ);
 #pragma unroll 1
     for (int k = 0; k < M; k++) {
-        cx<double> acc = rf[k];
-        for (int j = 0; j < M; j++) {
-            const cx<double> px = cmulc(F.ah[j], q[j]), py = cmulc(F.bh[j], q[j]);
-            if (k == j)
-                acc = csub(acc, cadd(cmul(F.Ad[j], px), cmul(F.Bd[j], py)));
-            else
-                acc = csub(acc, cscale(J[k * NPHC_JSTRIDE + j],
-                                       csub(cmul(F.y[k], px), cmul(F.x[k], py))));
-        }
-        b[k] = acc;
-    }
+        cx<double> wv = b.get(k);
 #pragma unroll 1
-    for (int k = 0; k < M; k++) {
-        cx<double> wv = b[k];
-        for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(F.A[i][k], b[i]));
-        wv = cmul(F.tauc[k], wv);
-        b[k] = csub(b[k], wv);
-        for (int i = k + 1; i < M; i++) b[i] = csub(b[i], cmul(F.A[i][k], wv));
-    }
+        for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(G.S(i, k), b.get(i)));
+        wv = cmul(TQ.get(k), wv);
+        b.set(k, csub(b.get(k), wv));
 #pragma unroll 1
-    for (int k = M - 1; k >= 0; k--) {
-        cx<double> acc = b[k];
-        for (int c = k + 1; c < M; c++) acc = csub(acc, cmul(F.A[k][c], b[c]));
-        b[k] = cscale(1.0 / F.dg[k], acc);
+        for (int i = k + 1; i < M; i++) b.set(i, csub(b.get(i), cmul(G.S(i, k), wv)));
     }
     double n2 = 0.0;
 #pragma unroll 1
-    for (int j = 0; j < M; j++) {
-        dx[j] = cadd(cmulc(F.ah[j], q[j]), cmul(F.bh[j], b[j]));
-        dy[j] = csub(cmulc(F.bh[j], q[j]), cmul(F.ah[j], b[j]));
-        n2 += cabs2(dx[j]) + cabs2(dy[j]);
+    for (int k = M - 1; k >= 0; k--) {
+        cx<double> acc = b.get(k);
+#pragma unroll 1
+        for (int c = k + 1; c < M; c++) acc = csub(acc, cmul(G.S(k, c), b.get(c)));
+        acc = cscale(1.0 / G.S(k, k).re, acc);
+        b.set(k, acc);
+        n2 += cabs2(acc);
     }
     return n2;
 }
 
-// beta = ||DP^-1 P||, ||DP^-1||_F and ||P||_inf at (x, y).  Returns false if singular.
+// C_kj (the q_j-coefficient of gradient row k in the frame).
 template <int M>
-__device__ bool xy_beta_invnorm(Fac64<M> &F, const double *__restrict__ J, double &beta,
-                                double &invF, double &res) {
-    cx<double> f[M], g[M], dx[M], dy[M];
-    xy_eval_p_acc<M>(J, F.x, F.y, f, g);
-    res = 0.0;
+__device__ __forceinline__ cx<double> eg_C(const EG<M> &G, const double *__restrict__ J, int k,
+                                           int j) {
+    using L = EGLayout<M>;
+    const cx<double> ah = G.v(L::AH).get(j), bh = G.v(L::BH).get(j);
+    if (k == j)
+        return cadd(cmulc(ah, G.v(L::AD).get(j)), cmulc(bh, G.v(L::BD).get(j)));
+    const double Jkj = J[k * NPHC_JSTRIDE + j];
+    return cscale(Jkj, csub(cmulc(ah, G.v(L::Y).get(k)), cmulc(bh, G.v(L::X).get(k))));
+}
+
+// D <- DP^-1 R (after eg_factor); returns ||D||^2.
+template <int M>
+__device__ double eg_solve(const EG<M> &G, const double *__restrict__ J) {
+    using L = EGLayout<M>;
+    const EGVec R = G.v(L::R), Dv = G.v(L::D), IV = G.v(L::IV), AH = G.v(L::AH), BH = G.v(L::BH);
+    // q_j = iv_j r_gj into D[M + j]; Schur right-hand side r_fk - sum_j C_kj q_j into D[k]
+#pragma unroll 1
+    for (int j = 0; j < M; j++) Dv.set(M + j, cscale(IV.get(j).re, R.get(M + j)));
+#pragma unroll 1
     for (int k = 0; k < M; k++) {
-        res = fmax(res, sqrt(cabs2(f[k])));
-        res = fmax(res, sqrt(cabs2(g[k])));
-        f[k] = cx<double>{-f[k].re, -f[k].im};
-        g[k] = cx<double>{-g[k].re, -g[k].im};
+        cx<double> acc = R.get(k);
+#pragma unroll 1
+        for (int j = 0; j < M; j++) acc = csub(acc, cmul(eg_C<M>(G, J, k, j), Dv.get(M + j)));
+        Dv.set(k, acc);
     }
-    fac_build<M>(F, J);
-    if (!F.ok) return false;
-    beta = sqrt(fac_apply<M>(F, J, f, g, dx, dy));
+    eg_schur_solve<M>(G, Dv);
+    double n2 = 0.0;
+#pragma unroll 1
+    for (int j = 0; j < M; j++) {
+        const cx<double> ah = AH.get(j), bh = BH.get(j), q = Dv.get(M + j), sj = Dv.get(j);
+        const cx<double> dx = cadd(cmulc(ah, q), cmul(bh, sj));
+        const cx<double> dy = csub(cmulc(bh, q), cmul(ah, sj));
+        Dv.set(j, dx);
+        Dv.set(M + j, dy);
+        n2 += cabs2(dx) + cabs2(dy);
+    }
+    return n2;
+}
+
+// ||DP^-1||_F after eg_factor (block formula above); uses D as scratch.
+template <int M>
+__device__ double eg_inv_fro(const EG<M> &G, const double *__restrict__ J) {
+    using L = EGLayout<M>;
+    const EGVec Dv = G.v(L::D), IV = G.v(L::IV);
     double s = 0.0;
 #pragma unroll 1
-    for (int i = 0; i < 2 * M; i++) {
-        for (int k = 0; k < M; k++) {
-            f[k] = cx<double>{i == k ? 1.0 : 0.0, 0.0};
-            g[k] = cx<double>{i == M + k ? 1.0 : 0.0, 0.0};
-        }
-        s += fac_apply<M>(F, J, f, g, dx, dy);
+    for (int j = 0; j < M; j++) s += IV.get(j).re * IV.get(j).re;
+    // columns of S^-1 and of S^-1 C D^-1
+#pragma unroll 1
+    for (int col = 0; col < 2 * M; col++) {
+        const int j = col < M ? col : col - M;
+#pragma unroll 1
+        for (int k = 0; k < M; k++)
+            Dv.set(k, col < M ? cx<double>{k == j ? 1.0 : 0.0, 0.0}
+                              : cscale(IV.get(j).re, eg_C<M>(G, J, k, j)));
+        s += eg_schur_solve<M>(G, Dv);
     }
-    invF = sqrt(s);
+    return sqrt(s);
+}
+
+// beta = ||DP^-1 P||, ||DP^-1||_F and ||P||_inf at (X, Y).  Returns false if singular.
+template <int M>
+__device__ bool eg_beta_invnorm(const EG<M> &G, const double *__restrict__ J, double &beta,
+                                double &invF, double &res) {
+    res = eg_minus_p<M>(G, J);
+    if (!eg_factor<M>(G, J)) return false;
+    beta = sqrt(eg_solve<M>(G, J));
+    invF = eg_inv_fro<M>(G, J);
     return isfinite(beta) && isfinite(invF);
 }
 
@@ -250,111 +316,127 @@ __device__ bool xy_beta_invnorm(Fac64<M> &F, const double *__restrict__ J, doubl
 #define SHORTCUT_TRUST 1e-2
 
 template <int M>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(EG_BLOCK)
     xy_refine_certify_kernel(const __grid_constant__ XYSys S, double tol_sol, double refine_eps,
                              int refine_iters, const EPView ep, const WorkList wl, int shortcut) {
+    using L = EGLayout<M>;
+    extern __shared__ __align__(16) unsigned char egraw[];
+    const EG<M> G{reinterpret_cast<cx<double> *>(egraw) + threadIdx.x};
+    const EGVec X = G.v(L::X), Y = G.v(L::Y), Dv = G.v(L::D);
     const int64_t total = worklist_size(wl, ep.count);
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= total) return;
-    const int64_t e = worklist_entry(wl, i);
     const int64_t cnt = ep.count;
-    const int st = ep.status[e];
-    const bool sc = shortcut && st == NPHC_PATH_HANDOFF;
-    if (!sc) {
-        ep.alpha[e] = INFINITY;
-        ep.beta[e] = INFINITY;
-        ep.gamma[e] = INFINITY;
-        ep.resid[e] = INFINITY;
-        if (st == NPHC_PATH_DIVERGED) {
-            ep.cls[e] = NPHC_END_NONE;
-            return;
-        }
-        if (st != NPHC_PATH_REACHED) {
-            ep.cls[e] = NPHC_END_FAILED;
-            return;
-        }
-    }
     const double *J = S.Jd;
     const double alpha0 = (13.0 - 3.0 * sqrt(17.0)) / 4.0;
-    Fac64<M> F;
-    for (int k = 0; k < M; k++) {
-        F.x[k] = cx<double>{ep.z_re[k * cnt + e], ep.z_im[k * cnt + e]};
-        F.y[k] = cx<double>{ep.z_re[(M + k) * cnt + e], ep.z_im[(M + k) * cnt + e]};
-    }
-    int cls = NPHC_END_SINGULAR;
-    bool finite = true;
-    // Newton refinement on P
-    for (int it = 0; it < refine_iters; it++) {
-        cx<double> f[M], g[M], dx[M], dy[M];
-        xy_eval_p_acc<M>(J, F.x, F.y, f, g);
+    for (int64_t i = (int64_t)blockIdx.x * EG_BLOCK + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * EG_BLOCK) {
+        const int64_t e = worklist_entry(wl, i);
+        const int st = ep.status[e];
+        const bool sc = shortcut && st == NPHC_PATH_HANDOFF;
+        if (!sc) {
+            ep.alpha[e] = INFINITY;
+            ep.beta[e] = INFINITY;
+            ep.gamma[e] = INFINITY;
+            ep.resid[e] = INFINITY;
+            if (st == NPHC_PATH_DIVERGED) {
+                ep.cls[e] = NPHC_END_NONE;
+                continue;
+            }
+            if (st != NPHC_PATH_REACHED) {
+                ep.cls[e] = NPHC_END_FAILED;
+                continue;
+            }
+        }
+#pragma unroll 1
         for (int k = 0; k < M; k++) {
-            f[k] = cx<double>{-f[k].re, -f[k].im};
-            g[k] = cx<double>{-g[k].re, -g[k].im};
+            X.set(k, cx<double>{ep.z_re[k * cnt + e], ep.z_im[k * cnt + e]});
+            Y.set(k, cx<double>{ep.z_re[(M + k) * cnt + e], ep.z_im[(M + k) * cnt + e]});
         }
-        fac_build<M>(F, J);
-        if (!F.ok) break;
-        const double dn = sqrt(fac_apply<M>(F, J, f, g, dx, dy));
-        if (sc && it == 0) {
-            double z0 = 0.0;
-            for (int k = 0; k < M; k++) z0 += cabs2(F.x[k]) + cabs2(F.y[k]);
-            if (!(dn <= SHORTCUT_TRUST * (1.0 + sqrt(z0)))) return;   // not in a basin: untouched
+        int cls = NPHC_END_SINGULAR;
+        bool finite = true, untouched = false;
+        // Newton refinement on P
+#pragma unroll 1
+        for (int it = 0; it < refine_iters; it++) {
+            eg_minus_p<M>(G, J);
+            if (!eg_factor<M>(G, J)) break;
+            const double dn = sqrt(eg_solve<M>(G, J));
+            if (sc && it == 0) {
+                double z0 = 0.0;
+#pragma unroll 1
+                for (int k = 0; k < M; k++) z0 += cabs2(X.get(k)) + cabs2(Y.get(k));
+                if (!(dn <= SHORTCUT_TRUST * (1.0 + sqrt(z0)))) {   // not in a basin
+                    untouched = true;
+                    break;
+                }
+            }
+            double zn = 0.0;
+#pragma unroll 1
+            for (int k = 0; k < M; k++) {
+                const cx<double> xk = cadd(X.get(k), Dv.get(k)), yk = cadd(Y.get(k), Dv.get(M + k));
+                X.set(k, xk);
+                Y.set(k, yk);
+                zn += cabs2(xk) + cabs2(yk);
+            }
+            if (!isfinite(dn) || !isfinite(zn)) {
+                finite = false;
+                break;
+            }
+            if (dn <= refine_eps * (1.0 + sqrt(zn))) break;
         }
-        double zn = 0.0;
-        for (int k = 0; k < M; k++) {
-            F.x[k] = cadd(F.x[k], dx[k]);
-            F.y[k] = cadd(F.y[k], dy[k]);
-            zn += cabs2(F.x[k]) + cabs2(F.y[k]);
+        if (untouched) continue;
+        double beta = INFINITY, invF = INFINITY, res = INFINITY;
+        double alpha = INFINITY, gam = INFINITY;
+        bool real_test = false;
+        if (finite && eg_beta_invnorm<M>(G, J, beta, invF, res)) {
+            gam = invF * S.d2norm;
+            alpha = beta * gam;
+            // Delta_sol relative to the size of the (quadratic) terms: max(1, ||z||_inf^2)
+            double zi = 0.0, im2 = 0.0;
+#pragma unroll 1
+            for (int k = 0; k < M; k++) {
+                const cx<double> xk = X.get(k), yk = Y.get(k);
+                zi = fmax(zi, fmax(sqrt(cabs2(xk)), sqrt(cabs2(yk))));
+                im2 += xk.im * xk.im + yk.im * yk.im;
+            }
+            if (res <= tol_sol * fmax(1.0, zi * zi) && alpha < alpha0) {
+                if (sqrt(im2) > 2.0 * beta)
+                    cls = NPHC_END_NONREAL;
+                else
+                    real_test = true;
+            }
+        } else {
+            beta = INFINITY;
         }
-        if (!isfinite(dn) || !isfinite(zn)) {
-            finite = false;
-            break;
-        }
-        if (dn <= refine_eps * (1.0 + sqrt(zn))) break;
-    }
-    double beta = INFINITY, invF = INFINITY, res = INFINITY;
-    if (finite && xy_beta_invnorm<M>(F, J, beta, invF, res)) {
-        const double gam = invF * S.d2norm, alpha = beta * gam;
+        if (sc && !(real_test || cls == NPHC_END_NONREAL)) continue;   // left for FP64 tracking
         ep.alpha[e] = alpha;
         ep.beta[e] = beta;
         ep.gamma[e] = gam;
-        ep.resid[e] = res;
-        // Delta_sol relative to the size of the (quadratic) terms: max(1, ||z||_inf^2)
-        double zi = 0.0;
-        for (int k = 0; k < M; k++) zi = fmax(zi, fmax(sqrt(cabs2(F.x[k])), sqrt(cabs2(F.y[k]))));
-        if (res <= tol_sol * fmax(1.0, zi * zi) && alpha < alpha0) {
-            double im2 = 0.0;
-            for (int k = 0; k < M; k++) im2 += F.x[k].im * F.x[k].im + F.y[k].im * F.y[k].im;
-            if (sqrt(im2) > 2.0 * beta) {
-                cls = NPHC_END_NONREAL;
-            } else {
-                // real test at Re z
-                Fac64<M> G;
-                for (int k = 0; k < M; k++) {
-                    G.x[k] = cx<double>{F.x[k].re, 0.0};
-                    G.y[k] = cx<double>{F.y[k].re, 0.0};
-                }
-                double br, ir, rr;
-                if (xy_beta_invnorm<M>(G, J, br, ir, rr) && br * ir * S.d2norm < alpha0)
-                    cls = NPHC_END_REAL;
-                else
-                    cls = NPHC_END_UNDECIDED;
-            }
+        ep.resid[e] = finite ? res : INFINITY;
+        if (sc) {
+            ep.status[e] = NPHC_PATH_REACHED;
+            ep.t[e] = 1.0;
         }
-    } else if (finite) {
-        ep.resid[e] = res;
+#pragma unroll 1
+        for (int k = 0; k < M; k++) {
+            const cx<double> xk = X.get(k), yk = Y.get(k);
+            ep.z_re[k * cnt + e] = xk.re;
+            ep.z_im[k * cnt + e] = xk.im;
+            ep.z_re[(M + k) * cnt + e] = yk.re;
+            ep.z_im[(M + k) * cnt + e] = yk.im;
+        }
+        if (real_test) {
+            // the alpha-test at Re z (the refined z is already written out)
+#pragma unroll 1
+            for (int k = 0; k < M; k++) {
+                X.set(k, cx<double>{X.get(k).re, 0.0});
+                Y.set(k, cx<double>{Y.get(k).re, 0.0});
+            }
+            double br, ir, rr;
+            cls = (eg_beta_invnorm<M>(G, J, br, ir, rr) && br * ir * S.d2norm < alpha0)
+                      ? NPHC_END_REAL
+                      : NPHC_END_UNDECIDED;
+        }
+        ep.cls[e] = cls;
     }
-    if (sc) {
-        if (cls != NPHC_END_REAL && cls != NPHC_END_NONREAL && cls != NPHC_END_UNDECIDED) return;
-        ep.status[e] = NPHC_PATH_REACHED;
-        ep.t[e] = 1.0;
-    }
-    for (int k = 0; k < M; k++) {
-        ep.z_re[k * cnt + e] = F.x[k].re;
-        ep.z_im[k * cnt + e] = F.x[k].im;
-        ep.z_re[(M + k) * cnt + e] = F.y[k].re;
-        ep.z_im[(M + k) * cnt + e] = F.y[k].im;
-    }
-    ep.cls[e] = cls;
 }
 
 template <int M>

@@ -52,9 +52,25 @@ cudaError_t NPHC_CAT(launch_xy_refine_certify_m, NPHC_INST_M)(const XYSys &sys, 
                                                              const WorkList &wl, int shortcut,
                                                              cudaStream_t st) {
     if (cap <= 0) return cudaSuccess;
-    const int grid = (int)((cap + 127) / 128);
-    xy_refine_certify_kernel<NPHC_INST_M><<<grid, 128, 0, st>>>(sys, tol_sol, refine_eps,
-                                                               refine_iters, ep, wl, shortcut);
+    constexpr int M = NPHC_INST_M;
+    const size_t smem = eg_smem_per_thread<M>() * EG_BLOCK;
+    auto k = xy_refine_certify_kernel<M>;
+    static bool attr_set = false;   // once per process for this instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, EG_BLOCK, smem);
+    if (e != cudaSuccess) return e;
+    // grid-stride over the entries: at most every SM filled, at most one entry per thread
+    const int64_t need = (cap + EG_BLOCK - 1) / EG_BLOCK;
+    const int64_t full = (int64_t)sms * (per > 0 ? per : 1);
+    const int grid = (int)(need < full ? need : full);
+    k<<<grid, EG_BLOCK, smem, st>>>(sys, tol_sol, refine_eps, refine_iters, ep, wl, shortcut);
     nphc_launch_counter(1);
     return cudaGetLastError();
 }
