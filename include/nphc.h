@@ -151,8 +151,35 @@ nphc_status nphc_xy_couplings(int N, double sigma, const double *g, double eps, 
  * NPHC_EINVAL for N outside [NPHC_MIN_N, NPHC_MAX_N], bad J, or out == NULL. */
 nphc_status nphc_system_create_xy(int N, double sigma, const double *J, nphc_system **out);
 
+/* Largest number of unknowns of a generic quadratic system. */
+#define NPHC_QUAD_MAX_N 12
+
+/* A generic square system of (at most) quadratic polynomials in n unknowns, for the
+ * paper's one-variable example (x^2 - 5, tracked from x^2 - 1, section "Numerical
+ * Polynomial Homotopy Continuation Method") and for tests on systems with known roots:
+ *   P_i(z) = sum over the terms t with eq[t] == i of coef_t * w(va[t]) * w(vb[t]),
+ *   w(k) = z_k for 0 <= k < n, w(-1) = 1,
+ * so a term is a constant (va = vb = -1), linear (one of them -1) or quadratic.  The
+ * homotopy is the one of the XY ring, H = gamma (1-t) Q + t P with Q_i = z_i^2 - 1, over
+ * the 2^n start points z in {+1, -1}^n (path p: z_i = -1 iff bit i of p is set); it is
+ * tracked in FP64 whatever the precision option, then refined, certified (beta, gamma
+ * bound with ||D^2P/2|| <= sqrt(sum_i ||M_i||_F^2), M_i the symmetric matrix of the
+ * quadratic part of P_i) and deduplicated exactly as for the XY ring.  Classification
+ * and stationary points do not apply (nphc_classify and nphc_result_copy_sps return
+ * NPHC_EINVAL; nphc_system_info reports N = 0).
+ *   eq, va, vb (host int32 [nterms]) and coef_re, coef_im (host [nterms]) are copied; the
+ * system keeps the term list in device memory on the current device (freed by
+ * nphc_system_destroy).
+ *   NPHC_EINVAL for n outside [1, NPHC_QUAD_MAX_N], nterms < 1, NULL arrays, an index out
+ * of range or a non-finite coefficient; NPHC_ENOMEM / NPHC_ECUDA when the device copy
+ * fails. */
+nphc_status nphc_system_create_quadratic(int n, int nterms, const int32_t *eq, const int32_t *va,
+                                         const int32_t *vb, const double *coef_re,
+                                         const double *coef_im, nphc_system **out);
+
 /* Dimensions of a system: ring size N, unknowns n = 2(N-1), Bezout number 4^(N-1)
- * (the number of paths).  Any output may be NULL. */
+ * (the number of paths); for a generic quadratic system N = 0, n and 2^n.  Any output
+ * may be NULL. */
 nphc_status nphc_system_info(const nphc_system *sys, int *N, int *n, int64_t *npaths);
 
 /* The couplings of a system (host, N*N row-major). */
@@ -181,7 +208,9 @@ nphc_status nphc_track(const nphc_system *sys, const nphc_options *opt, nphc_pre
 /* FP64 Newton refinement of every selected entry with status NPHC_PATH_REACHED, then
  * the paper's solution tolerance and alpha-theory certification: beta = ||DP^-1 P||,
  * gamma <= ||DP^-1||_F ||D^2P/2||, certified when beta * gamma < (13 - 3 sqrt 17)/4;
- * real when the same test passes at Re z, non-real when ||Im z|| > 2 beta.  Writes z
+ * real when z and Re z share their zero (alpha < 0.03, ||Im z|| < 1/(20 gamma)) and the
+ * same test passes at Re z, otherwise non-real when ||Im z|| > 2 beta, else undecided.
+ * Writes z
  * (refined), cls, alpha, beta, gamma, resid.  Other statuses get NPHC_END_NONE
  * (diverged) or NPHC_END_FAILED.  list / list_count as in nphc_track. */
 nphc_status nphc_refine_certify(const nphc_system *sys, const nphc_options *opt,
@@ -276,6 +305,37 @@ nphc_status nphc_result_copy_sps(const nphc_result *res, int64_t cap, double *th
 nphc_status nphc_result_copy_endpoints(const nphc_result *res, int64_t cap, double *z_re,
                                        double *z_im, int32_t *status, int32_t *cls,
                                        int64_t *n_out);
+
+/* ---------------------------------------------------------------------------------
+ * Batches: many independent systems solved together (the paper's method per system;
+ * batching is a scheduling choice of this library).  Instance i runs the whole method
+ * of nphc_solve_into on one of NPHC_BATCH_STREAMS internal streams, forked from and
+ * joined back to the caller's stream with events, so that small systems fill the GPU
+ * together; deduplication and classification stay per instance.
+ * --------------------------------------------------------------------------------- */
+#define NPHC_BATCH_STREAMS 8
+typedef struct nphc_batch nphc_batch;   /* opaque; owns one nphc_result per instance */
+
+/* A batch over systems[0 .. count-1] (borrowed: they must outlive the batch).  Creates
+ * one result per instance (device memory as nphc_result_create) and the internal streams.
+ * NPHC_EINVAL for count < 1 or a NULL system; NPHC_ENOMEM / NPHC_ECUDA on allocation. */
+nphc_status nphc_batch_create(int count, const nphc_system *const *systems, nphc_batch **out);
+
+/* Solves every instance with its options opts[i] (host array of count), asynchronously
+ * on `stream`: the call returns once the work is enqueued; the caller's stream is
+ * ordered after every instance.  graph = 0: eager launches.  graph != 0: the first solve
+ * of the batch runs eagerly, the next one captures the whole batch (fork, every
+ * instance's launches, join) into one CUDA graph in relaxed capture mode and launches
+ * it, and later solves with the same options replay that graph (new options capture a
+ * new one).  The caller must not capture `stream` itself around this call.
+ * NPHC_EINVAL for NULL arguments or invalid options. */
+nphc_status nphc_batch_solve(nphc_batch *batch, const nphc_options *opts, int graph, void *stream);
+
+/* The result of instance i (borrowed; valid until nphc_batch_destroy).  Read it with
+ * the nphc_result_* calls after the solve (they synchronise on the caller's stream). */
+nphc_status nphc_batch_result(const nphc_batch *batch, int i, const nphc_result **out);
+
+void nphc_batch_destroy(nphc_batch *batch);
 
 /* Device endpoint arrays of a result (valid until nphc_result_destroy). */
 nphc_status nphc_result_endpoints(const nphc_result *res, nphc_endpoints *ep);

@@ -30,7 +30,8 @@
  *     solution tolerance Delta_sol and the real tolerance Delta_R (same section);
  *   - Smale alpha-theory certification (the alphaCertified step of the same section):
  *     beta = ||DP^-1 P||, gamma <= ||DP^-1|| * ||D^2 P / 2||, alpha = beta * gamma <
- *     (13 - 3 sqrt 17)/4, a real test at Re z and a non-real test ||Im z|| > 2 beta;
+ *     (13 - 3 sqrt 17)/4, a real test at Re z (when z and Re z share their zero) and a
+ *     non-real test ||Im z|| > 2 beta;
  *   - theta recovery theta_k = atan2(s_k, c_k) in (-pi, pi], the Hessian of V in
  *     theta_1..theta_{N-1}, its index (number of negative eigenvalues, introduction)
  *     and the energy V (section "A First Application").
@@ -619,21 +620,26 @@ static int refine_certify_one(const qsys *S, double d2, const oracle_cert_opts *
      * 1e-10 would sit below the rounding of their sum */
     double zi = norminf(n, z), scale = zi > 1.0 ? zi * zi : 1.0;
     if (!(res <= o->tol_sol * scale) || !(alpha < o->alpha0)) return OC_SINGULAR;
+    double im = 0;
+    for (int i = 0; i < n; i++) im += cimag(z[i]) * cimag(z[i]);
+    im = sqrt(im);
     /* real test: alpha at x = Re z, a real point of a real system, so that Newton's
-     * iterates from x stay real and converge to a real solution */
-    cplx *x = w->zs;
-    for (int i = 0; i < n; i++) x[i] = creal(z[i]);
-    double beta_r, invF_r;
-    if (!beta_and_inv_norm(S, x, &beta_r, &invF_r, w)) {
-        double ar = beta_r * invF_r * d2;
-        *alpha_re_out = ar;
-        if (ar < o->alpha0) return OC_REAL;
+     * iterates from x stay real and converge to a real solution.  That solution is z's
+     * own when z and x share their associated zero: alpha(z) < 0.03 and
+     * ||z - x|| = ||Im z|| < 1 / (20 gamma(z)) (alpha theory's robust-zero bound) */
+    if (alpha < 0.03 && im < 1.0 / (20.0 * gam)) {
+        cplx *x = w->zs;
+        for (int i = 0; i < n; i++) x[i] = creal(z[i]);
+        double beta_r, invF_r;
+        if (!beta_and_inv_norm(S, x, &beta_r, &invF_r, w)) {
+            double ar = beta_r * invF_r * d2;
+            *alpha_re_out = ar;
+            if (ar < o->alpha0) return OC_REAL;
+        }
     }
     /* non-real test: z and conj(z) have distinct associated solutions when
      * ||z - conj z|| = 2 ||Im z|| > 2 (beta(z) + beta(conj z)) = 4 beta(z) */
-    double im = 0;
-    for (int i = 0; i < n; i++) im += cimag(z[i]) * cimag(z[i]);
-    if (2.0 * sqrt(im) > 4.0 * beta) return OC_NONREAL;
+    if (im > 2.0 * beta) return OC_NONREAL;
     return OC_UNDECIDED;
 }
 

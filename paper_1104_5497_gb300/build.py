@@ -23,6 +23,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 M_RANGE = range(2, 13)          # N = 3 .. 13
 KINDS = {0: "track_f32", 1: "track_f64", 2: "endgame"}
+QUAD_RANGE = range(1, 13)       # generic quadratic systems, n = 1 .. 12 unknowns
 
 
 def _nvcc() -> str:
@@ -40,6 +41,8 @@ def _units():
         for m in M_RANGE:
             units.append(("xy_inst.cu", [f"-DNPHC_INST_M={m}", f"-DNPHC_INST_KIND={kind}"],
                           f"xy_{name}_m{m}.o"))
+    for nv in QUAD_RANGE:
+        units.append(("quad_inst.cu", [f"-DNPHC_QUAD_NV={nv}"], f"quad_n{nv}.o"))
     return units
 
 

@@ -43,19 +43,19 @@ int64_t table_size_for(int64_t count) {
 }
 
 // Device scratch: [queue counters | tracker path state | dedup cell keys | cell list
-// heads | list links | flags].  The tracker state holds three vectors of 2M complex
+// heads | list links | flags].  The tracker state holds three vectors of n complex
 // doubles for each of NPHC_TRACK_MAX_THREADS threads (enough for either precision).
 struct WsLayout {
     size_t queue, state, keys, head, next, inlist, total;
     int64_t tsize;
 };
 
-WsLayout ws_layout(int M, int64_t count) {
+WsLayout ws_layout(int n, int64_t count) {
     WsLayout L;
     L.tsize = table_size_for(count);
     size_t o = 0;
     L.queue = o;  o += align256(64);
-    L.state = o;  o += align256((size_t)3 * 2 * M * NPHC_TRACK_MAX_THREADS * 2 * sizeof(double));
+    L.state = o;  o += align256((size_t)3 * n * NPHC_TRACK_MAX_THREADS * 2 * sizeof(double));
     L.keys = o;   o += align256(sizeof(unsigned long long) * L.tsize * DD_LEVELS);
     L.head = o;   o += align256(sizeof(int32_t) * L.tsize * DD_LEVELS);
     L.next = o;   o += align256(sizeof(int32_t) * count * DD_LEVELS);
@@ -82,10 +82,13 @@ unsigned long long *ws_queue(void *ws, int slot) {
 }  // namespace
 
 struct nphc_system {
-    int N, M, n;
+    int N, M, n;             // a generic quadratic system has N = M = 0
     int64_t npaths;
     std::vector<double> J;   // N x N
     XYSys xs;                // coupling tables; gamma is filled per call
+    bool quad = false;       // generic quadratic system (nphc_system_create_quadratic)
+    QSys qs;                 // its device term list; gamma is filled per call
+    void *qdev = nullptr;    // device allocation holding qs.row and qs.terms
 };
 
 struct nphc_result {
@@ -217,15 +220,96 @@ nphc_status nphc_system_info(const nphc_system *S, int *N, int *n, int64_t *npat
 
 nphc_status nphc_system_couplings(const nphc_system *S, double *J) {
     if (!S || !J) return fail(NPHC_EINVAL, "NULL argument");
+    if (S->quad) return fail(NPHC_EINVAL, "a generic quadratic system has no couplings");
     std::memcpy(J, S->J.data(), sizeof(double) * S->J.size());
     return NPHC_OK;
 }
 
-void nphc_system_destroy(nphc_system *S) { delete S; }
+void nphc_system_destroy(nphc_system *S) {
+    if (!S) return;
+    if (S->qdev) cudaFree(S->qdev);
+    delete S;
+}
+
+nphc_status nphc_system_create_quadratic(int n, int nterms, const int32_t *eq, const int32_t *va,
+                                         const int32_t *vb, const double *coef_re,
+                                         const double *coef_im, nphc_system **out) {
+    if (!out) return fail(NPHC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > NPHC_QUAD_MAX_N) return fail(NPHC_EINVAL, "n outside [1, NPHC_QUAD_MAX_N]");
+    if (nterms < 1 || !eq || !va || !vb || !coef_re || !coef_im)
+        return fail(NPHC_EINVAL, "empty or missing term arrays");
+    // terms sorted by equation (stable), row offsets, ||D^2 P / 2|| from the symmetric
+    // coefficient matrices M_i of the quadratic parts: z^T M_i z
+    std::vector<int32_t> row(n + 1, 0);
+    std::vector<QTerm> terms(nterms);
+    std::vector<std::vector<double>> m2(n, std::vector<double>((size_t)n * n * 2, 0.0));
+    for (int t = 0; t < nterms; t++) {
+        if (eq[t] < 0 || eq[t] >= n) return fail(NPHC_EINVAL, "term equation index out of range");
+        if (va[t] < -1 || va[t] >= n || vb[t] < -1 || vb[t] >= n)
+            return fail(NPHC_EINVAL, "term variable index out of range");
+        if (!std::isfinite(coef_re[t]) || !std::isfinite(coef_im[t]))
+            return fail(NPHC_EINVAL, "term coefficient not finite");
+        row[eq[t] + 1]++;
+    }
+    for (int i = 0; i < n; i++) row[i + 1] += row[i];
+    std::vector<int32_t> fill(row.begin(), row.end() - 1);
+    for (int t = 0; t < nterms; t++) {
+        QTerm q;
+        q.a = va[t];
+        q.b = vb[t];
+        q.cre = coef_re[t];
+        q.cim = coef_im[t];
+        terms[fill[eq[t]]++] = q;
+        if (q.a >= 0 && q.b >= 0) {
+            std::vector<double> &Mi = m2[eq[t]];
+            const double h = q.a == q.b ? 1.0 : 0.5;
+            for (int rep = 0; rep < (q.a == q.b ? 1 : 2); rep++) {
+                const size_t k = rep == 0 ? ((size_t)q.a * n + q.b) : ((size_t)q.b * n + q.a);
+                Mi[2 * k] += h * q.cre;
+                Mi[2 * k + 1] += h * q.cim;
+            }
+        }
+    }
+    double d2 = 0.0;
+    for (int i = 0; i < n; i++)
+        for (double v : m2[i]) d2 += v * v;
+    nphc_system *S = new (std::nothrow) nphc_system;
+    if (!S) return fail(NPHC_ENOMEM, "host allocation");
+    S->N = 0;
+    S->M = 0;
+    S->n = n;
+    S->npaths = (int64_t)1 << n;
+    std::memset(&S->xs, 0, sizeof(S->xs));
+    S->quad = true;
+    const size_t rbytes = align256(sizeof(int32_t) * (n + 1));
+    const size_t bytes = rbytes + sizeof(QTerm) * nterms;
+    if (cudaMalloc(&S->qdev, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete S;
+        return fail(NPHC_ENOMEM, "device allocation for the term list");
+    }
+    char *d = static_cast<char *>(S->qdev);
+    cudaError_t e = cudaMemcpy(d, row.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d + rbytes, terms.data(), sizeof(QTerm) * nterms, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        nphc_system_destroy(S);
+        return fail(NPHC_ECUDA, std::string("term list upload: ") + cudaGetErrorString(e));
+    }
+    S->qs.n = n;
+    S->qs.row = reinterpret_cast<const int32_t *>(d);
+    S->qs.terms = reinterpret_cast<const QTerm *>(d + rbytes);
+    S->qs.gre = 1.0;
+    S->qs.gim = 0.0;
+    S->qs.d2norm = std::sqrt(d2);
+    *out = S;
+    return NPHC_OK;
+}
 
 nphc_status nphc_workspace_size(const nphc_system *S, int64_t count, size_t *bytes) {
     if (!S || !bytes || count < 0) return fail(NPHC_EINVAL, "invalid argument");
-    *bytes = ws_layout(S->M, count).total;
+    *bytes = ws_layout(S->n, count).total;
     return NPHC_OK;
 }
 
@@ -244,6 +328,13 @@ nphc_status check_opt(const nphc_options *o) {
           o->refine_iters >= 0))
         return fail(NPHC_EINVAL, "options out of range");
     return NPHC_OK;
+}
+
+QSys quad_with_gamma(const nphc_system *S, const nphc_options *o) {
+    QSys q = S->qs;
+    q.gre = o->gamma_re;
+    q.gim = o->gamma_im;
+    return q;
 }
 
 XYSys sys_with_gamma(const nphc_system *S, const nphc_options *o) {
@@ -295,16 +386,17 @@ EPView view(const nphc_endpoints *e) {
 nphc_status track_impl(const nphc_system *S, const nphc_options *o, nphc_precision prec,
                        const nphc_endpoints *ep, const int32_t *list, const int32_t *list_count,
                        bool resume, bool accumulate, void *ws, int queue_slot, cudaStream_t st) {
-    const bool f32 = prec == NPHC_PREC_MIXED;
+    const bool f32 = prec == NPHC_PREC_MIXED && !S->quad;   // generic systems: FP64
     const XYSys xs = sys_with_gamma(S, o);
     XYCtl ctl = make_ctl(o, f32, resume, accumulate);
-    // short FP64 lists (hand-offs, re-tracks) run one path per warp, spread over every SM
+    // FP64 lists (hand-offs, re-tracks) spread over every SM: ceil(list / warps) paths
+    // per warp, up to 32
     ctl.sparse = (!f32 && list != nullptr) ? 1 : 0;
     WorkList wl;
     wl.list = list;
     wl.list_count = list_count;
     wl.queue = ws_queue(ws, queue_slot);
-    wl.state = static_cast<char *>(ws) + ws_layout(S->M, 0).state;
+    wl.state = static_cast<char *>(ws) + ws_layout(S->n, 0).state;
     wl.state_threads = NPHC_TRACK_MAX_THREADS;
     NPHC_CK(cudaMemsetAsync(wl.queue, 0, sizeof(unsigned long long), st));
     int grid = 0;
@@ -315,7 +407,9 @@ nphc_status track_impl(const nphc_system *S, const nphc_options *o, nphc_precisi
         grid = sms * o->blocks_per_sm;
     }
     const EPView v = view(ep);
-    if (f32)
+    if (S->quad)
+        NPHC_CK(launch_quad_track(S->n, quad_with_gamma(S, o), ctl, v, wl, 0, st));
+    else if (f32)
         NPHC_CK(launch_xy_track_f32(S->M, xs, ctl, v, wl, 0, grid, st));
     else
         NPHC_CK(launch_xy_track_f64(S->M, xs, ctl, v, wl, 0, 0, st));
@@ -346,7 +440,7 @@ nphc_status nphc_track(const nphc_system *S, const nphc_options *o, nphc_precisi
     if ((s = check_opt(o)) != NPHC_OK) return s;
     if (prec != NPHC_PREC_FP64 && prec != NPHC_PREC_MIXED) return fail(NPHC_EINVAL, "precision");
     if ((list == nullptr) != (list_count == nullptr)) return fail(NPHC_EINVAL, "list without count");
-    if (!ws || ws_bytes < ws_layout(S->M, ep->count).total) return fail(NPHC_EINVAL, "workspace too small");
+    if (!ws || ws_bytes < ws_layout(S->n, ep->count).total) return fail(NPHC_EINVAL, "workspace too small");
     return track_impl(S, o, prec, ep, list, list_count, resume != 0, resume != 0, ws, 0,
                       (cudaStream_t)stream);
 }
@@ -364,8 +458,14 @@ nphc_status nphc_refine_certify(const nphc_system *S, const nphc_options *o,
     wl.queue = nullptr;
     wl.state = nullptr;
     wl.state_threads = 0;
-    NPHC_CK(launch_xy_refine_certify(S->M, sys_with_gamma(S, o), o->tol_sol, o->refine_eps,
-                                     o->refine_iters, view(ep), ep->count, wl, 0, (cudaStream_t)stream));
+    if (S->quad)
+        NPHC_CK(launch_quad_refine_certify(S->n, quad_with_gamma(S, o), o->tol_sol, o->refine_eps,
+                                           o->refine_iters, view(ep), ep->count, wl,
+                                           (cudaStream_t)stream));
+    else
+        NPHC_CK(launch_xy_refine_certify(S->M, sys_with_gamma(S, o), o->tol_sol, o->refine_eps,
+                                         o->refine_iters, view(ep), ep->count, wl, 0,
+                                         (cudaStream_t)stream));
     return NPHC_OK;
 }
 
@@ -376,7 +476,7 @@ nphc_status nphc_dedup(const nphc_system *S, const nphc_options *o, const nphc_e
     if ((s = check_ep(S, ep, true)) != NPHC_OK) return s;
     (void)o;
     if ((dup_list == nullptr) != (dup_count == nullptr)) return fail(NPHC_EINVAL, "list without count");
-    const WsLayout L = ws_layout(S->M, ep->count);
+    const WsLayout L = ws_layout(S->n, ep->count);
     if (!ws || ws_bytes < L.total) return fail(NPHC_EINVAL, "workspace too small");
     NPHC_CK(launch_dedup(view(ep), S->n, kDedupDelta, dedup_scratch(ws, L), dup_list, dup_count,
                          (cudaStream_t)stream));
@@ -388,6 +488,7 @@ nphc_status nphc_classify(const nphc_system *S, const nphc_endpoints *ep, double
     nphc_status s;
     if ((s = check_ep(S, ep, true)) != NPHC_OK) return s;
     if (!theta || !index || !energy) return fail(NPHC_EINVAL, "output arrays missing");
+    if (S->quad) return fail(NPHC_EINVAL, "classification needs an XY system");
     XYSys xs = S->xs;
     NPHC_CK(launch_xy_classify(S->M, xs, view(ep), theta, index, energy, min_abs_eig,
                                (cudaStream_t)stream));
@@ -399,7 +500,7 @@ nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
     *out = nullptr;
     const int64_t P = S->npaths;
     const int n = S->n, M = S->M;
-    const WsLayout L = ws_layout(M, P);
+    const WsLayout L = ws_layout(n, P);
     // sub-allocation plan
     std::vector<size_t> sz = {
         sizeof(int64_t) * P,            // 0 path
@@ -514,13 +615,30 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
     const nphc_endpoints *ep = &R->ep;
     const EPView v = view(ep);
     const XYSys xs = sys_with_gamma(S, o);
-    const WsLayout L = ws_layout(R->M, R->P);
+    const WsLayout L = ws_layout(R->n, R->P);
     const DedupScratch dsc = dedup_scratch(R->ws, L);
     R->solved = false;
     const int64_t launches0 = nphc_launch_counter(0);
     NPHC_CK(cudaMemsetAsync(R->flags, 0, sizeof(int32_t) * R->P, st));
     NPHC_CK(cudaMemsetAsync(R->lcount, 0, sizeof(int32_t) * 8, st));
     const bool mixed = o->precision == NPHC_PREC_MIXED;
+    if (S->quad) {
+        // generic quadratic system: FP64 tracking, refinement, certification, dedup; no
+        // classification (index -1 everywhere)
+        if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, nullptr, nullptr, false, false, R->ws, 0, st)))
+            return s;
+        NPHC_CK(launch_compact(v, PRED_REACHED, R->flags, R->list[3], R->lcount + 3, st));
+        WorkList l3 = {R->list[3], R->lcount + 3, nullptr, nullptr, 0};
+        NPHC_CK(launch_quad_refine_certify(S->n, quad_with_gamma(S, o), o->tol_sol, o->refine_eps,
+                                           o->refine_iters, v, R->P, l3, st));
+        NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st));
+        NPHC_CK(cudaMemsetAsync(R->index, 0xff, sizeof(int32_t) * R->P, st));
+        NPHC_CK(launch_counts(v, R->flags, R->index, R->counts, st));
+        R->stream = st;
+        R->solved = true;
+        R->launches = nphc_launch_counter(0) - launches0;
+        return NPHC_OK;
+    }
     if (mixed) {
         // FP32 pass over every path
         if ((s = track_impl(S, o, NPHC_PREC_MIXED, ep, nullptr, nullptr, false, false, R->ws, 0, st)))
@@ -538,7 +656,8 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
         WorkList l3 = {R->list[3], R->lcount + 3, nullptr, nullptr, 0};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
                                          R->P, l3, 0, st));
-        // FP64 re-track of FP32 endpoints that did not certify
+        // FP64 re-track from t = 0 of FP32 endpoints that did not certify and of hand-offs
+        // whose continuation did not end certified
         NPHC_CK(launch_compact(v, PRED_UNCERTIFIED_FP32, R->flags, R->list[1], R->lcount + 1, st));
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[1], R->lcount + 1, false, true, R->ws, 2, st)))
             return s;
@@ -603,6 +722,7 @@ nphc_status nphc_result_copy_sps(const nphc_result *R, int64_t cap, double *thet
                                  int32_t *index, double *alpha, int64_t *path, int64_t *n_out) {
     if (!R || !n_out || cap < 0) return fail(NPHC_EINVAL, "invalid argument");
     if (!R->solved) return fail(NPHC_ESTATE, "no solve on this result");
+    if (R->M == 0) return fail(NPHC_EINVAL, "a generic quadratic system has no stationary points; copy its endpoints");
     cudaStream_t st = R->stream;
     NPHC_CK(launch_real_list(view(&R->ep), R->real_list, R->lcount + 4, st));
     NPHC_CK(launch_gather_sps(view(&R->ep), R->M, R->real_list, R->lcount + 4, R->P, R->theta,
@@ -766,3 +886,160 @@ nphc_status nphc_dedup_noalloc(const nphc_system *S, const nphc_options *o,
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------- batch --
+// Independent systems solved together: instance i runs the whole method
+// (nphc_solve_into) on internal stream i % NPHC_BATCH_STREAMS, forked from the caller's
+// stream and joined back with events, so that small instances fill the GPU together.
+// The first solve of a batch runs eagerly (it also sets each kernel's attributes once);
+// with graph != 0 the second solve captures the whole fork / solve / join sequence into
+// one CUDA graph (relaxed capture mode), and later solves replay it.
+struct nphc_batch {
+    std::vector<const nphc_system *> sys;
+    std::vector<nphc_result *> res;
+    std::vector<nphc_options> opts;   // options of the captured solve
+    cudaStream_t streams[NPHC_BATCH_STREAMS] = {};
+    cudaStream_t origin = nullptr;    // the captured stream (the caller's may be the legacy one)
+    cudaEvent_t start = nullptr, done = nullptr;
+    cudaEvent_t fork = nullptr, join[NPHC_BATCH_STREAMS] = {};
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int solves = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+nphc_status batch_enqueue(nphc_batch *B, const nphc_options *opts, cudaStream_t st) {
+    NPHC_CK(cudaEventRecord(B->fork, st));
+    for (int k = 0; k < NPHC_BATCH_STREAMS; k++) NPHC_CK(cudaStreamWaitEvent(B->streams[k], B->fork, 0));
+    for (size_t i = 0; i < B->sys.size(); i++) {
+        nphc_status s = nphc_solve_into(B->sys[i], &opts[i], B->res[i],
+                                        B->streams[i % NPHC_BATCH_STREAMS]);
+        if (s != NPHC_OK) return s;
+    }
+    for (int k = 0; k < NPHC_BATCH_STREAMS; k++) {
+        NPHC_CK(cudaEventRecord(B->join[k], B->streams[k]));
+        NPHC_CK(cudaStreamWaitEvent(st, B->join[k], 0));
+    }
+    return NPHC_OK;
+}
+
+bool same_options(const std::vector<nphc_options> &a, const nphc_options *b) {
+    for (size_t i = 0; i < a.size(); i++)
+        if (std::memcmp(&a[i], &b[i], sizeof(nphc_options)) != 0) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+void nphc_batch_destroy(nphc_batch *B) {
+    if (!B) return;
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    if (B->graph) cudaGraphDestroy(B->graph);
+    for (int k = 0; k < NPHC_BATCH_STREAMS; k++) {
+        if (B->streams[k]) {
+            cudaStreamSynchronize(B->streams[k]);
+            cudaStreamDestroy(B->streams[k]);
+        }
+        if (B->join[k]) cudaEventDestroy(B->join[k]);
+    }
+    if (B->fork) cudaEventDestroy(B->fork);
+    if (B->origin) {
+        cudaStreamSynchronize(B->origin);
+        cudaStreamDestroy(B->origin);
+    }
+    if (B->start) cudaEventDestroy(B->start);
+    if (B->done) cudaEventDestroy(B->done);
+    for (nphc_result *R : B->res) nphc_result_destroy(R);
+    delete B;
+}
+
+nphc_status nphc_batch_create(int count, const nphc_system *const *systems, nphc_batch **out) {
+    if (!out) return fail(NPHC_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !systems) return fail(NPHC_EINVAL, "empty batch");
+    for (int i = 0; i < count; i++)
+        if (!systems[i]) return fail(NPHC_EINVAL, "NULL system in the batch");
+    nphc_batch *B = new (std::nothrow) nphc_batch;
+    if (!B) return fail(NPHC_ENOMEM, "host allocation");
+    auto bail = [&](nphc_status s) {
+        nphc_batch_destroy(B);
+        return s;
+    };
+    for (int k = 0; k < NPHC_BATCH_STREAMS; k++) {
+        if (cudaStreamCreateWithFlags(&B->streams[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->join[k], cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(NPHC_ECUDA, "batch streams"));
+    }
+    if (cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->start, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&B->done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&B->origin, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(NPHC_ECUDA, "batch events"));
+    for (int i = 0; i < count; i++) {
+        nphc_result *R = nullptr;
+        nphc_status s = nphc_result_create(systems[i], &R);
+        if (s != NPHC_OK) return bail(s);
+        B->sys.push_back(systems[i]);
+        B->res.push_back(R);
+    }
+    *out = B;
+    return NPHC_OK;
+}
+
+nphc_status nphc_batch_solve(nphc_batch *B, const nphc_options *opts, int graph, void *stream) {
+    if (!B || !opts) return fail(NPHC_EINVAL, "NULL argument");
+    for (size_t i = 0; i < B->sys.size(); i++) {
+        nphc_status s = check_opt(&opts[i]);
+        if (s != NPHC_OK) return s;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (B->exec && !same_options(B->opts, opts)) {   // new options: capture again
+        cudaGraphExecDestroy(B->exec);
+        cudaGraphDestroy(B->graph);
+        B->exec = nullptr;
+        B->graph = nullptr;
+    }
+    if (graph && B->exec) {
+        NPHC_CK(cudaGraphLaunch(B->exec, st));
+        nphc_launch_counter(B->launches);
+    } else if (graph && B->solves > 0) {
+        // capture on the batch's own stream: the graph then runs on the caller's
+        NPHC_CK(cudaEventRecord(B->start, st));
+        NPHC_CK(cudaStreamWaitEvent(B->origin, B->start, 0));
+        NPHC_CK(cudaStreamSynchronize(B->origin));
+        const int64_t l0 = nphc_launch_counter(0);
+        NPHC_CK(cudaStreamBeginCapture(B->origin, cudaStreamCaptureModeRelaxed));
+        nphc_status s = batch_enqueue(B, opts, B->origin);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(B->origin, &g);
+        if (s != NPHC_OK) {
+            if (g) cudaGraphDestroy(g);
+            return s;
+        }
+        NPHC_CK(e);
+        B->graph = g;
+        NPHC_CK(cudaGraphInstantiate(&B->exec, g, 0));
+        B->launches = nphc_launch_counter(0) - l0;
+        B->opts.assign(opts, opts + B->sys.size());
+        NPHC_CK(cudaGraphLaunch(B->exec, st));
+    } else {
+        nphc_status s = batch_enqueue(B, opts, st);
+        if (s != NPHC_OK) return s;
+    }
+    for (nphc_result *R : B->res) R->stream = st;   // results are read after the join
+    B->solves++;
+    return NPHC_OK;
+}
+
+nphc_status nphc_batch_result(const nphc_batch *B, int i, const nphc_result **out) {
+    if (!B || !out || i < 0 || i >= (int)B->res.size()) return fail(NPHC_EINVAL, "invalid argument");
+    *out = B->res[i];
+    return NPHC_OK;
+}
+
+}  // extern "C"
+

@@ -132,7 +132,7 @@ struct XYCtl {                              // step control of one tracking call
     int handoff;                            // 1: stops become NPHC_PATH_HANDOFF (FP32 pass)
     int resume;                             // 1: continue from (z, t, h) of the entry
     int accumulate;                         // 1: add to the entry's step/solve counters
-    int sparse;                             // 1: one path per warp (lane 0 only)
+    int sparse;                             // 1: spread a short list, ceil(list / warps) paths per warp
     int crawl_steps;                        // near t = 1, 1 - t must halve within this many
                                             // accepted steps (0: no crawl test)
 };
@@ -164,6 +164,21 @@ __device__ __forceinline__ int64_t worklist_entry(const WorkList &w, int64_t i) 
     return w.list ? (int64_t)w.list[i] : i;
 }
 
+// A generic quadratic system (quad.cuh): P_i(z) = sum of c w(a) w(b), w(-1) = 1, terms
+// sorted by equation.
+struct QTerm {
+    int32_t a, b;      // variable indices, -1 for the constant 1
+    double cre, cim;   // coefficient
+};
+
+struct QSys {
+    int n;
+    const int32_t *row;    // [n + 1] term offsets per equation (device)
+    const QTerm *terms;    // [row[n]] (device)
+    double gre, gim;       // gamma
+    double d2norm;         // ||D^2 P / 2|| bound
+};
+
 // ------------------------------------------------------ kernel launchers --
 // Implemented per precision / ring size in the .cu files; return cudaGetLastError().
 cudaError_t launch_xy_track_f32(int M, const XYSys &sys, const XYCtl &ctl, const EPView &ep,
@@ -176,6 +191,11 @@ cudaError_t launch_xy_refine_certify(int M, const XYSys &sys, double tol_sol, do
 cudaError_t launch_xy_classify(int M, const XYSys &sys, const EPView &ep, double *theta,
                                int32_t *index, double *energy, double *min_eig,
                                cudaStream_t st);
+cudaError_t launch_quad_track(int n, const QSys &sys, const XYCtl &ctl, const EPView &ep,
+                              const WorkList &wl, int grid, cudaStream_t st);
+cudaError_t launch_quad_refine_certify(int n, const QSys &sys, double tol_sol, double refine_eps,
+                                       int refine_iters, const EPView &ep, int64_t cap,
+                                       const WorkList &wl, cudaStream_t st);
 // Host-side count of kernel launches made by this library (for the result counters).
 int64_t nphc_launch_counter(int64_t add);
 int xy_track_f32_block(int M);

@@ -19,7 +19,14 @@ __global__ void compact_kernel(const EPView ep, int pred, int32_t *flags, int32_
         take = ep.status[e] == NPHC_PATH_HANDOFF;
         if (take) flags[e] |= FLAG_FP64_CONTINUED;
     } else if (pred == PRED_UNCERTIFIED_FP32) {
-        take = ep.cls[e] == NPHC_END_SINGULAR && !(flags[e] & (FLAG_FP64_CONTINUED | FLAG_RETRACKED));
+        // FP32 endpoints that do not certify, and FP32 hand-offs whose FP64 continuation
+        // did not end certified (the FP32 pass stalled on them, so its trajectory near the
+        // hand-off is not trusted): both are tracked again from t = 0 in FP64
+        const int c = ep.cls[e], f = flags[e];
+        const bool certified = c == NPHC_END_REAL || c == NPHC_END_NONREAL || c == NPHC_END_UNDECIDED;
+        take = !(f & FLAG_RETRACKED) &&
+               ((c == NPHC_END_SINGULAR && !(f & FLAG_FP64_CONTINUED)) ||
+                ((f & FLAG_FP64_CONTINUED) && !certified));
         if (take) flags[e] |= FLAG_RETRACKED;
     } else if (pred == PRED_REACHED) {
         // endpoints to refine; every other path gets its final class here

@@ -34,3 +34,18 @@ cudaError_t launch_xy_classify(int M, const XYSys &sys, const EPView &ep, double
 
 int xy_track_f32_block(int M) { (void)M; return NPHC_TRACK_BLOCK; }
 int xy_track_f64_block(int M) { (void)M; return NPHC_TRACK_BLOCK; }
+
+cudaError_t launch_quad_track(int n, const QSys &sys, const XYCtl &ctl, const EPView &ep,
+                              const WorkList &wl, int grid, cudaStream_t st) {
+#define C(NN) case NN: return launch_quad_track_n##NN(sys, ctl, ep, wl, grid, st);
+    switch (n) { NPHC_FOR_EACH_QN(C) default: return cudaErrorInvalidValue; }
+#undef C
+}
+
+cudaError_t launch_quad_refine_certify(int n, const QSys &sys, double tol_sol, double refine_eps,
+                                       int refine_iters, const EPView &ep, int64_t cap,
+                                       const WorkList &wl, cudaStream_t st) {
+#define C(NN) case NN: return launch_quad_refine_certify_n##NN(sys, tol_sol, refine_eps, refine_iters, ep, cap, wl, st);
+    switch (n) { NPHC_FOR_EACH_QN(C) default: return cudaErrorInvalidValue; }
+#undef C
+}

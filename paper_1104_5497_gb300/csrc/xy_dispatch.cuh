@@ -23,3 +23,13 @@
                                          double *, double *, cudaStream_t);
 NPHC_FOR_EACH_M(NPHC_DECL)
 #undef NPHC_DECL
+
+#define NPHC_FOR_EACH_QN(X) X(1) X(2) X(3) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
+#define NPHC_QDECL(NN)                                                                        \
+    cudaError_t launch_quad_track_n##NN(const QSys &, const XYCtl &, const EPView &,         \
+                                        const WorkList &, int, cudaStream_t);                 \
+    cudaError_t launch_quad_refine_certify_n##NN(const QSys &, double, double, int,          \
+                                                 const EPView &, int64_t, const WorkList &,  \
+                                                 cudaStream_t);
+NPHC_FOR_EACH_QN(NPHC_QDECL)
+#undef NPHC_QDECL

@@ -7,9 +7,10 @@
 //   alpha-theory certification (the alphaCertified step of the same section):
 //     beta = ||DP^-1 P||_2, gamma <= ||DP^-1||_F ||D^2 P / 2|| (P is quadratic, so
 //     D^k P = 0 for k >= 3 and Smale's gamma is ||DP^-1 D^2P/2|| exactly), certified when
-//     alpha = beta gamma < (13 - 3 sqrt 17) / 4; real when the test passes at Re z (a real
-//     point of a real system: Newton's iterates stay real), non-real when
-//     ||z - conj z|| > 2 (beta(z) + beta(conj z)), i.e. ||Im z|| > 2 beta;
+//     alpha = beta gamma < (13 - 3 sqrt 17) / 4; real when z and Re z share their zero
+//     (alpha < 0.03 and ||Im z|| < 1 / (20 gamma)) and the test passes at Re z (a real
+//     point of a real system: Newton's iterates stay real), otherwise non-real when
+//     ||z - conj z|| > 2 (beta(z) + beta(conj z)), i.e. ||Im z|| > 2 beta, else undecided;
 //   classification of real stationary points (introduction and section "A First
 //     Application"): theta_k = atan2(s_k, c_k) in (-pi, pi], the Hessian of
 //     V = sum_{i<j} J_ij (1 - cos(theta_i - theta_j)) in theta_1..theta_M, its number of
@@ -138,13 +139,49 @@ __device__ double eg_minus_p(const EG<M> &G, const double *__restrict__ J) {
     return res;
 }
 
+// Householder QR of the M x M matrix G.S in place: R above the diagonal with a real
+// diagonal (stored as (beta, 0)), the reflectors (1, v) below it, conj(tau) in TQ.
+// Returns false when the matrix is singular.
+template <int M>
+__device__ bool eg_qr(const EG<M> &G) {
+    const EGVec TQ = G.v(EGLayout<M>::TQ);
+    bool ok = true;
+#pragma unroll 1
+    for (int k = 0; k < M; k++) {
+        const cx<double> al = G.S(k, k);
+        double xn2 = 0.0;
+#pragma unroll 1
+        for (int i = k + 1; i < M; i++) xn2 += cabs2(G.S(i, k));
+        const double an = sqrt(cabs2(al) + xn2);
+        ok = ok && an > 0.0;
+        const double beta = al.re >= 0.0 ? -an : an;
+        const cx<double> tauc = cx<double>{(beta - al.re) / beta, al.im / beta};
+        const cx<double> sc = crecip(cx<double>{al.re - beta, al.im});
+#pragma unroll 1
+        for (int i = k + 1; i < M; i++) G.setS(i, k, cmul(G.S(i, k), sc));
+        G.setS(k, k, cx<double>{beta, 0.0});
+        TQ.set(k, tauc);
+#pragma unroll 1
+        for (int c = k + 1; c < M; c++) {
+            cx<double> wv = G.S(k, c);
+#pragma unroll 1
+            for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(G.S(i, k), G.S(i, c)));
+            wv = cmul(tauc, wv);
+            G.setS(k, c, csub(G.S(k, c), wv));
+#pragma unroll 1
+            for (int i = k + 1; i < M; i++) G.setS(i, c, csub(G.S(i, c), cmul(G.S(i, k), wv)));
+        }
+    }
+    return ok;
+}
+
 // Frames, diagonal Jacobian entries and the Householder QR of S at the point (X, Y).
 // Returns false when S is singular.
 template <int M>
 __device__ bool eg_factor(const EG<M> &G, const double *__restrict__ J) {
     using L = EGLayout<M>;
     const EGVec X = G.v(L::X), Y = G.v(L::Y), AH = G.v(L::AH), BH = G.v(L::BH), IV = G.v(L::IV),
-                AD = G.v(L::AD), BD = G.v(L::BD), TQ = G.v(L::TQ);
+                AD = G.v(L::AD), BD = G.v(L::BD);
 #pragma unroll 1
     for (int j = 0; j < M; j++) {
         const double *Jj = J + j * NPHC_JSTRIDE;
@@ -178,34 +215,7 @@ __device__ bool eg_factor(const EG<M> &G, const double *__restrict__ J) {
             G.setS(k, j, e);
         }
     }
-    bool ok = true;
-#pragma unroll 1
-    for (int k = 0; k < M; k++) {
-        const cx<double> al = G.S(k, k);
-        double xn2 = 0.0;
-#pragma unroll 1
-        for (int i = k + 1; i < M; i++) xn2 += cabs2(G.S(i, k));
-        const double an = sqrt(cabs2(al) + xn2);
-        ok = ok && an > 0.0;
-        const double beta = al.re >= 0.0 ? -an : an;
-        const cx<double> tauc = cx<double>{(beta - al.re) / beta, al.im / beta};
-        const cx<double> sc = crecip(cx<double>{al.re - beta, al.im});
-#pragma unroll 1
-        for (int i = k + 1; i < M; i++) G.setS(i, k, cmul(G.S(i, k), sc));
-        G.setS(k, k, cx<double>{beta, 0.0});
-        TQ.set(k, tauc);
-#pragma unroll 1
-        for (int c = k + 1; c < M; c++) {
-            cx<double> wv = G.S(k, c);
-#pragma unroll 1
-            for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(G.S(i, k), G.S(i, c)));
-            wv = cmul(tauc, wv);
-            G.setS(k, c, csub(G.S(k, c), wv));
-#pragma unroll 1
-            for (int i = k + 1; i < M; i++) G.setS(i, c, csub(G.S(i, c), cmul(G.S(i, k), wv)));
-        }
-    }
-    return ok;
+    return eg_qr<M>(G);
 }
 
 // b <- R^-1 Q^H b (b: M entries of a per-thread array); returns ||b||^2 afterwards.
@@ -297,17 +307,6 @@ __device__ double eg_inv_fro(const EG<M> &G, const double *__restrict__ J) {
     return sqrt(s);
 }
 
-// beta = ||DP^-1 P||, ||DP^-1||_F and ||P||_inf at (X, Y).  Returns false if singular.
-template <int M>
-__device__ bool eg_beta_invnorm(const EG<M> &G, const double *__restrict__ J, double &beta,
-                                double &invF, double &res) {
-    res = eg_minus_p<M>(G, J);
-    if (!eg_factor<M>(G, J)) return false;
-    beta = sqrt(eg_solve<M>(G, J));
-    invF = eg_inv_fro<M>(G, J);
-    return isfinite(beta) && isfinite(invF);
-}
-
 // shortcut = 1: entries handed off by the FP32 pass close to t = 1 are refined at t = 1
 // directly (Newton on P from the hand-off point: for a path to a nonsingular solution xi,
 // z(t) = xi + (1 - t) z'(1) + ..., so the point is already in xi's Newton basin).  The
@@ -315,128 +314,211 @@ __device__ bool eg_beta_invnorm(const EG<M> &G, const double *__restrict__ J, do
 // certifies becomes NPHC_PATH_REACHED, any other entry is left untouched.
 #define SHORTCUT_TRUST 1e-2
 
+// The system an endgame kernel works on, as a policy for refine_body: the unknowns
+// (NZ, stored in G's X then Y), -P into R, the factorisation of DP, the Newton step
+// D = DP^-1 R, ||DP^-1||_F and ||D^2 P / 2||.  EGXY: the XY ring (frames + Schur QR).
+template <int M>
+struct EGXY {
+    using Sys = XYSys;
+    static constexpr int DIM = M;        // EG<DIM> storage
+    static constexpr int NZ = 2 * M;
+    static __device__ __forceinline__ cx<double> zget(const EG<M> &G, int k) {
+        return k < M ? G.v(EGLayout<M>::X).get(k) : G.v(EGLayout<M>::Y).get(k - M);
+    }
+    static __device__ __forceinline__ void zset(const EG<M> &G, int k, cx<double> v) {
+        if (k < M) G.v(EGLayout<M>::X).set(k, v);
+        else G.v(EGLayout<M>::Y).set(k - M, v);
+    }
+    static __device__ __forceinline__ double minus_p(const EG<M> &G, const Sys &S) {
+        return eg_minus_p<M>(G, S.Jd);
+    }
+    static __device__ __forceinline__ bool factor(const EG<M> &G, const Sys &S) {
+        return eg_factor<M>(G, S.Jd);
+    }
+    static __device__ __forceinline__ double solve(const EG<M> &G, const Sys &S) {
+        return eg_solve<M>(G, S.Jd);
+    }
+    static __device__ __forceinline__ double inv_fro(const EG<M> &G, const Sys &S) {
+        return eg_inv_fro<M>(G, S.Jd);
+    }
+    static __device__ __forceinline__ double d2norm(const Sys &S) { return S.d2norm; }
+};
+
+// beta = ||DP^-1 P||, ||DP^-1||_F and ||P||_inf at the point in G.  False if singular.
+template <class Q>
+__device__ bool eg_beta_invnorm_p(const EG<Q::DIM> &G, const typename Q::Sys &S, double &beta,
+                                  double &invF, double &res) {
+    res = Q::minus_p(G, S);
+    if (!Q::factor(G, S)) return false;
+    beta = sqrt(Q::solve(G, S));
+    invF = Q::inv_fro(G, S);
+    return isfinite(beta) && isfinite(invF);
+}
+
+// Refinement and certification of entry e.  Returns true when e still needs the
+// alpha-test at Re z (its refined z is already written out; the caller runs the test).
+template <class Q>
+__device__ bool eg_refine_certify_one(const EG<Q::DIM> &G, const typename Q::Sys &S,
+                                      double tol_sol, double refine_eps, int refine_iters,
+                                      const EPView &ep, int64_t e, int shortcut) {
+    constexpr int NZ = Q::NZ;
+    const EGVec Dv = G.v(EGLayout<Q::DIM>::D);
+    const int64_t cnt = ep.count;
+    const double alpha0 = (13.0 - 3.0 * sqrt(17.0)) / 4.0;
+    const int st = ep.status[e];
+    const bool sc = shortcut && st == NPHC_PATH_HANDOFF;
+    if (!sc) {
+        ep.alpha[e] = INFINITY;
+        ep.beta[e] = INFINITY;
+        ep.gamma[e] = INFINITY;
+        ep.resid[e] = INFINITY;
+        if (st == NPHC_PATH_DIVERGED) {
+            ep.cls[e] = NPHC_END_NONE;
+            return false;
+        }
+        if (st != NPHC_PATH_REACHED) {
+            ep.cls[e] = NPHC_END_FAILED;
+            return false;
+        }
+    }
+#pragma unroll 1
+    for (int k = 0; k < NZ; k++) Q::zset(G, k, cx<double>{ep.z_re[k * cnt + e], ep.z_im[k * cnt + e]});
+    int cls = NPHC_END_SINGULAR;
+    bool finite = true;
+    // Newton refinement on P
+#pragma unroll 1
+    for (int it = 0; it < refine_iters; it++) {
+        Q::minus_p(G, S);
+        if (!Q::factor(G, S)) break;
+        const double dn = sqrt(Q::solve(G, S));
+        if (sc && it == 0) {
+            double z0 = 0.0;
+#pragma unroll 1
+            for (int k = 0; k < NZ; k++) z0 += cabs2(Q::zget(G, k));
+            if (!(dn <= SHORTCUT_TRUST * (1.0 + sqrt(z0)))) return false;   // not in a basin
+        }
+        double zn = 0.0;
+#pragma unroll 1
+        for (int k = 0; k < NZ; k++) {
+            const cx<double> zk = cadd(Q::zget(G, k), Dv.get(k));
+            Q::zset(G, k, zk);
+            zn += cabs2(zk);
+        }
+        if (!isfinite(dn) || !isfinite(zn)) {
+            finite = false;
+            break;
+        }
+        if (dn <= refine_eps * (1.0 + sqrt(zn))) break;
+    }
+    double beta = INFINITY, invF = INFINITY, res = INFINITY;
+    double alpha = INFINITY, gam = INFINITY;
+    bool real_test = false;
+    if (finite && eg_beta_invnorm_p<Q>(G, S, beta, invF, res)) {
+        gam = invF * Q::d2norm(S);
+        alpha = beta * gam;
+        // Delta_sol relative to the size of the (quadratic) terms: max(1, ||z||_inf^2)
+        double zi = 0.0, im2 = 0.0;
+#pragma unroll 1
+        for (int k = 0; k < NZ; k++) {
+            const cx<double> zk = Q::zget(G, k);
+            zi = fmax(zi, sqrt(cabs2(zk)));
+            im2 += zk.im * zk.im;
+        }
+        if (res <= tol_sol * fmax(1.0, zi * zi) && alpha < alpha0) {
+            // z and Re z share their associated zero when alpha < 0.03 and
+            // ||Im z|| < 1 / (20 gamma): then the real test at Re z decides (queued)
+            const double im = sqrt(im2);
+            if (alpha < 0.03 && im < 1.0 / (20.0 * gam))
+                real_test = true;
+            else
+                cls = im > 2.0 * beta ? NPHC_END_NONREAL : NPHC_END_UNDECIDED;
+        }
+    } else {
+        beta = INFINITY;
+    }
+    if (sc && !(real_test || cls == NPHC_END_NONREAL || cls == NPHC_END_UNDECIDED))
+        return false;   // left for FP64 tracking
+    ep.alpha[e] = alpha;
+    ep.beta[e] = beta;
+    ep.gamma[e] = gam;
+    ep.resid[e] = finite ? res : INFINITY;
+    if (sc) {
+        ep.status[e] = NPHC_PATH_REACHED;
+        ep.t[e] = 1.0;
+    }
+#pragma unroll 1
+    for (int k = 0; k < NZ; k++) {
+        const cx<double> zk = Q::zget(G, k);
+        ep.z_re[k * cnt + e] = zk.re;
+        ep.z_im[k * cnt + e] = zk.im;
+    }
+    if (!real_test) ep.cls[e] = cls;
+    return real_test;
+}
+
+// The alpha-test at Re z of a certified entry e that shares its zero with Re z: real
+// when it passes there; otherwise non-real when ||Im z|| > 2 beta (z and conj z then
+// have distinct zeros), else undecided.
+template <class Q>
+__device__ void eg_real_test(const EG<Q::DIM> &G, const typename Q::Sys &S, const EPView &ep,
+                             int64_t e) {
+    const int64_t cnt = ep.count;
+    const double alpha0 = (13.0 - 3.0 * sqrt(17.0)) / 4.0;
+    double im2 = 0.0;
+#pragma unroll 1
+    for (int k = 0; k < Q::NZ; k++) {
+        const double yi = ep.z_im[k * cnt + e];
+        im2 += yi * yi;
+        Q::zset(G, k, cx<double>{ep.z_re[k * cnt + e], 0.0});
+    }
+    double br, ir, rr;
+    if (eg_beta_invnorm_p<Q>(G, S, br, ir, rr) && br * ir * Q::d2norm(S) < alpha0)
+        ep.cls[e] = NPHC_END_REAL;
+    else
+        ep.cls[e] = sqrt(im2) > 2.0 * ep.beta[e] ? NPHC_END_NONREAL : NPHC_END_UNDECIDED;
+}
+
+// One warp per block.  Entries are taken 32 at a time; the few that need the real test
+// (about one in thirty at N = 10) go to a per-warp queue that is drained 32 at a time,
+// so that the test runs on full warps instead of costing most warps a pass with one
+// active lane.
+template <class Q>
+__device__ __forceinline__ void refine_body(const typename Q::Sys &S, double tol_sol,
+                                            double refine_eps, int refine_iters, const EPView &ep,
+                                            const WorkList &wl, int shortcut) {
+    extern __shared__ __align__(16) unsigned char egraw[];
+    __shared__ int64_t rq[2 * EG_BLOCK];
+    const int lane = threadIdx.x;
+    const EG<Q::DIM> G{reinterpret_cast<cx<double> *>(egraw) + lane};
+    const int64_t total = worklist_size(wl, ep.count);
+    int qn = 0;   // queued real tests (the same in every lane)
+    for (int64_t base = (int64_t)blockIdx.x * EG_BLOCK; base < total;
+         base += (int64_t)gridDim.x * EG_BLOCK) {
+        const int64_t i = base + lane;
+        int64_t e = -1;
+        bool rt = false;
+        if (i < total) {
+            e = worklist_entry(wl, i);
+            rt = eg_refine_certify_one<Q>(G, S, tol_sol, refine_eps, refine_iters, ep, e, shortcut);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, rt);
+        if (rt) rq[qn + __popc(m & ((1u << lane) - 1u))] = e;
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= EG_BLOCK) {
+            eg_real_test<Q>(G, S, ep, rq[qn - EG_BLOCK + lane]);
+            qn -= EG_BLOCK;
+            __syncwarp();
+        }
+    }
+    if (lane < qn) eg_real_test<Q>(G, S, ep, rq[lane]);
+}
+
 template <int M>
 __global__ void __launch_bounds__(EG_BLOCK)
     xy_refine_certify_kernel(const __grid_constant__ XYSys S, double tol_sol, double refine_eps,
                              int refine_iters, const EPView ep, const WorkList wl, int shortcut) {
-    using L = EGLayout<M>;
-    extern __shared__ __align__(16) unsigned char egraw[];
-    const EG<M> G{reinterpret_cast<cx<double> *>(egraw) + threadIdx.x};
-    const EGVec X = G.v(L::X), Y = G.v(L::Y), Dv = G.v(L::D);
-    const int64_t total = worklist_size(wl, ep.count);
-    const int64_t cnt = ep.count;
-    const double *J = S.Jd;
-    const double alpha0 = (13.0 - 3.0 * sqrt(17.0)) / 4.0;
-    for (int64_t i = (int64_t)blockIdx.x * EG_BLOCK + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * EG_BLOCK) {
-        const int64_t e = worklist_entry(wl, i);
-        const int st = ep.status[e];
-        const bool sc = shortcut && st == NPHC_PATH_HANDOFF;
-        if (!sc) {
-            ep.alpha[e] = INFINITY;
-            ep.beta[e] = INFINITY;
-            ep.gamma[e] = INFINITY;
-            ep.resid[e] = INFINITY;
-            if (st == NPHC_PATH_DIVERGED) {
-                ep.cls[e] = NPHC_END_NONE;
-                continue;
-            }
-            if (st != NPHC_PATH_REACHED) {
-                ep.cls[e] = NPHC_END_FAILED;
-                continue;
-            }
-        }
-#pragma unroll 1
-        for (int k = 0; k < M; k++) {
-            X.set(k, cx<double>{ep.z_re[k * cnt + e], ep.z_im[k * cnt + e]});
-            Y.set(k, cx<double>{ep.z_re[(M + k) * cnt + e], ep.z_im[(M + k) * cnt + e]});
-        }
-        int cls = NPHC_END_SINGULAR;
-        bool finite = true, untouched = false;
-        // Newton refinement on P
-#pragma unroll 1
-        for (int it = 0; it < refine_iters; it++) {
-            eg_minus_p<M>(G, J);
-            if (!eg_factor<M>(G, J)) break;
-            const double dn = sqrt(eg_solve<M>(G, J));
-            if (sc && it == 0) {
-                double z0 = 0.0;
-#pragma unroll 1
-                for (int k = 0; k < M; k++) z0 += cabs2(X.get(k)) + cabs2(Y.get(k));
-                if (!(dn <= SHORTCUT_TRUST * (1.0 + sqrt(z0)))) {   // not in a basin
-                    untouched = true;
-                    break;
-                }
-            }
-            double zn = 0.0;
-#pragma unroll 1
-            for (int k = 0; k < M; k++) {
-                const cx<double> xk = cadd(X.get(k), Dv.get(k)), yk = cadd(Y.get(k), Dv.get(M + k));
-                X.set(k, xk);
-                Y.set(k, yk);
-                zn += cabs2(xk) + cabs2(yk);
-            }
-            if (!isfinite(dn) || !isfinite(zn)) {
-                finite = false;
-                break;
-            }
-            if (dn <= refine_eps * (1.0 + sqrt(zn))) break;
-        }
-        if (untouched) continue;
-        double beta = INFINITY, invF = INFINITY, res = INFINITY;
-        double alpha = INFINITY, gam = INFINITY;
-        bool real_test = false;
-        if (finite && eg_beta_invnorm<M>(G, J, beta, invF, res)) {
-            gam = invF * S.d2norm;
-            alpha = beta * gam;
-            // Delta_sol relative to the size of the (quadratic) terms: max(1, ||z||_inf^2)
-            double zi = 0.0, im2 = 0.0;
-#pragma unroll 1
-            for (int k = 0; k < M; k++) {
-                const cx<double> xk = X.get(k), yk = Y.get(k);
-                zi = fmax(zi, fmax(sqrt(cabs2(xk)), sqrt(cabs2(yk))));
-                im2 += xk.im * xk.im + yk.im * yk.im;
-            }
-            if (res <= tol_sol * fmax(1.0, zi * zi) && alpha < alpha0) {
-                if (sqrt(im2) > 2.0 * beta)
-                    cls = NPHC_END_NONREAL;
-                else
-                    real_test = true;
-            }
-        } else {
-            beta = INFINITY;
-        }
-        if (sc && !(real_test || cls == NPHC_END_NONREAL)) continue;   // left for FP64 tracking
-        ep.alpha[e] = alpha;
-        ep.beta[e] = beta;
-        ep.gamma[e] = gam;
-        ep.resid[e] = finite ? res : INFINITY;
-        if (sc) {
-            ep.status[e] = NPHC_PATH_REACHED;
-            ep.t[e] = 1.0;
-        }
-#pragma unroll 1
-        for (int k = 0; k < M; k++) {
-            const cx<double> xk = X.get(k), yk = Y.get(k);
-            ep.z_re[k * cnt + e] = xk.re;
-            ep.z_im[k * cnt + e] = xk.im;
-            ep.z_re[(M + k) * cnt + e] = yk.re;
-            ep.z_im[(M + k) * cnt + e] = yk.im;
-        }
-        if (real_test) {
-            // the alpha-test at Re z (the refined z is already written out)
-#pragma unroll 1
-            for (int k = 0; k < M; k++) {
-                X.set(k, cx<double>{X.get(k).re, 0.0});
-                Y.set(k, cx<double>{Y.get(k).re, 0.0});
-            }
-            double br, ir, rr;
-            cls = (eg_beta_invnorm<M>(G, J, br, ir, rr) && br * ir * S.d2norm < alpha0)
-                      ? NPHC_END_REAL
-                      : NPHC_END_UNDECIDED;
-        }
-        ep.cls[e] = cls;
-    }
+    refine_body<EGXY<M>>(S, tol_sol, refine_eps, refine_iters, ep, wl, shortcut);
 }
 
 template <int M>

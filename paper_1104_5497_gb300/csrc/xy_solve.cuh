@@ -110,6 +110,102 @@ __device__ __forceinline__ void g_frame(cx<R> xj, cx<R> yj, R s, cx<R> sg, cx<R>
     bh = cscale(iv, bb);
 }
 
+// Solve S x = b for the M x M matrix S of an augmented per-thread matrix
+// [S | b0 | b1] (b1 only when two_rhs) by Householder QR: Q^H [S | b] = [R | Q^H b] with a
+// real diagonal (stored as (beta, 0) on the diagonal of S), then back substitution in
+// place: the solutions end in columns M and M + 1.  Returns false when S is singular.
+template <int M, class R, int BLOCK>
+__device__ __forceinline__ bool aug_qr_solve(const SMat<M, R, BLOCK> &A, bool two_rhs) {
+    const int ncol = two_rhs ? M + 2 : M + 1;
+    bool ok = true;
+#pragma unroll 1
+    for (int k = 0; k < M; k++) {
+        const int n = M - k;   // active rows k .. M-1, relative index i = 0 .. n-1
+        const SMat<M, R, BLOCK> Ak{A.p + k * BLOCK};   // Ak.get(i, c) = S(k + i, c)
+        // loads first, then arithmetic (all shared loads of a column in flight at once),
+        // sums split in two chains
+        cx<R> v[M];
+        const cx<R> al = Ak.get(0, k);
+#pragma unroll
+        for (int i = 1; i < M; i++) {
+            if (i >= n) break;
+            v[i] = Ak.get(i, k);
+        }
+        R xa = R(0), xb = R(0);
+#pragma unroll
+        for (int i = 1; i < M; i++) {
+            if (i >= n) break;
+            if (i & 1) xa += cabs2(v[i]);
+            else xb += cabs2(v[i]);
+        }
+        const R an = sqrt_r(cabs2(al) + (xa + xb));
+        ok = ok && (an > R(0));
+        const R beta = al.re >= R(0) ? -an : an;
+        const R ib = recip_r(beta);
+        const cx<R> tauc = cx<R>{(beta - al.re) * ib, al.im * ib};   // conj(tau)
+        const cx<R> sc = crecip(cx<R>{al.re - beta, al.im});
+#pragma unroll
+        for (int i = 1; i < M; i++) {
+            if (i >= n) break;
+            v[i] = cmul(v[i], sc);   // reflector (1, v_1, .., v_{n-1})
+        }
+        Ak.set(0, k, cx<R>{beta, R(0)});
+#pragma unroll 1
+        for (int c = k + 1; c < ncol; c++) {
+            cx<R> col[M];
+#pragma unroll
+            for (int i = 0; i < M; i++) {
+                if (i >= n) break;
+                col[i] = Ak.get(i, c);
+            }
+            cx<R> wa = col[0], wb = cx<R>{R(0), R(0)};
+#pragma unroll
+            for (int i = 1; i < M; i++) {
+                if (i >= n) break;
+                if (i & 1) wb = cadd(wb, cmulc(v[i], col[i]));
+                else wa = cadd(wa, cmulc(v[i], col[i]));
+            }
+            const cx<R> wv = cmul(tauc, cadd(wa, wb));
+            Ak.set(0, c, csub(col[0], wv));
+#pragma unroll
+            for (int i = 1; i < M; i++) {
+                if (i >= n) break;
+                Ak.set(i, c, csub(col[i], cmul(v[i], wv)));
+            }
+        }
+    }
+
+    // ---- back substitution R s = Q^H b, column by column, in place in columns M, M + 1
+#pragma unroll 1
+    for (int k = M - 1; k >= 0; k--) {
+        const R ir = recip_r(A.get(k, k).re);
+        const cx<R> s0 = cscale(ir, A.get(k, M));
+        A.set(k, M, s0);
+        cx<R> s1 = cx<R>{R(0), R(0)};
+        if (two_rhs) {
+            s1 = cscale(ir, A.get(k, M + 1));
+            A.set(k, M + 1, s1);
+        }
+        constexpr int MA = M > 1 ? M - 1 : 1;
+        cx<R> Rc[MA], c0[MA], c1[MA];
+#pragma unroll
+        for (int i = 0; i < M - 1; i++) {
+            if (i >= k) break;
+            Rc[i] = A.get(i, k);
+            c0[i] = A.get(i, M);
+            if (two_rhs) c1[i] = A.get(i, M + 1);
+        }
+#pragma unroll
+        for (int i = 0; i < M - 1; i++) {
+            if (i >= k) break;
+            A.set(i, M, csub(c0[i], cmul(Rc[i], s0)));
+            if (two_rhs) A.set(i, M + 1, csub(c1[i], cmul(Rc[i], s1)));
+        }
+    }
+
+    return ok;
+}
+
 // Solve H_z(z, t) d = r at the point in `pt`, with t given as (s, omt) = (t, 1 - t).
 //   two_rhs == false: r = -H_t (predictor: d = dz/dt), written to out1.
 //   two_rhs == true:  r1 = the residual vector in `res` (corrector: -H), written to out1;
@@ -178,75 +274,7 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
         if (two_rhs) A.set(k, M + 1, b1[k]);
     }
 
-    // ---- Householder QR: Q^H [S | b] = [R | Q^H b], R with a real diagonal (stored as
-    // (beta, 0) on the diagonal of S)
-    const int ncol = two_rhs ? M + 2 : M + 1;
-    bool ok = true;
-#pragma unroll 1
-    for (int k = 0; k < M; k++) {
-        const int n = M - k;   // active rows k .. M-1, relative index i = 0 .. n-1
-        const SMat<M, R, BLOCK> Ak{A.p + k * BLOCK};   // Ak.get(i, c) = S(k + i, c)
-        cx<R> v[M];
-        R xn2 = R(0);
-#pragma unroll
-        for (int i = 1; i < M; i++) {
-            if (i >= n) break;
-            v[i] = Ak.get(i, k);
-            xn2 += cabs2(v[i]);
-        }
-        const cx<R> al = Ak.get(0, k);
-        const R an = sqrt_r(cabs2(al) + xn2);
-        ok = ok && (an > R(0));
-        const R beta = al.re >= R(0) ? -an : an;
-        const R ib = recip_r(beta);
-        const cx<R> tauc = cx<R>{(beta - al.re) * ib, al.im * ib};   // conj(tau)
-        const cx<R> sc = crecip(cx<R>{al.re - beta, al.im});
-#pragma unroll
-        for (int i = 1; i < M; i++) {
-            if (i >= n) break;
-            v[i] = cmul(v[i], sc);   // reflector (1, v_1, .., v_{n-1})
-        }
-        Ak.set(0, k, cx<R>{beta, R(0)});
-#pragma unroll 1
-        for (int c = k + 1; c < ncol; c++) {
-            cx<R> col[M];
-            col[0] = Ak.get(0, c);
-            cx<R> wv = col[0];
-#pragma unroll
-            for (int i = 1; i < M; i++) {
-                if (i >= n) break;
-                col[i] = Ak.get(i, c);
-                wv = cadd(wv, cmulc(v[i], col[i]));
-            }
-            wv = cmul(tauc, wv);
-            Ak.set(0, c, csub(col[0], wv));
-#pragma unroll
-            for (int i = 1; i < M; i++) {
-                if (i >= n) break;
-                Ak.set(i, c, csub(col[i], cmul(v[i], wv)));
-            }
-        }
-    }
-
-    // ---- back substitution R s = Q^H b, column by column, in place in columns M, M + 1
-#pragma unroll 1
-    for (int k = M - 1; k >= 0; k--) {
-        const R ir = recip_r(A.get(k, k).re);
-        const cx<R> s0 = cscale(ir, A.get(k, M));
-        A.set(k, M, s0);
-        cx<R> s1 = cx<R>{R(0), R(0)};
-        if (two_rhs) {
-            s1 = cscale(ir, A.get(k, M + 1));
-            A.set(k, M + 1, s1);
-        }
-#pragma unroll
-        for (int i = 0; i < M - 1; i++) {
-            if (i >= k) break;
-            const cx<R> Rik = A.get(i, k);
-            A.set(i, M, csub(A.get(i, M), cmul(Rik, s0)));
-            if (two_rhs) A.set(i, M + 1, csub(A.get(i, M + 1), cmul(Rik, s1)));
-        }
-    }
+    bool ok = aug_qr_solve<M, R, BLOCK>(A, two_rhs);
 
     // ---- back to (dx, dy)
     R chk = R(0);

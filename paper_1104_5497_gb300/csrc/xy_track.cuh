@@ -53,46 +53,115 @@ struct JSel<double> {
 #define NEAR_END 1e-5     // FP32 radius crossings with 1 - t below this ...
 #define RDIV_BAND 1e-3    // ... and ||z||_inf within rdiv (1 + RDIV_BAND) go to FP64
 
-template <int M, class R, class V>
+template <int NV, class R, class V>
 __device__ __forceinline__ R vnorm2(const V &v) {
     R s = R(0);
 #pragma unroll 1
-    for (int i = 0; i < 2 * M; i++) s += cabs2(v.get(i));
+    for (int i = 0; i < NV; i++) s += cabs2(v.get(i));
     return sqrt_r(s);
 }
 
-template <int M, class R, class V>
+template <int NV, class R, class V>
 __device__ __forceinline__ R vnorminf(const V &v) {
     R s = R(0);
 #pragma unroll 1
-    for (int i = 0; i < 2 * M; i++) s = fmax(s, sqrt_r(cabs2(v.get(i))));
+    for (int i = 0; i < NV; i++) s = fmax(s, sqrt_r(cabs2(v.get(i))));
     return s;
 }
 
-template <int M, class R, int BLOCK>
-__global__ void __launch_bounds__(BLOCK)
-    xy_track_kernel(const __grid_constant__ XYSys S, const __grid_constant__ XYCtl C,
-                    const EPView ep, const WorkList wl) {
+// The problem a tracker runs on, as a policy for track_body: the unknowns (NV), the
+// per-thread shared matrix (MD x (MD + 2)), the start point with its dz/dt, the
+// corrector residual -H and the linear solve.  XYProblem: the XY ring (structured Schur
+// solve, M = N - 1 free sites, NV = 2M).
+template <int M, class RT, int BLK>
+struct XYProblem {
+    using R = RT;
+    using Sys = XYSys;
+    static constexpr int BLOCK = BLK;
+    static constexpr int NV = 2 * M;
+    static constexpr int MD = M;
+
+    // start point of path p and its derivative: at t = 0, H_z = 2 gamma diag(z) and
+    // H_t = P(z), so dz_i/dt = -P_i(z) / (2 gamma z_i)
+    static __device__ __forceinline__ void start(const Sys &S, int64_t p, const GVec<R> &Z0,
+                                                 const GVec<R> &K1) {
+        const R *J = JSel<R>::get(S);
+        const cx<R> gam = cx<R>{(R)S.gre, (R)S.gim};
+        cx<R> x[M], y[M];
+#pragma unroll
+        for (int k = 0; k < M; k++) {
+            x[k] = cx<R>{((p >> k) & 1) ? R(-1) : R(1), R(0)};
+            y[k] = cx<R>{((p >> (M + k)) & 1) ? R(-1) : R(1), R(0)};
+        }
+        const cx<R> ig = crecip(gam);
+#pragma unroll 1
+        for (int k = 0; k < M; k++) {
+            const cx<R> xk = cx<R>{((p >> k) & 1) ? R(-1) : R(1), R(0)};
+            const cx<R> yk = cx<R>{((p >> (M + k)) & 1) ? R(-1) : R(1), R(0)};
+            cx<R> u, w, rf, rg;
+            xy_uw<M, R>(J, x, y, k, u, w);
+            minus_ht_rows<R>(xk, yk, u, w, gam, rf, rg);
+            Z0.set(k, xk);
+            Z0.set(M + k, yk);
+            K1.set(k, cscale(R(0.5) * xk.re, cmul(ig, rf)));
+            K1.set(M + k, cscale(R(0.5) * yk.re, cmul(ig, rg)));
+        }
+    }
+
+    static __device__ __forceinline__ void residual(const Sys &S, const SVec<R, BLOCK> &pt, R s,
+                                                    R omt, const SVec<R, BLOCK> &out, bool wr) {
+        xy_residual_comp<M, R, BLOCK>(JSel<R>::get(S), pt, s, omt, cx<R>{(R)S.gre, (R)S.gim}, out,
+                                      wr);
+    }
+
+    template <class Out2>
+    static __device__ __forceinline__ bool solve(const Sys &S, const SMat<M, R, BLOCK> &A,
+                                                 const SVec<R, BLOCK> &pt, R s, R omt,
+                                                 bool two_rhs, const SVec<R, BLOCK> &res,
+                                                 const SVec<R, BLOCK> &out1, const Out2 &out2,
+                                                 bool wr) {
+        return xy_solve<M, R, BLOCK>(JSel<R>::get(S), A, pt, s, omt, cx<R>{(R)S.gre, (R)S.gim},
+                                     two_rhs, res, out1, out2, wr);
+    }
+};
+
+// Shared memory per thread of a tracker on problem P: the augmented matrix and two
+// vectors (evaluation point, solve output).
+template <class P>
+constexpr size_t track_smem_per_thread() {
+    return sizeof(cx<typename P::R>) * (size_t)(P::MD * (P::MD + 2) + 2 * P::NV);
+}
+
+template <class P>
+__device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl &C,
+                                           const EPView &ep, const WorkList &wl) {
+    using R = typename P::R;
+    constexpr int BLOCK = P::BLOCK, NV = P::NV, MD = P::MD;
     extern __shared__ __align__(16) unsigned char smraw[];
     cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
     const int tid = threadIdx.x, lane = tid & 31;
-    const SMat<M, R, BLOCK> A{sm + tid};
-    const SVec<R, BLOCK> ZC{sm + M * (M + 2) * BLOCK + tid};           // evaluation point / iterate
-    const SVec<R, BLOCK> W1{sm + (M * (M + 2) + 2 * M) * BLOCK + tid}; // solve output / residual
+    const SMat<MD, R, BLOCK> A{sm + tid};
+    const SVec<R, BLOCK> ZC{sm + MD * (MD + 2) * BLOCK + tid};        // evaluation point / iterate
+    const SVec<R, BLOCK> W1{sm + (MD * (MD + 2) + NV) * BLOCK + tid}; // solve output / residual
     const int64_t gtid = (int64_t)blockIdx.x * BLOCK + tid;
     const int64_t nth = wl.state_threads;
     cx<R> *st = reinterpret_cast<cx<R> *>(wl.state);
-    const GVec<R> Z0{st + (0 * 2 * M) * nth + gtid, nth};       // accepted point
-    const GVec<R> K1{st + (1 * 2 * M) * nth + gtid, nth};       // dz/dt at Z0
-    const GVec<R> AC{st + (2 * 2 * M) * nth + gtid, nth};       // RK4 sum; next K1 in correction
-    const R *J = JSel<R>::get(S);
-    const cx<R> gam = cx<R>{(R)S.gre, (R)S.gim};
+    const GVec<R> Z0{st + (0 * NV) * nth + gtid, nth};       // accepted point
+    const GVec<R> K1{st + (1 * NV) * nth + gtid, nth};       // dz/dt at Z0
+    const GVec<R> AC{st + (2 * NV) * nth + gtid, nth};       // RK4 sum; next K1 in correction
     const int64_t total = worklist_size(wl, ep.count);
     const int64_t cnt = ep.count;
 
-    // short lists run one path per warp (lane 0), spread over every SM
-    const bool sparse = C.sparse && total <= (int64_t)gridDim.x * (BLOCK / 32) * 2;
-    int64_t e = (sparse && lane != 0) ? -2 : -1;   // entry index; -1 idle, -2 drained
+    // short lists: at most `lanes` paths per warp, so that the list spreads over every SM
+    // instead of filling the first warps 32 at a time (FP64 continuation of a few
+    // thousand hand-offs would otherwise run on a third of the SMs)
+    int lanes = 32;
+    if (C.sparse) {
+        const int64_t warps = (int64_t)gridDim.x * (BLOCK / 32);
+        const int64_t per = (total + warps - 1) / warps;
+        lanes = per < 1 ? 1 : (per > 32 ? 32 : (int)per);
+    }
+    int64_t e = (lane >= lanes) ? -2 : -1;   // entry index; -1 idle, -2 drained
     double t = 0.0, h = 0.0, hacc = 0.0;
     double tmark = 0.0;   // 1 - t recorded every CRAWL_STEPS accepted steps near t = 1
     int since = 0;
@@ -118,7 +187,7 @@ __global__ void __launch_bounds__(BLOCK)
                     attempts = 0;
                     if (C.resume) {
 #pragma unroll 1
-                        for (int k = 0; k < 2 * M; k++)
+                        for (int k = 0; k < NV; k++)
                             Z0.set(k, cx<R>{(R)ep.z_re[k * cnt + e], (R)ep.z_im[k * cnt + e]});
                         t = ep.t[e];
                         // restart with a step on the scale of 1 - t: the FP32 pass may have
@@ -130,28 +199,7 @@ __global__ void __launch_bounds__(BLOCK)
                         newton = ep.newton[e];
                         need_k1 = true;
                     } else {
-                        // start point and its derivative: at t = 0, H_z = 2 gamma diag(z)
-                        // and H_t = P(z), so dz_i/dt = -P_i(z) / (2 gamma z_i)
-                        const int64_t p = ep.path[e];
-                        cx<R> x[M], y[M];
-#pragma unroll
-                        for (int k = 0; k < M; k++) {
-                            x[k] = cx<R>{((p >> k) & 1) ? R(-1) : R(1), R(0)};
-                            y[k] = cx<R>{((p >> (M + k)) & 1) ? R(-1) : R(1), R(0)};
-                        }
-                        const cx<R> ig = crecip(gam);
-#pragma unroll 1
-                        for (int k = 0; k < M; k++) {
-                            const cx<R> xk = cx<R>{((p >> k) & 1) ? R(-1) : R(1), R(0)};
-                            const cx<R> yk = cx<R>{((p >> (M + k)) & 1) ? R(-1) : R(1), R(0)};
-                            cx<R> u, w, rf, rg;
-                            xy_uw<M, R>(J, x, y, k, u, w);
-                            minus_ht_rows<R>(xk, yk, u, w, gam, rf, rg);
-                            Z0.set(k, xk);
-                            Z0.set(M + k, yk);
-                            K1.set(k, cscale(R(0.5) * xk.re, cmul(ig, rf)));
-                            K1.set(M + k, cscale(R(0.5) * yk.re, cmul(ig, rg)));
-                        }
+                        P::start(S, ep.path[e], Z0, K1);
                         t = 0.0;
                         h = C.h0;
                         steps = C.accumulate ? ep.steps[e] : 0;
@@ -205,8 +253,8 @@ __global__ void __launch_bounds__(BLOCK)
             if (w && ph < 4) {
                 // evaluation point of the phase: z0, z0 + h/2 k1, z0 + h/2 k2, z0 + h k3
                 const R c = ph == 3 ? hr : R(0.5) * hr;
-#pragma unroll 1
-                for (int k = 0; k < 2 * M; k++) {
+#pragma unroll 6
+                for (int k = 0; k < NV; k++) {
                     if (ph == 0) {
                         ZC.set(k, Z0.get(k));
                     } else {
@@ -216,14 +264,14 @@ __global__ void __launch_bounds__(BLOCK)
                 }
             }
             const R tr = (R)te, omt = (R)(1.0 - te);
-            if (corr) xy_residual_comp<M, R, BLOCK>(J, ZC, tr, omt, gam, W1, w);
-            const bool oks = xy_solve<M, R, BLOCK>(J, A, ZC, tr, omt, gam, corr, W1, W1, AC, w);
+            if (corr) P::residual(S, ZC, tr, omt, W1, w);
+            const bool oks = P::solve(S, A, ZC, tr, omt, corr, W1, W1, AC, w);
             if (!w) continue;
             solves++;
             if (ph == 0) {
                 // z0 += Newton correction at t; dz/dt from the second right-hand side
-#pragma unroll 1
-                for (int k = 0; k < 2 * M; k++) {
+#pragma unroll 6
+                for (int k = 0; k < NV; k++) {
                     Z0.set(k, cadd(ZC.get(k), W1.get(k)));
                     K1.set(k, AC.get(k));
                 }
@@ -233,16 +281,16 @@ __global__ void __launch_bounds__(BLOCK)
             } else if (!corr) {
                 bad = bad || !oks;
                 if (ph == 1) {
-#pragma unroll 1
-                    for (int k = 0; k < 2 * M; k++) AC.set(k, cadd(K1.get(k), cscale(R(2), W1.get(k))));
+#pragma unroll 6
+                    for (int k = 0; k < NV; k++) AC.set(k, cadd(K1.get(k), cscale(R(2), W1.get(k))));
                 } else if (ph == 2) {
-#pragma unroll 1
-                    for (int k = 0; k < 2 * M; k++) AC.set(k, cadd(AC.get(k), cscale(R(2), W1.get(k))));
+#pragma unroll 6
+                    for (int k = 0; k < NV; k++) AC.set(k, cadd(AC.get(k), cscale(R(2), W1.get(k))));
                 } else {
                     // predicted point z0 + h/6 (k1 + 2 k2 + 2 k3 + k4)
                     R zz = R(0);
-#pragma unroll 1
-                    for (int k = 0; k < 2 * M; k++) {
+#pragma unroll 6
+                    for (int k = 0; k < NV; k++) {
                         const cx<R> zp = cadd(Z0.get(k), cscale(hr / R(6), cadd(AC.get(k), W1.get(k))));
                         ZC.set(k, zp);
                         zz += cabs2(zp);
@@ -251,7 +299,7 @@ __global__ void __launch_bounds__(BLOCK)
                 }
             } else {
                 newton++;
-                const R dn = vnorm2<M, R>(W1);
+                const R dn = vnorm2<NV, R>(W1);
                 if (!oks || !finite_r(dn)) {
                     bad = true;
                 } else if (ph == 4 && dn > (R)C.trust * (R(1) + zpn)) {
@@ -259,7 +307,7 @@ __global__ void __launch_bounds__(BLOCK)
                 } else {
                     R zz = R(0);
 #pragma unroll 1
-                    for (int k = 0; k < 2 * M; k++) {
+                    for (int k = 0; k < NV; k++) {
                         const cx<R> zn = cadd(ZC.get(k), W1.get(k));
                         ZC.set(k, zn);
                         zz += cabs2(zn);
@@ -275,8 +323,8 @@ __global__ void __launch_bounds__(BLOCK)
             attempts++;
             if (conv) {
                 R zi = R(0);
-#pragma unroll 1
-                for (int k = 0; k < 2 * M; k++) {
+#pragma unroll 6
+                for (int k = 0; k < NV; k++) {
                     const cx<R> v = ZC.get(k);
                     Z0.set(k, v);
                     K1.set(k, AC.get(k));
@@ -328,7 +376,7 @@ __global__ void __launch_bounds__(BLOCK)
         }
         if (act && status != NPHC_PATH_RUNNING) {
 #pragma unroll 1
-            for (int k = 0; k < 2 * M; k++) {
+            for (int k = 0; k < NV; k++) {
                 const cx<R> v = Z0.get(k);
                 ep.z_re[k * cnt + e] = (double)v.re;
                 ep.z_im[k * cnt + e] = (double)v.im;
@@ -342,4 +390,11 @@ __global__ void __launch_bounds__(BLOCK)
             e = -1;
         }
     }
+}
+
+template <int M, class R, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    xy_track_kernel(const __grid_constant__ XYSys S, const __grid_constant__ XYCtl C,
+                    const EPView ep, const WorkList wl) {
+    track_body<XYProblem<M, R, BLOCK>>(S, C, ep, wl);
 }

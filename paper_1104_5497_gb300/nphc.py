@@ -79,6 +79,10 @@ def lib():
         "nphc_options_default": [ctypes.POINTER(nphc_options)],
         "nphc_xy_couplings": [i32, d, pd, d, pd],
         "nphc_system_create_xy": [i32, d, pd, ctypes.POINTER(vp)],
+        "nphc_system_create_quadratic": [i32, i32, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32), pd, pd,
+                                         ctypes.POINTER(vp)],
         "nphc_system_info": [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), pi64],
         "nphc_system_couplings": [vp, pd],
         "nphc_workspace_size": [vp, i64, ctypes.POINTER(ctypes.c_size_t)],
@@ -98,6 +102,9 @@ def lib():
         "nphc_result_copy_sps": [vp, i64, pd, pd, pi32, pd, pi64, pi64],
         "nphc_result_copy_endpoints": [vp, i64, pd, pd, pi32, pi32, pi64],
         "nphc_result_endpoints": [vp, ctypes.POINTER(nphc_endpoints)],
+        "nphc_batch_create": [i32, ctypes.POINTER(vp), ctypes.POINTER(vp)],
+        "nphc_batch_solve": [vp, ctypes.POINTER(nphc_options), i32, vp],
+        "nphc_batch_result": [vp, i32, ctypes.POINTER(vp)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -107,6 +114,8 @@ def lib():
     L.nphc_system_destroy.restype = None
     L.nphc_result_destroy.argtypes = [vp]
     L.nphc_result_destroy.restype = None
+    L.nphc_batch_destroy.argtypes = [vp]
+    L.nphc_batch_destroy.restype = None
     L.nphc_last_error.argtypes = []
     L.nphc_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -166,6 +175,9 @@ class System:
         _check("nphc_system_create_xy",
                lib().nphc_system_create_xy(int(N), float(sigma), None if Jc is None else _pd(Jc),
                                            ctypes.byref(h)))
+        self._attach(h)
+
+    def _attach(self, h):
         self.handle = h
         n = ctypes.c_int()
         NN = ctypes.c_int()
@@ -173,7 +185,26 @@ class System:
         _check("nphc_system_info", lib().nphc_system_info(h, ctypes.byref(NN), ctypes.byref(n),
                                                         ctypes.byref(P)))
         self.N, self.n, self.npaths = NN.value, n.value, P.value
-        self.M = self.N - 1
+        self.M = max(self.N - 1, 0)
+
+    @classmethod
+    def quadratic(cls, n: int, eq, va, vb, coef) -> "System":
+        """nphc_system_create_quadratic: P_i = sum over terms with eq == i of
+        coef * w(va) * w(vb), w(-1) = 1 (a term list, as oracle.Terms)."""
+        eq = np.ascontiguousarray(eq, dtype=np.int32)
+        va = np.ascontiguousarray(va, dtype=np.int32)
+        vb = np.ascontiguousarray(vb, dtype=np.int32)
+        coef = np.asarray(coef, dtype=complex)
+        cre = np.ascontiguousarray(coef.real, dtype=np.float64)
+        cim = np.ascontiguousarray(coef.imag, dtype=np.float64)
+        pi32 = ctypes.POINTER(ctypes.c_int32)
+        h = ctypes.c_void_p()
+        _check("nphc_system_create_quadratic", lib().nphc_system_create_quadratic(
+            int(n), int(len(eq)), eq.ctypes.data_as(pi32), va.ctypes.data_as(pi32),
+            vb.ctypes.data_as(pi32), _pd(cre), _pd(cim), ctypes.byref(h)))
+        self = cls.__new__(cls)
+        self._attach(h)
+        return self
 
     def couplings(self) -> np.ndarray:
         J = np.zeros((self.N, self.N))
@@ -236,9 +267,41 @@ class Result:
         return ep
 
     def __del__(self):
-        if getattr(self, "handle", None) and _lib is not None:
+        if getattr(self, "handle", None) and _lib is not None and not getattr(self, "borrowed", False):
             _lib.nphc_result_destroy(self.handle)
-            self.handle = None
+        self.handle = None
+
+
+class Batch:
+    """nphc_batch: independent systems solved together (one result per instance)."""
+
+    def __init__(self, systems):
+        self.systems = list(systems)   # the batch borrows them
+        arr = (ctypes.c_void_p * len(self.systems))(*[s.handle.value for s in self.systems])
+        h = ctypes.c_void_p()
+        _check("nphc_batch_create", lib().nphc_batch_create(len(self.systems), arr, ctypes.byref(h)))
+        self.handle = h
+
+    def solve(self, opts, graph: bool = False, stream=None) -> None:
+        """nphc_batch_solve: opts is one nphc_options per instance."""
+        arr = (nphc_options * len(self.systems))(*opts)
+        _check("nphc_batch_solve", lib().nphc_batch_solve(self.handle, arr, int(bool(graph)),
+                                                         _stream_ptr(stream)))
+
+    def result(self, i: int) -> Result:
+        h = ctypes.c_void_p()
+        _check("nphc_batch_result", lib().nphc_batch_result(self.handle, int(i), ctypes.byref(h)))
+        r = Result.__new__(Result)
+        r.handle = h
+        r.system = self.systems[i]
+        r.borrowed = True
+        r.owner = self
+        return r
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.nphc_batch_destroy(self.handle)
+        self.handle = None
 
 
 def solve_into(system: System, opts: nphc_options, result: Result, stream=None) -> None:
@@ -319,6 +382,7 @@ def dedup(system: System, opts: nphc_options, ep: DeviceEndpoints, workspace, du
 
 
 DEDUP_NOALLOC_MAX = 65536   # NPHC_DEDUP_NOALLOC_MAX
+QUAD_MAX_N = 12             # NPHC_QUAD_MAX_N
 
 
 def dedup_noalloc(system: System, opts: nphc_options, ep: DeviceEndpoints, dup_list=None,

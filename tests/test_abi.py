@@ -78,3 +78,19 @@ def test_system_dimensions(N_, N):
     assert (s.N, s.n, s.npaths) == (N, 2 * (N - 1), 4 ** (N - 1))
     assert np.array_equal(s.couplings(), B.ring_couplings(N, 1.0))
     assert s.workspace_size(1000) < s.workspace_size(100000)
+
+
+def test_quadratic_system_argument_checks(N_):
+    """nphc_system_create_quadratic validates the term list before touching the device."""
+    ok = dict(eq=[0, 0], va=[0, -1], vb=[0, -1], coef=[1.0, -5.0])
+    bad = [
+        (0, ok), (N_.QUAD_MAX_N + 1, ok),
+        (1, dict(ok, eq=[0, 1])),                      # equation index out of range
+        (1, dict(ok, va=[0, -2])),                     # variable index out of range
+        (1, dict(ok, vb=[1, -1])),
+        (1, dict(ok, coef=[1.0, float("nan")])),
+    ]
+    for n, t in bad:
+        with pytest.raises(N_.NphcError) as ei:
+            N_.System.quadratic(n, t["eq"], t["va"], t["vb"], t["coef"])
+        assert ei.value.status == 1

@@ -1,0 +1,56 @@
+"""Batches of independent systems (nphc_batch_*): the 64-instance disordered workload
+(N = 6..9, one gamma per instance) solved together, eagerly and through one captured CUDA
+graph, gives every instance the same results as solving it alone; a subset is checked
+against the oracle."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gpu_common import nphc
+from paper_1104_5497_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def instance_system(N_, inst):
+    J = N_.xy_couplings(inst.N, inst.sigma, inst.g, inst.eps)
+    return N_.System(inst.N, inst.sigma, J)
+
+
+def certified(res, N_):
+    ep = res.endpoints()
+    c = np.isin(ep["cls"], [N_.END_REAL, N_.END_NONREAL])
+    z = ep["z"][c]
+    return z[np.lexsort(np.round(np.concatenate([z.real, z.imag], axis=1).T, 8))]
+
+
+def test_batch64_matches_single_solves_and_graph_replays():
+    N_ = nphc()
+    insts = I.workload_batch64()
+    assert len(insts) == 64
+    systems = [instance_system(N_, inst) for inst in insts]
+    opts = [N_.options_default(gamma=inst.gamma) for inst in insts]
+    batch = N_.Batch(systems)
+    for mode in ("eager", "capture", "replay"):
+        batch.solve(opts, graph=(mode != "eager"))
+        for i in (0, 5, 17, 33, 63):
+            single = N_.solve(systems[i], opts[i])
+            a, b = batch.result(i).counts(), single.counts()
+            for k in ("paths", "real", "nonreal", "duplicate", "index_hist"):
+                assert a[k] == b[k], (mode, i, k, a[k], b[k])
+            za, zb = certified(batch.result(i), N_), certified(single, N_)
+            assert za.shape == zb.shape
+            assert np.abs(za - zb).max() <= 1e-9 * (1 + np.abs(zb).max())
+
+
+def test_batch_instances_match_the_oracle():
+    N_ = nphc()
+    insts = [inst for inst in I.workload_batch64() if inst.N <= 7][:4]
+    systems = [instance_system(N_, inst) for inst in insts]
+    batch = N_.Batch(systems)
+    batch.solve([N_.options_default(gamma=inst.gamma) for inst in insts], graph=True)
+    for i, inst in enumerate(insts):
+        ref = O.solve_xy(inst.N, inst.sigma, inst.gamma, g=inst.g, eps=inst.eps)
+        c = batch.result(i).counts()
+        assert c["real"] == (ref["cls"] == O.C_REAL).sum()
+        assert c["nonreal"] == (ref["cls"] == O.C_NONREAL).sum()

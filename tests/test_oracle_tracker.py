@@ -8,13 +8,9 @@ import numpy as np
 import pytest
 
 import oracle as O
+from systems import product_system, x2_minus_5
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-
-
-def x2_minus_5():
-    # P(x) = x^2 - 5 as terms: 1 * x * x  +  (-5) * 1 * 1
-    return O.Terms(1, [0, 0], [0, -1], [0, -1], [1.0, -5.0])
 
 
 def test_paper_worked_example_x2_minus_5():
@@ -49,25 +45,6 @@ def test_alpha_closed_form_univariate():
         assert rc["beta"][0] == pytest.approx(beta, rel=1e-13)
         assert rc["gamma"][0] == pytest.approx(gam, rel=1e-13)
         assert rc["alpha"][0] == pytest.approx(beta * gam, rel=1e-13)
-
-
-def product_system(n, seed):
-    """P_i(z) = (w_i - a_i)(w_i - b_i) with w = A z: its 2^n roots are z = A^-1 w,
-    w in prod_i {a_i, b_i}, all nonsingular when a_i != b_i and A is invertible."""
-    rng = np.random.default_rng(seed)
-    A = rng.standard_normal((n, n)) + 0.5 * np.eye(n)
-    a = rng.standard_normal(n)
-    b = rng.standard_normal(n) + 1j * rng.standard_normal(n) * (rng.random(n) < 0.5)
-    eq, va, vb, co = [], [], [], []
-    for i in range(n):
-        for j in range(n):
-            for k in range(n):
-                eq.append(i); va.append(j); vb.append(k); co.append(A[i, j] * A[i, k])
-        for j in range(n):
-            eq.append(i); va.append(j); vb.append(-1); co.append(-(a[i] + b[i]) * A[i, j])
-        eq.append(i); va.append(-1); vb.append(-1); co.append(a[i] * b[i])
-    roots = [np.linalg.solve(A, np.array(w)) for w in itertools.product(*zip(a, b))]
-    return O.Terms(n, eq, va, vb, co), np.array(roots)
 
 
 @pytest.mark.parametrize("n,seed", [(2, 0), (3, 1), (4, 2), (5, 3)])
