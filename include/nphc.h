@@ -207,7 +207,8 @@ nphc_status nphc_track(const nphc_system *sys, const nphc_options *opt, nphc_pre
 
 /* FP64 Newton refinement of every selected entry with status NPHC_PATH_REACHED, then
  * the paper's solution tolerance and alpha-theory certification: beta = ||DP^-1 P||,
- * gamma <= ||DP^-1||_F ||D^2P/2||, certified when beta * gamma < (13 - 3 sqrt 17)/4;
+ * gamma <= ||DP^-1||_F ||D^2P/2||, certified when beta * gamma < (13 - 3 sqrt 17)/8 (half
+ * of Smale's constant: an FP64 test keeps a margin where alphaCertified is exact);
  * real when z and Re z share their zero (alpha < 0.03, ||Im z|| < 1/(20 gamma)) and the
  * same test passes at Re z, otherwise non-real when ||Im z|| > 2 beta, else undecided.
  * Writes z
@@ -256,10 +257,30 @@ nphc_status nphc_dedup_noalloc(const nphc_system *sys, const nphc_options *opt,
 /* For every entry with cls == NPHC_END_REAL: theta_k = atan2(s_k, c_k) in (-pi, pi]
  * (theta: device [(N-1) * count], SoA), the Hessian of V in theta_1..theta_{N-1}, its
  * index (device int32 [count]: number of negative eigenvalues), its smallest |eigenvalue|
- * (device [count], may be NULL) and V = sum_{i<j} J_ij (1 - cos(theta_i - theta_j))
- * (device [count]).  Other entries get index -1. */
+ * (device [count], may be NULL), log |det H| (device [count], may be NULL: the paper's
+ * |det H|^(1/N) is exp(log |det H| / N), section "A First Application") and
+ * V = sum_{i<j} J_ij (1 - cos(theta_i - theta_j)) (device [count]).  Other entries get
+ * index -1. */
 nphc_status nphc_classify(const nphc_system *sys, const nphc_endpoints *ep, double *theta,
-                          int32_t *index, double *energy, double *min_abs_eig, void *stream);
+                          int32_t *index, double *energy, double *min_abs_eig,
+                          double *log_abs_det, void *stream);
+
+/* Gradient with respect to the couplings of a loss L summed over real stationary points
+ * (derivatives of the method's outputs; the paper computes none): given, per point,
+ * dL/dV (g_energy) and dL/dtheta (g_theta), adds to dJ
+ *   dL/dJ_ij = g_energy (1 - cos(theta_i - theta_j)) - (lambda_i - lambda_j) sin(theta_i - theta_j),
+ * H lambda = g_theta (H the Hessian of V in theta_1..theta_{N-1}, lambda_N = 0): the
+ * envelope theorem for V (grad V = 0 at the point) and the implicit function theorem for
+ * theta*.  For couplings J_ij = d_ij^-sigma (1 + eps g_ij), dL/dsigma is
+ * sum_{i<j} dL/dJ_ij (-ln d_ij) J_ij.
+ *   theta: device [count * (N-1)], one row per point (as nphc_result_copy_sps writes it);
+ * g_energy: device [count] or NULL (0); g_theta: device [count * (N-1)] or NULL (0);
+ * dJ: device [N * N], accumulated (+=), symmetric (J_ij and J_ji both get the value of
+ * the one parameter), diagonal untouched.  A point whose Hessian is singular adds
+ * nothing.  NPHC_EINVAL for NULL arrays or a generic quadratic system. */
+nphc_status nphc_xy_adjoint(const nphc_system *sys, int64_t count, const double *theta,
+                            const double *g_energy, const double *g_theta, double *dJ,
+                            void *stream);
 
 /* Result counters (nphc_result_counts). */
 enum {
@@ -294,11 +315,11 @@ nphc_status nphc_solve(const nphc_system *sys, const nphc_options *opt, void *st
 nphc_status nphc_result_counts(const nphc_result *res, int64_t *counts);
 
 /* Real stationary points, ordered by path index, into host buffers of capacity cap:
- * theta [cap * (N-1)] (row per SP), energy, index, alpha, path.  Any output may be NULL.
- * *n_out = number of real SPs (may exceed cap; only cap are written). */
+ * theta [cap * (N-1)] (row per SP), energy, index, alpha, path, log |det H|.  Any output
+ * may be NULL.  *n_out = number of real SPs (may exceed cap; only cap are written). */
 nphc_status nphc_result_copy_sps(const nphc_result *res, int64_t cap, double *theta,
                                  double *energy, int32_t *index, double *alpha, int64_t *path,
-                                 int64_t *n_out);
+                                 double *log_abs_det, int64_t *n_out);
 
 /* Every path's endpoint (host, path-major z [cap * n]), status and class.  Any output may
  * be NULL.  *n_out = number of paths. */

@@ -14,7 +14,8 @@ method is in the C file; this file only orders the calls:
     track      (gamma-trick total-degree homotopy, predictor-corrector tracking)
     refine_certify (Newton refinement, Delta_sol, alpha-theory, real / non-real tests)
     dedup      (alpha-theory same/distinct tests between certified endpoints)
-    xy_classify (theta = atan2(s, c), Hessian index, energy V)
+    xy_classify (theta = atan2(s, c), Hessian index, energy V, log |det H|)
+    xy_adjoint  (gradient of a loss on an SP with respect to the couplings)
 """
 from __future__ import annotations
 
@@ -38,6 +39,9 @@ REACHED, DIVERGED, MIN_STEP, STEP_BUDGET, NONFINITE = 1, 2, 3, 4, 5
 C_NONE, C_SINGULAR, C_REAL, C_NONREAL, C_UNDECIDED, C_DUPLICATE, C_FAILED = 0, 1, 2, 3, 4, 5, 6
 
 ALPHA0 = (13.0 - 3.0 * math.sqrt(17.0)) / 4.0   # Smale's alpha-theorem constant
+# FP64 is a soft alpha test (alphaCertified works in exact arithmetic): certify below
+# half the constant, so that rounding cannot carry a near-singular point across it
+ALPHA_CERT = 0.5 * ALPHA0
 
 
 class TrackOpts(ctypes.Structure):
@@ -62,7 +66,7 @@ def default_track_opts(**kw) -> TrackOpts:
 
 def default_cert_opts(**kw) -> CertOpts:
     """Delta_sol = 1e-10 (the paper's solution tolerance), alpha_0 from Smale's theorem."""
-    o = dict(tol_sol=1e-10, refine_eps=1e-14, refine_iters=8, alpha0=ALPHA0)
+    o = dict(tol_sol=1e-10, refine_eps=1e-14, refine_iters=8, alpha0=ALPHA_CERT)
     o.update(kw)
     return CertOpts(**o)
 
@@ -103,7 +107,8 @@ def lib():
                                             I, D, I, D, D, D, D, D]
         L.oracle_dedup.argtypes = [ctypes.c_int, I64, D, D, D, D, I]
         L.oracle_dedup.restype = ctypes.c_int64
-        L.oracle_xy_classify.argtypes = [ctypes.c_int, D, D, D, D, I, D, D, D]
+        L.oracle_xy_classify.argtypes = [ctypes.c_int, D, D, D, D, I, D, D, D, D]
+        L.oracle_xy_adjoint.argtypes = [ctypes.c_int, D, D, ctypes.c_double, D, D]
         _lib = L
     return _lib
 
@@ -259,10 +264,24 @@ def xy_classify(N: int, J: np.ndarray, c: np.ndarray, s: np.ndarray) -> dict:
     s = np.ascontiguousarray(s, dtype=np.float64)
     theta, hess = np.zeros(m), np.zeros((m, m))
     idx = np.zeros(1, np.int32)
-    en, mn = np.zeros(1), np.zeros(1)
-    lib().oracle_xy_classify(N, _d(Jc), _d(c), _d(s), _d(theta), _i(idx), _d(en), _d(mn), _d(hess))
+    en, mn, ld = np.zeros(1), np.zeros(1), np.zeros(1)
+    lib().oracle_xy_classify(N, _d(Jc), _d(c), _d(s), _d(theta), _i(idx), _d(en), _d(mn), _d(ld),
+                             _d(hess))
     return dict(theta=theta, index=int(idx[0]), energy=float(en[0]), min_abs_eig=float(mn[0]),
-                hessian=hess)
+                log_abs_det=float(ld[0]), hessian=hess)
+
+
+def xy_adjoint(N: int, J: np.ndarray, theta: np.ndarray, g_energy: float,
+               g_theta: np.ndarray | None = None) -> np.ndarray:
+    """dL/dJ_ij (N x N symmetric) of a loss L(V*, theta*) at the real SP theta* (N-1
+    angles), given dL/dV and dL/dtheta (implicit function theorem, envelope for V)."""
+    Jc = np.ascontiguousarray(J, dtype=np.float64)
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    g = None if g_theta is None else np.ascontiguousarray(g_theta, dtype=np.float64)
+    dJ = np.zeros((N, N))
+    if lib().oracle_xy_adjoint(N, _d(Jc), _d(th), float(g_energy), None if g is None else _d(g), _d(dJ)):
+        raise ValueError("singular Hessian at the stationary point")
+    return dJ
 
 
 def solve_system(T: Terms, gamma: complex, track_opts=None, cert_opts=None, nthreads=None,

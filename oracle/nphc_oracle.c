@@ -565,9 +565,18 @@ double oracle_d2_norm(int n, int nterms, const int *eq, const int *va, const int
 }
 
 /* beta = ||DP(z)^-1 P(z)||_2 and ||DP(z)^-1||_F at z.  Returns 1 if DP(z) is singular. */
-static int beta_and_inv_norm(const qsys *S, const cplx *z, double *beta, double *invF, work *w) {
+/* KAPPA_SING: an endpoint whose Jacobian has Frobenius condition number
+ * ||DP||_F ||DP^-1||_F above this is singular.  At a point of a positive-dimensional
+ * solution set P vanishes to double-double precision, so beta is tiny, while rounding
+ * leaves the computed DP^-1 merely huge: the soft FP64 alpha test alone can pass there. */
+#define KAPPA_SING 1e12
+
+static int beta_and_inv_norm(const qsys *S, const cplx *z, double *beta, double *invF,
+                             double *cond, work *w) {
     int n = S->n;
     sys_jac(S, z, w->A);
+    double fro = 0;
+    for (int i = 0; i < n * n; i++) fro += creal(w->A[i]) * creal(w->A[i]) + cimag(w->A[i]) * cimag(w->A[i]);
     if (lu_factor(n, w->A, w->piv)) return 1;
     sys_eval_acc(S, z, w->b);
     lu_apply(n, w->A, w->piv, w->b);
@@ -580,6 +589,7 @@ static int beta_and_inv_norm(const qsys *S, const cplx *z, double *beta, double 
         s += v * v;
     }
     *invF = sqrt(s);
+    *cond = sqrt(fro) * *invF;
     return 0;
 }
 
@@ -587,7 +597,7 @@ typedef struct {
     double tol_sol;       /* Delta_sol: ||P(z)||_inf <= tol_sol * max(1, ||z||_inf^2) */
     double refine_eps;    /* Newton refinement stops when ||dz|| <= eps (1 + ||z||) */
     int refine_iters;     /* at most this many refinement steps */
-    double alpha0;        /* alpha threshold, (13 - 3 sqrt 17) / 4 */
+    double alpha0;        /* alpha threshold: half of (13 - 3 sqrt 17) / 4 (FP64 soft test) */
 } oracle_cert_opts;
 
 /* Refine and certify one endpoint.  Outputs: class, alpha, beta, residual, alpha at
@@ -611,15 +621,15 @@ static int refine_certify_one(const qsys *S, double d2, const oracle_cert_opts *
     sys_eval_acc(S, z, w->P);
     double res = norminf(n, w->P);
     *res_out = res;
-    double beta, invF;
-    if (beta_and_inv_norm(S, z, &beta, &invF, w)) return OC_SINGULAR;
+    double beta, invF, cond;
+    if (beta_and_inv_norm(S, z, &beta, &invF, &cond, w)) return OC_SINGULAR;
     double gam = invF * d2, alpha = beta * gam;
     *alpha_out = alpha; *beta_out = beta; *gam_out = gam;
     /* the solution tolerance is applied relative to the size of the equations' terms:
      * every equation is quadratic, so at ||z|| >> 1 its terms are ~||z||^2 and an absolute
      * 1e-10 would sit below the rounding of their sum */
     double zi = norminf(n, z), scale = zi > 1.0 ? zi * zi : 1.0;
-    if (!(res <= o->tol_sol * scale) || !(alpha < o->alpha0)) return OC_SINGULAR;
+    if (!(res <= o->tol_sol * scale) || !(alpha < o->alpha0) || !(cond <= KAPPA_SING)) return OC_SINGULAR;
     double im = 0;
     for (int i = 0; i < n; i++) im += cimag(z[i]) * cimag(z[i]);
     im = sqrt(im);
@@ -630,11 +640,11 @@ static int refine_certify_one(const qsys *S, double d2, const oracle_cert_opts *
     if (alpha < 0.03 && im < 1.0 / (20.0 * gam)) {
         cplx *x = w->zs;
         for (int i = 0; i < n; i++) x[i] = creal(z[i]);
-        double beta_r, invF_r;
-        if (!beta_and_inv_norm(S, x, &beta_r, &invF_r, w)) {
+        double beta_r, invF_r, cond_r;
+        if (!beta_and_inv_norm(S, x, &beta_r, &invF_r, &cond_r, w)) {
             double ar = beta_r * invF_r * d2;
             *alpha_re_out = ar;
-            if (ar < o->alpha0) return OC_REAL;
+            if (ar < o->alpha0 && cond_r <= KAPPA_SING) return OC_REAL;
         }
     }
     /* non-real test: z and conj(z) have distinct associated solutions when
@@ -763,7 +773,7 @@ int64_t oracle_dedup(int n, int64_t count, const double *zre, const double *zim,
  * hess_out (m*m, may be NULL) receives H. */
 int oracle_xy_classify(int N, const double *J, const double *c, const double *s,
                        double *theta, int *index, double *energy, double *min_abs_eig,
-                       double *hess_out) {
+                       double *log_abs_det, double *hess_out) {
     int m = N - 1;
     double *th = malloc(sizeof(double) * N), *H = malloc(sizeof(double) * m * m),
            *w = malloc(sizeof(double) * m);
@@ -790,11 +800,67 @@ int oracle_xy_classify(int N, const double *J, const double *c, const double *s,
         for (int j = i + 1; j < N; j++) V += J[i * N + j] * (1.0 - cos(th[i] - th[j]));
     jacobi_eig(m, H, w);
     int neg = 0;
-    double mn = INFINITY;
-    for (int k = 0; k < m; k++) { if (w[k] < 0) neg++; if (fabs(w[k]) < mn) mn = fabs(w[k]); }
+    double mn = INFINITY, ld = 0.0;
+    for (int k = 0; k < m; k++) {
+        if (w[k] < 0) neg++;
+        if (fabs(w[k]) < mn) mn = fabs(w[k]);
+        ld += log(fabs(w[k]));   /* log |det H| = sum of log |eigenvalue| */
+    }
     *index = neg;
     *energy = V;
     *min_abs_eig = mn;
+    *log_abs_det = ld;
     free(th); free(H); free(w);
     return 0;
 }
+
+/* ----------------------------------------------------------------- adjoint -- */
+/* Gradient with respect to the couplings of a loss L(V*, theta*) at a real stationary
+ * point theta* (theta_N = 0 pinned) of V = sum_{i<j} J_ij (1 - cos(theta_i - theta_j)).
+ * theta* solves G(theta; J) = grad_theta V = 0, so (implicit function theorem)
+ * d(theta*) / dJ_ij = -H^-1 dG/dJ_ij with H the Hessian in theta_1..theta_m, and
+ * d(V at theta*) / dJ_ij = dV/dJ_ij (G = 0).  With H lambda = dL/dtheta (lambda_N = 0) and
+ * dG_i/dJ_ij = sin(theta_i - theta_j) = -dG_j/dJ_ij:
+ *   dL/dJ_ij = gV (1 - cos(theta_i - theta_j)) - (lambda_i - lambda_j) sin(theta_i - theta_j).
+ * gV = dL/dV; g = dL/dtheta (m entries, NULL = 0).  dJ (N x N, symmetric, zero diagonal)
+ * receives dL/dJ_ij for the one parameter J_ij = J_ji.  Returns 1 if H is singular. */
+int oracle_xy_adjoint(int N, const double *J, const double *theta, double gV, const double *g,
+                      double *dJ) {
+    int m = N - 1;
+    double *th = malloc(sizeof(double) * N), *lam = calloc(N, sizeof(double));
+    cplx *H = malloc(sizeof(cplx) * m * m), *b = malloc(sizeof(cplx) * m);
+    int *piv = malloc(sizeof(int) * m), bad = 0;
+    for (int k = 0; k < m; k++) th[k] = theta[k];
+    th[m] = 0.0;
+    if (g) {
+        for (int k = 0; k < m; k++)
+            for (int l = 0; l < m; l++) {
+                double v;
+                if (k == l) {
+                    v = 0;
+                    for (int j = 0; j < N; j++) if (j != k) v += J[k * N + j] * cos(th[k] - th[j]);
+                } else {
+                    v = -J[k * N + l] * cos(th[k] - th[l]);
+                }
+                H[k * m + l] = v;
+            }
+        for (int k = 0; k < m; k++) b[k] = g[k];
+        if (lu_factor(m, H, piv)) bad = 1;
+        else {
+            lu_apply(m, H, piv, b);
+            for (int k = 0; k < m; k++) lam[k] = creal(b[k]);
+        }
+    }
+    for (int i = 0; i < N; i++) {
+        dJ[i * N + i] = 0.0;
+        for (int j = i + 1; j < N; j++) {
+            double d = th[i] - th[j];
+            double v = gV * (1.0 - cos(d)) - (lam[i] - lam[j]) * sin(d);
+            dJ[i * N + j] = v;
+            dJ[j * N + i] = v;
+        }
+    }
+    free(th); free(lam); free(H); free(b); free(piv);
+    return bad;
+}
+

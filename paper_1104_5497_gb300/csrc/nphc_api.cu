@@ -43,7 +43,7 @@ int64_t table_size_for(int64_t count) {
 }
 
 // Device scratch: [queue counters | tracker path state | dedup cell keys | cell list
-// heads | list links | flags].  The tracker state holds three vectors of n complex
+// heads | list links | flags].  The tracker state holds four vectors of n complex
 // doubles for each of NPHC_TRACK_MAX_THREADS threads (enough for either precision).
 struct WsLayout {
     size_t queue, state, keys, head, next, inlist, total;
@@ -55,7 +55,7 @@ WsLayout ws_layout(int n, int64_t count) {
     L.tsize = table_size_for(count);
     size_t o = 0;
     L.queue = o;  o += align256(64);
-    L.state = o;  o += align256((size_t)3 * n * NPHC_TRACK_MAX_THREADS * 2 * sizeof(double));
+    L.state = o;  o += align256((size_t)4 * n * NPHC_TRACK_MAX_THREADS * 2 * sizeof(double));
     L.keys = o;   o += align256(sizeof(unsigned long long) * L.tsize * DD_LEVELS);
     L.head = o;   o += align256(sizeof(int32_t) * L.tsize * DD_LEVELS);
     L.next = o;   o += align256(sizeof(int32_t) * count * DD_LEVELS);
@@ -97,10 +97,10 @@ struct nphc_result {
     void *block;             // single device allocation
     size_t bytes;
     nphc_endpoints ep;       // device arrays for all paths
-    double *theta, *energy, *mineig;
+    double *theta, *energy, *mineig, *logdet;
     int32_t *index, *flags, *list[4], *lcount, *real_list;
     int64_t *counts;
-    double *o_theta, *o_energy, *o_alpha;
+    double *o_theta, *o_energy, *o_alpha, *o_logdet;
     int32_t *o_index;
     int64_t *o_path;
     void *ws;
@@ -409,6 +409,8 @@ nphc_status track_impl(const nphc_system *S, const nphc_options *o, nphc_precisi
     const EPView v = view(ep);
     if (S->quad)
         NPHC_CK(launch_quad_track(S->n, quad_with_gamma(S, o), ctl, v, wl, 0, st));
+    else if (!f32 && list != nullptr)   // short FP64 lists: one path per warp
+        NPHC_CK(launch_xy_track_f64_warp(S->M, xs, ctl, v, wl, st));
     else if (f32)
         NPHC_CK(launch_xy_track_f32(S->M, xs, ctl, v, wl, 0, grid, st));
     else
@@ -484,14 +486,25 @@ nphc_status nphc_dedup(const nphc_system *S, const nphc_options *o, const nphc_e
 }
 
 nphc_status nphc_classify(const nphc_system *S, const nphc_endpoints *ep, double *theta,
-                          int32_t *index, double *energy, double *min_abs_eig, void *stream) {
+                          int32_t *index, double *energy, double *min_abs_eig,
+                          double *log_abs_det, void *stream) {
     nphc_status s;
     if ((s = check_ep(S, ep, true)) != NPHC_OK) return s;
     if (!theta || !index || !energy) return fail(NPHC_EINVAL, "output arrays missing");
     if (S->quad) return fail(NPHC_EINVAL, "classification needs an XY system");
     XYSys xs = S->xs;
-    NPHC_CK(launch_xy_classify(S->M, xs, view(ep), theta, index, energy, min_abs_eig,
+    NPHC_CK(launch_xy_classify(S->M, xs, view(ep), theta, index, energy, min_abs_eig, log_abs_det,
                                (cudaStream_t)stream));
+    return NPHC_OK;
+}
+
+nphc_status nphc_xy_adjoint(const nphc_system *S, int64_t count, const double *theta,
+                            const double *g_energy, const double *g_theta, double *dJ,
+                            void *stream) {
+    if (!S || count < 0 || (count > 0 && !theta) || !dJ) return fail(NPHC_EINVAL, "NULL argument");
+    if (S->quad) return fail(NPHC_EINVAL, "the adjoint needs an XY system");
+    NPHC_CK(launch_xy_adjoint(S->M, S->xs, count, theta, g_energy, g_theta, dJ,
+                              (cudaStream_t)stream));
     return NPHC_OK;
 }
 
@@ -534,7 +547,9 @@ nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
         sizeof(double) * P,             // 28 o_alpha
         sizeof(int32_t) * P,            // 29 o_index
         sizeof(int64_t) * P,            // 30 o_path
-        L.total};                       // 31 workspace
+        L.total,                        // 31 workspace
+        sizeof(double) * P,             // 32 logdet
+        sizeof(double) * P};            // 33 o_logdet
     std::vector<size_t> off(sz.size());
     size_t tot = 0;
     for (size_t i = 0; i < sz.size(); i++) {
@@ -591,6 +606,8 @@ nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
     R->o_index = (int32_t *)at(29);
     R->o_path = (int64_t *)at(30);
     R->ws = at(31);
+    R->logdet = (double *)at(32);
+    R->o_logdet = (double *)at(33);
     R->ws_bytes = L.total;
     R->stream = nullptr;
     R->solved = false;
@@ -656,8 +673,7 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
         WorkList l3 = {R->list[3], R->lcount + 3, nullptr, nullptr, 0};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
                                          R->P, l3, 0, st));
-        // FP64 re-track from t = 0 of FP32 endpoints that did not certify and of hand-offs
-        // whose continuation did not end certified
+        // FP64 re-track from t = 0 of FP32 endpoints that did not certify
         NPHC_CK(launch_compact(v, PRED_UNCERTIFIED_FP32, R->flags, R->list[1], R->lcount + 1, st));
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[1], R->lcount + 1, false, true, R->ws, 2, st)))
             return s;
@@ -673,7 +689,22 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
         WorkList l2 = {R->list[2], R->lcount + 2, nullptr, nullptr, 0};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
                                          R->P, l2, 0, st));
-        NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st));
+        // a solution still reached twice means a path jumped in FP64 too: its paths are
+        // tracked once more with an 8x smaller step ceiling and trust bound (only the
+        // re-tracked entries can have changed: the dedups match just those)
+        NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, R->list[0], R->lcount + 0, st, R->list[2],
+                             R->lcount + 2));
+        NPHC_CK(launch_flag_list(R->list[0], R->lcount + 0, R->P, R->flags, FLAG_RETRACKED_DUP, st));
+        nphc_options strict = *o;
+        strict.h_max = o->h_max / 8.0;
+        strict.h0 = std::min(o->h0, strict.h_max);
+        strict.trust = o->trust / 8.0;
+        if ((s = track_impl(S, &strict, NPHC_PREC_FP64, ep, R->list[0], R->lcount + 0, false, true, R->ws, 4, st)))
+            return s;
+        WorkList l0s = {R->list[0], R->lcount + 0, nullptr, nullptr, 0};
+        NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
+                                         R->P, l0s, 0, st));
+        NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st, R->list[0], R->lcount + 0));
     } else {
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, nullptr, nullptr, false, false, R->ws, 0, st)))
             return s;
@@ -683,7 +714,7 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
                                          R->P, l3, 0, st));
         NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st));
     }
-    NPHC_CK(launch_xy_classify(S->M, xs, v, R->theta, R->index, R->energy, R->mineig, st));
+    NPHC_CK(launch_xy_classify(S->M, xs, v, R->theta, R->index, R->energy, R->mineig, R->logdet, st));
     NPHC_CK(launch_counts(v, R->flags, R->index, R->counts, st));
     R->stream = st;
     R->solved = true;
@@ -719,7 +750,8 @@ nphc_status nphc_result_counts(const nphc_result *R, int64_t *counts) {
 }
 
 nphc_status nphc_result_copy_sps(const nphc_result *R, int64_t cap, double *theta, double *energy,
-                                 int32_t *index, double *alpha, int64_t *path, int64_t *n_out) {
+                                 int32_t *index, double *alpha, int64_t *path, double *log_abs_det,
+                                 int64_t *n_out) {
     if (!R || !n_out || cap < 0) return fail(NPHC_EINVAL, "invalid argument");
     if (!R->solved) return fail(NPHC_ESTATE, "no solve on this result");
     if (R->M == 0) return fail(NPHC_EINVAL, "a generic quadratic system has no stationary points; copy its endpoints");
@@ -727,7 +759,7 @@ nphc_status nphc_result_copy_sps(const nphc_result *R, int64_t cap, double *thet
     NPHC_CK(launch_real_list(view(&R->ep), R->real_list, R->lcount + 4, st));
     NPHC_CK(launch_gather_sps(view(&R->ep), R->M, R->real_list, R->lcount + 4, R->P, R->theta,
                               R->index, R->energy, R->o_theta, R->o_index, R->o_energy, R->o_alpha,
-                              R->o_path, st));
+                              R->o_path, R->logdet, R->o_logdet, st));
     int32_t cnt = 0;
     NPHC_CK(cudaMemcpyAsync(&cnt, R->lcount + 4, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     NPHC_CK(cudaStreamSynchronize(st));
@@ -743,11 +775,12 @@ nphc_status nphc_result_copy_sps(const nphc_result *R, int64_t cap, double *thet
     std::vector<int64_t> ord(cnt);
     std::iota(ord.begin(), ord.end(), 0);
     std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) { return pa[a] < pa[b]; });
-    std::vector<double> th_all(cnt * M), en_all(cnt), al_all(cnt);
+    std::vector<double> th_all(cnt * M), en_all(cnt), al_all(cnt), ld_all(cnt);
     std::vector<int32_t> ix_all(cnt);
     NPHC_CK(cudaMemcpy(th_all.data(), R->o_theta, sizeof(double) * cnt * M, cudaMemcpyDeviceToHost));
     NPHC_CK(cudaMemcpy(en_all.data(), R->o_energy, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
     NPHC_CK(cudaMemcpy(al_all.data(), R->o_alpha, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
+    NPHC_CK(cudaMemcpy(ld_all.data(), R->o_logdet, sizeof(double) * cnt, cudaMemcpyDeviceToHost));
     NPHC_CK(cudaMemcpy(ix_all.data(), R->o_index, sizeof(int32_t) * cnt, cudaMemcpyDeviceToHost));
     for (int64_t i = 0; i < k; i++) {
         const int64_t j = ord[i];
@@ -756,6 +789,7 @@ nphc_status nphc_result_copy_sps(const nphc_result *R, int64_t cap, double *thet
         if (index) index[i] = ix_all[j];
         if (alpha) alpha[i] = al_all[j];
         if (path) path[i] = pa[j];
+        if (log_abs_det) log_abs_det[i] = ld_all[j];
     }
     return NPHC_OK;
 }

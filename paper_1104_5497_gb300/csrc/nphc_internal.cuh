@@ -185,17 +185,24 @@ cudaError_t launch_xy_track_f32(int M, const XYSys &sys, const XYCtl &ctl, const
                                 const WorkList &wl, int block, int grid, cudaStream_t st);
 cudaError_t launch_xy_track_f64(int M, const XYSys &sys, const XYCtl &ctl, const EPView &ep,
                                 const WorkList &wl, int block, int grid, cudaStream_t st);
+// FP64 tracking with one path per warp (xy_track_warp.cuh), for short lists.
+cudaError_t launch_xy_track_f64_warp(int M, const XYSys &sys, const XYCtl &ctl, const EPView &ep,
+                                     const WorkList &wl, cudaStream_t st);
 cudaError_t launch_xy_refine_certify(int M, const XYSys &sys, double tol_sol, double refine_eps,
                                      int refine_iters, const EPView &ep, int64_t cap,
                                      const WorkList &wl, int shortcut, cudaStream_t st);
 cudaError_t launch_xy_classify(int M, const XYSys &sys, const EPView &ep, double *theta,
                                int32_t *index, double *energy, double *min_eig,
+                               double *log_abs_det,
                                cudaStream_t st);
 cudaError_t launch_quad_track(int n, const QSys &sys, const XYCtl &ctl, const EPView &ep,
                               const WorkList &wl, int grid, cudaStream_t st);
 cudaError_t launch_quad_refine_certify(int n, const QSys &sys, double tol_sol, double refine_eps,
                                        int refine_iters, const EPView &ep, int64_t cap,
                                        const WorkList &wl, cudaStream_t st);
+cudaError_t launch_xy_adjoint(int M, const XYSys &sys, int64_t count, const double *theta,
+                              const double *g_energy, const double *g_theta, double *dJ,
+                              cudaStream_t st);
 // Host-side count of kernel launches made by this library (for the result counters).
 int64_t nphc_launch_counter(int64_t add);
 int xy_track_f32_block(int M);

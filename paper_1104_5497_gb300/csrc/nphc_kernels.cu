@@ -19,14 +19,9 @@ __global__ void compact_kernel(const EPView ep, int pred, int32_t *flags, int32_
         take = ep.status[e] == NPHC_PATH_HANDOFF;
         if (take) flags[e] |= FLAG_FP64_CONTINUED;
     } else if (pred == PRED_UNCERTIFIED_FP32) {
-        // FP32 endpoints that do not certify, and FP32 hand-offs whose FP64 continuation
-        // did not end certified (the FP32 pass stalled on them, so its trajectory near the
-        // hand-off is not trusted): both are tracked again from t = 0 in FP64
-        const int c = ep.cls[e], f = flags[e];
-        const bool certified = c == NPHC_END_REAL || c == NPHC_END_NONREAL || c == NPHC_END_UNDECIDED;
-        take = !(f & FLAG_RETRACKED) &&
-               ((c == NPHC_END_SINGULAR && !(f & FLAG_FP64_CONTINUED)) ||
-                ((f & FLAG_FP64_CONTINUED) && !certified));
+        // FP32 endpoints that do not certify are tracked again from t = 0 in FP64 (hand-offs
+        // already continued in FP64 from where they entered the end zone)
+        take = ep.cls[e] == NPHC_END_SINGULAR && !(flags[e] & (FLAG_FP64_CONTINUED | FLAG_RETRACKED));
         if (take) flags[e] |= FLAG_RETRACKED;
     } else if (pred == PRED_REACHED) {
         // endpoints to refine; every other path gets its final class here
@@ -164,10 +159,20 @@ __device__ __forceinline__ void dd_pair(const EPView &ep, DedupScratch &w, int32
 }
 
 // phase 2: compare with the endpoints of the own and the neighbouring cells at level L(e)
+// The entry a dedup thread matches: every entry, or only those of mlist (entries whose
+// solution may have changed since the last dedup, e.g. after a re-track).
+__device__ __forceinline__ int64_t dd_entry(const EPView &ep, const int32_t *mlist,
+                                            const int32_t *mcount) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (mlist) return i < *mcount ? (int64_t)mlist[i] : -1;
+    return i < ep.count ? i : -1;
+}
+
 __global__ void dedup_match_kernel(const EPView ep, int n, double delta0, DedupScratch w,
-                                   int32_t *list, int32_t *count) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ep.count || !is_certified(ep.cls[e])) return;
+                                   int32_t *list, int32_t *count, const int32_t *mlist,
+                                   const int32_t *mcount) {
+    const int64_t e = dd_entry(ep, mlist, mcount);
+    if (e < 0 || !is_certified(ep.cls[e])) return;
     const int L = dd_level(ep.beta[e], delta0);
     if (L >= DD_LEVELS) return;   // phase 3
     double v[4];
@@ -212,9 +217,10 @@ __global__ void dedup_match_kernel(const EPView ep, int n, double delta0, DedupS
 }
 
 __global__ void dedup_unhashed_kernel(const EPView ep, int n, double delta0, DedupScratch w,
-                                      int32_t *list, int32_t *count) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= ep.count || !is_certified(ep.cls[e]) || dd_level(ep.beta[e], delta0) < DD_LEVELS) return;
+                                      int32_t *list, int32_t *count, const int32_t *mlist,
+                                      const int32_t *mcount) {
+    const int64_t e = dd_entry(ep, mlist, mcount);
+    if (e < 0 || !is_certified(ep.cls[e]) || dd_level(ep.beta[e], delta0) < DD_LEVELS) return;
     for (int64_t j = 0; j < ep.count; j++) {
         if (j == e) continue;
         const int cj = ep.cls[j];
@@ -272,7 +278,8 @@ __global__ void iota_kernel(int64_t *path, int64_t n) {
 __global__ void gather_sps_kernel(const EPView ep, int M, const int32_t *list, const int32_t *count,
                                   const double *theta, const int32_t *index, const double *energy,
                                   double *o_theta, int32_t *o_index, double *o_energy,
-                                  double *o_alpha, int64_t *o_path) {
+                                  double *o_alpha, int64_t *o_path, const double *logdet,
+                                  double *o_logdet) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= *count) return;
     const int64_t e = list[i];
@@ -282,6 +289,7 @@ __global__ void gather_sps_kernel(const EPView ep, int M, const int32_t *list, c
     o_energy[i] = energy[e];
     o_alpha[i] = ep.alpha[e];
     o_path[i] = ep.path[e];
+    o_logdet[i] = logdet[e];
 }
 
 // ------------------------------------------------------------- launchers --
@@ -304,7 +312,8 @@ cudaError_t launch_flag_list(const int32_t *list, const int32_t *count, int64_t 
 }
 
 cudaError_t launch_dedup(const EPView &ep, int n, double delta, DedupScratch w, int32_t *list,
-                         int32_t *count, cudaStream_t st) {
+                         int32_t *count, cudaStream_t st, const int32_t *mlist,
+                         const int32_t *mcount) {
     if (ep.count == 0) return cudaSuccess;
     cudaError_t err;
     const size_t slots = (size_t)DD_LEVELS * w.table_size;
@@ -315,9 +324,9 @@ cudaError_t launch_dedup(const EPView &ep, int n, double delta, DedupScratch w, 
     const int g = blocks_for(ep.count, 256);
     dedup_insert_kernel<<<g, 256, 0, st>>>(ep, n, delta, w);
     nphc_launch_counter(1);
-    dedup_match_kernel<<<g, 256, 0, st>>>(ep, n, delta, w, list, count);
+    dedup_match_kernel<<<g, 256, 0, st>>>(ep, n, delta, w, list, count, mlist, mcount);
     nphc_launch_counter(1);
-    dedup_unhashed_kernel<<<g, 256, 0, st>>>(ep, n, delta, w, list, count);
+    dedup_unhashed_kernel<<<g, 256, 0, st>>>(ep, n, delta, w, list, count, mlist, mcount);
     nphc_launch_counter(1);
     return cudaGetLastError();
 }
@@ -349,10 +358,12 @@ cudaError_t launch_iota(int64_t *path, int64_t n, cudaStream_t st) {
 cudaError_t launch_gather_sps(const EPView &ep, int M, const int32_t *list, const int32_t *count,
                               int64_t cap, const double *theta, const int32_t *index,
                               const double *energy, double *o_theta, int32_t *o_index,
-                              double *o_energy, double *o_alpha, int64_t *o_path, cudaStream_t st) {
+                              double *o_energy, double *o_alpha, int64_t *o_path,
+                              const double *logdet, double *o_logdet, cudaStream_t st) {
     if (cap == 0) return cudaSuccess;
     gather_sps_kernel<<<blocks_for(cap, 256), 256, 0, st>>>(ep, M, list, count, theta, index, energy,
-                                                          o_theta, o_index, o_energy, o_alpha, o_path);
+                                                          o_theta, o_index, o_energy, o_alpha, o_path,
+                                                          logdet, o_logdet);
     nphc_launch_counter(1);
     return cudaGetLastError();
 }

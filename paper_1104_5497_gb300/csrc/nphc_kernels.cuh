@@ -22,8 +22,12 @@ cudaError_t launch_compact(const EPView &ep, int pred, int32_t *flags, int32_t *
                            int32_t *count, cudaStream_t st);
 cudaError_t launch_flag_list(const int32_t *list, const int32_t *count, int64_t cap,
                              int32_t *flags, int32_t bit, cudaStream_t st);
+// Marks duplicates among the certified entries of ep.  mlist / mcount (device, may be
+// NULL): only the pairs with an entry of mlist are examined (every other pair was
+// settled by an earlier dedup and its entries left unchanged since).
 cudaError_t launch_dedup(const EPView &ep, int n, double delta, DedupScratch w, int32_t *list,
-                         int32_t *count, cudaStream_t st);
+                         int32_t *count, cudaStream_t st, const int32_t *mlist = nullptr,
+                         const int32_t *mcount = nullptr);
 cudaError_t launch_counts(const EPView &ep, const int32_t *flags, const int32_t *index,
                           int64_t *counts, cudaStream_t st);
 cudaError_t launch_real_list(const EPView &ep, int32_t *list, int32_t *count, cudaStream_t st);
@@ -31,4 +35,5 @@ cudaError_t launch_iota(int64_t *path, int64_t n, cudaStream_t st);
 cudaError_t launch_gather_sps(const EPView &ep, int M, const int32_t *list, const int32_t *count,
                               int64_t cap, const double *theta, const int32_t *index,
                               const double *energy, double *o_theta, int32_t *o_index,
-                              double *o_energy, double *o_alpha, int64_t *o_path, cudaStream_t st);
+                              double *o_energy, double *o_alpha, int64_t *o_path,
+                              const double *logdet, double *o_logdet, cudaStream_t st);

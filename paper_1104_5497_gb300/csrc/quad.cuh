@@ -205,7 +205,17 @@ struct EGQuad {
                 if (T.b >= 0) G.setS(i, T.b, cadd(G.S(i, T.b), cmul(c, wa)));
             }
         }
+        // ||DP||_F, kept in the unused second half of R for jac_fro
+        double f = 0.0;
+#pragma unroll 1
+        for (int c = 0; c < NV; c++)
+#pragma unroll 1
+            for (int i = 0; i < NV; i++) f += cabs2(G.S(i, c));
+        G.v(EGLayout<NV>::R).set(NV, cx<double>{sqrt(f), 0.0});
         return eg_qr<NV>(G);
+    }
+    static __device__ __forceinline__ double jac_fro(const EG<NV> &G, const Sys &S) {
+        return G.v(EGLayout<NV>::R).get(NV).re;
     }
     static __device__ __forceinline__ double solve(const EG<NV> &G, const Sys &S) {
         const EGVec R = G.v(EGLayout<NV>::R), Dv = G.v(EGLayout<NV>::D);

@@ -17,6 +17,13 @@ cudaError_t launch_xy_track_f64(int M, const XYSys &sys, const XYCtl &ctl, const
 #undef C
 }
 
+cudaError_t launch_xy_track_f64_warp(int M, const XYSys &sys, const XYCtl &ctl, const EPView &ep,
+                                     const WorkList &wl, cudaStream_t st) {
+#define C(MM) case MM: return launch_xy_track_f64w_m##MM(sys, ctl, ep, wl, st);
+    switch (M) { NPHC_FOR_EACH_M(C) default: return cudaErrorInvalidValue; }
+#undef C
+}
+
 cudaError_t launch_xy_refine_certify(int M, const XYSys &sys, double tol_sol, double refine_eps,
                                      int refine_iters, const EPView &ep, int64_t cap,
                                      const WorkList &wl, int shortcut, cudaStream_t st) {
@@ -25,9 +32,18 @@ cudaError_t launch_xy_refine_certify(int M, const XYSys &sys, double tol_sol, do
 #undef C
 }
 
+cudaError_t launch_xy_adjoint(int M, const XYSys &sys, int64_t count, const double *theta,
+                              const double *g_energy, const double *g_theta, double *dJ,
+                              cudaStream_t st) {
+#define C(MM) case MM: return launch_xy_adjoint_m##MM(sys, count, theta, g_energy, g_theta, dJ, st);
+    switch (M) { NPHC_FOR_EACH_M(C) default: return cudaErrorInvalidValue; }
+#undef C
+}
+
 cudaError_t launch_xy_classify(int M, const XYSys &sys, const EPView &ep, double *theta,
-                               int32_t *index, double *energy, double *min_eig, cudaStream_t st) {
-#define C(MM) case MM: return launch_xy_classify_m##MM(sys, ep, theta, index, energy, min_eig, st);
+                               int32_t *index, double *energy, double *min_eig,
+                               double *log_abs_det, cudaStream_t st) {
+#define C(MM) case MM: return launch_xy_classify_m##MM(sys, ep, theta, index, energy, min_eig, log_abs_det, st);
     switch (M) { NPHC_FOR_EACH_M(C) default: return cudaErrorInvalidValue; }
 #undef C
 }

@@ -16,11 +16,15 @@
                                           const WorkList &, int, cudaStream_t);              \
     cudaError_t launch_xy_track_f64_m##MM(const XYSys &, const XYCtl &, const EPView &,     \
                                           const WorkList &, int, cudaStream_t);              \
+    cudaError_t launch_xy_track_f64w_m##MM(const XYSys &, const XYCtl &, const EPView &,    \
+                                           const WorkList &, cudaStream_t);                 \
     cudaError_t launch_xy_refine_certify_m##MM(const XYSys &, double, double, int,          \
                                                const EPView &, int64_t, const WorkList &,   \
                                                int, cudaStream_t);                          \
+    cudaError_t launch_xy_adjoint_m##MM(const XYSys &, int64_t, const double *, const double *, \
+                                        const double *, double *, cudaStream_t);              \
     cudaError_t launch_xy_classify_m##MM(const XYSys &, const EPView &, double *, int32_t *, \
-                                         double *, double *, cudaStream_t);
+                                         double *, double *, double *, cudaStream_t);
 NPHC_FOR_EACH_M(NPHC_DECL)
 #undef NPHC_DECL
 

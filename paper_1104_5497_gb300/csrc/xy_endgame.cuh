@@ -36,6 +36,18 @@
 
 #define EG_BLOCK 32
 
+// The certification threshold: half of Smale's (13 - 3 sqrt 17) / 4.  alphaCertified
+// decides in exact arithmetic; an FP64 test keeps a factor of two so that rounding cannot
+// carry a point near a singular solution set across the constant (on the N = 4 ring a
+// point of the positive-dimensional family reached alpha = 0.115 < 0.158).
+#define NPHC_ALPHA_CERT (0.5 * (13.0 - 3.0 * sqrt(17.0)) / 4.0)
+
+// An endpoint whose Jacobian has Frobenius condition number ||DP||_F ||DP^-1||_F above
+// this is singular: at a point of a positive-dimensional solution set P vanishes to
+// double-double precision (beta is tiny) while rounding leaves the computed DP^-1 merely
+// huge, and the soft alpha test alone can pass there.
+#define NPHC_KAPPA_SING 1e12
+
 // One thread's array of complex doubles in shared memory.
 struct EGVec {
     cx<double> *p;
@@ -341,18 +353,35 @@ struct EGXY {
     static __device__ __forceinline__ double inv_fro(const EG<M> &G, const Sys &S) {
         return eg_inv_fro<M>(G, S.Jd);
     }
+    // ||DP||_F after factor: gradient row k has J_kj y_k, -J_kj x_k (free j != k), -w_k,
+    // u_k; constraint row k has 2 x_k, 2 y_k
+    static __device__ __forceinline__ double jac_fro(const EG<M> &G, const Sys &S) {
+        using L = EGLayout<M>;
+        double f = 0.0;
+#pragma unroll 1
+        for (int k = 0; k < M; k++) {
+            const double xy = cabs2(G.v(L::X).get(k)) + cabs2(G.v(L::Y).get(k));
+            double jj = 0.0;
+#pragma unroll 1
+            for (int j = 0; j < M; j++) jj += S.Jd[k * NPHC_JSTRIDE + j] * S.Jd[k * NPHC_JSTRIDE + j];
+            f += jj * xy + cabs2(G.v(L::AD).get(k)) + cabs2(G.v(L::BD).get(k)) + 4.0 * xy;
+        }
+        return sqrt(f);
+    }
     static __device__ __forceinline__ double d2norm(const Sys &S) { return S.d2norm; }
 };
 
-// beta = ||DP^-1 P||, ||DP^-1||_F and ||P||_inf at the point in G.  False if singular.
+// beta = ||DP^-1 P||, ||DP^-1||_F and ||P||_inf at the point in G.  False if singular,
+// counting a Frobenius condition number above NPHC_KAPPA_SING as singular.
 template <class Q>
 __device__ bool eg_beta_invnorm_p(const EG<Q::DIM> &G, const typename Q::Sys &S, double &beta,
                                   double &invF, double &res) {
     res = Q::minus_p(G, S);
     if (!Q::factor(G, S)) return false;
+    const double fro = Q::jac_fro(G, S);
     beta = sqrt(Q::solve(G, S));
     invF = Q::inv_fro(G, S);
-    return isfinite(beta) && isfinite(invF);
+    return isfinite(beta) && isfinite(invF) && fro * invF <= NPHC_KAPPA_SING;
 }
 
 // Refinement and certification of entry e.  Returns true when e still needs the
@@ -364,7 +393,7 @@ __device__ bool eg_refine_certify_one(const EG<Q::DIM> &G, const typename Q::Sys
     constexpr int NZ = Q::NZ;
     const EGVec Dv = G.v(EGLayout<Q::DIM>::D);
     const int64_t cnt = ep.count;
-    const double alpha0 = (13.0 - 3.0 * sqrt(17.0)) / 4.0;
+    const double alpha0 = NPHC_ALPHA_CERT;
     const int st = ep.status[e];
     const bool sc = shortcut && st == NPHC_PATH_HANDOFF;
     if (!sc) {
@@ -463,7 +492,7 @@ template <class Q>
 __device__ void eg_real_test(const EG<Q::DIM> &G, const typename Q::Sys &S, const EPView &ep,
                              int64_t e) {
     const int64_t cnt = ep.count;
-    const double alpha0 = (13.0 - 3.0 * sqrt(17.0)) / 4.0;
+    const double alpha0 = NPHC_ALPHA_CERT;
     double im2 = 0.0;
 #pragma unroll 1
     for (int k = 0; k < Q::NZ; k++) {
@@ -524,7 +553,7 @@ __global__ void __launch_bounds__(EG_BLOCK)
 template <int M>
 __global__ void __launch_bounds__(128)
     xy_classify_kernel(const __grid_constant__ XYSys S, const EPView ep, double *theta,
-                       int32_t *index, double *energy, double *min_eig) {
+                       int32_t *index, double *energy, double *min_eig, double *log_abs_det) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t cnt = ep.count;
     if (e >= cnt) return;
@@ -532,6 +561,7 @@ __global__ void __launch_bounds__(128)
         index[e] = -1;
         energy[e] = 0.0;
         if (min_eig) min_eig[e] = 0.0;
+        if (log_abs_det) log_abs_det[e] = 0.0;
         for (int k = 0; k < M; k++) theta[k * cnt + e] = 0.0;
         return;
     }
@@ -596,13 +626,119 @@ __global__ void __launch_bounds__(128)
             }
     }
     int neg = 0;
-    double mn = INFINITY;
+    double mn = INFINITY, ld = 0.0;
     for (int k = 0; k < M; k++) {
         const double w = H[k * M + k];
         if (w < 0.0) neg++;
         mn = fmin(mn, fabs(w));
+        ld += log(fabs(w));   // log |det H| = sum of log |eigenvalue|
     }
     index[e] = neg;
     energy[e] = V;
     if (min_eig) min_eig[e] = mn;
+    if (log_abs_det) log_abs_det[e] = ld;
 }
+
+// Gradient with respect to the couplings of a loss L(V*, theta*) summed over real
+// stationary points (not part of the paper's method: derivatives of its outputs).  At
+// theta* the gradient G = grad_theta V vanishes, so dV*/dJ_ij = 1 - cos(theta_i - theta_j)
+// (envelope), and d theta*/dJ_ij = -H^-1 dG/dJ_ij (implicit function theorem); with
+// H lambda = dL/dtheta (lambda_N = 0) and dG_i/dJ_ij = sin(theta_i - theta_j) = -dG_j/dJ_ij:
+//   dL/dJ_ij = gV (1 - cos(theta_i - theta_j)) - (lambda_i - lambda_j) sin(theta_i - theta_j).
+// One stationary point per thread (theta: [count * M] row per point; g_energy [count] and
+// g_theta [count * M] may be NULL), the block's sum in shared memory, then one atomic add
+// per coupling and block into dJ (N x N, symmetric: both J_ij and J_ji get the value of
+// the one parameter).
+template <int M>
+__global__ void __launch_bounds__(128)
+    xy_adjoint_kernel(const __grid_constant__ XYSys S, int64_t count, const double *theta,
+                      const double *g_energy, const double *g_theta, double *dJ) {
+    constexpr int N = M + 1;
+    __shared__ double acc[N * N];
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) acc[i] = 0.0;
+    __syncthreads();
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < count) {
+        const double *J = S.Jd;
+        double c[N], s[N], lam[N];
+#pragma unroll 1
+        for (int k = 0; k < M; k++) sincos(theta[e * M + k], &s[k], &c[k]);
+        c[M] = 1.0;
+        s[M] = 0.0;
+#pragma unroll 1
+        for (int k = 0; k < N; k++) lam[k] = 0.0;
+        bool ok = true;
+        if (g_theta) {
+            // H lambda = g by Gaussian elimination with partial pivoting; cos(a - b) =
+            // c_a c_b + s_a s_b
+            double H[M * M], b[M];
+#pragma unroll 1
+            for (int k = 0; k < M; k++) {
+                double d = 0.0;
+#pragma unroll 1
+                for (int j = 0; j < N; j++)
+                    if (j != k) d += J[k * NPHC_JSTRIDE + j] * (c[k] * c[j] + s[k] * s[j]);
+#pragma unroll 1
+                for (int l = 0; l < M; l++)
+                    H[k * M + l] = (k == l) ? d : -J[k * NPHC_JSTRIDE + l] * (c[k] * c[l] + s[k] * s[l]);
+                b[k] = g_theta[e * M + k];
+            }
+#pragma unroll 1
+            for (int k = 0; k < M; k++) {
+                int p = k;
+#pragma unroll 1
+                for (int i = k + 1; i < M; i++)
+                    if (fabs(H[i * M + k]) > fabs(H[p * M + k])) p = i;
+                if (H[p * M + k] == 0.0) {
+                    ok = false;
+                    break;
+                }
+                if (p != k) {
+#pragma unroll 1
+                    for (int l = 0; l < M; l++) {
+                        const double tmp = H[k * M + l];
+                        H[k * M + l] = H[p * M + l];
+                        H[p * M + l] = tmp;
+                    }
+                    const double tb = b[k];
+                    b[k] = b[p];
+                    b[p] = tb;
+                }
+                const double ip = 1.0 / H[k * M + k];
+#pragma unroll 1
+                for (int i = k + 1; i < M; i++) {
+                    const double f = H[i * M + k] * ip;
+#pragma unroll 1
+                    for (int l = k + 1; l < M; l++) H[i * M + l] -= f * H[k * M + l];
+                    b[i] -= f * b[k];
+                }
+            }
+            if (ok) {
+#pragma unroll 1
+                for (int k = M - 1; k >= 0; k--) {
+                    double v = b[k];
+#pragma unroll 1
+                    for (int l = k + 1; l < M; l++) v -= H[k * M + l] * lam[l];
+                    lam[k] = v / H[k * M + k];
+                }
+            }
+        }
+        if (ok) {
+            const double gv = g_energy ? g_energy[e] : 0.0;
+#pragma unroll 1
+            for (int i = 0; i < N; i++)
+#pragma unroll 1
+                for (int j = i + 1; j < N; j++) {
+                    const double cd = c[i] * c[j] + s[i] * s[j];   // cos(theta_i - theta_j)
+                    const double sd = s[i] * c[j] - c[i] * s[j];   // sin(theta_i - theta_j)
+                    const double v = gv * (1.0 - cd) - (lam[i] - lam[j]) * sd;
+                    atomicAdd(&acc[i * N + j], v);
+                    atomicAdd(&acc[j * N + i], v);
+                }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x)
+        if (acc[i] != 0.0) atomicAdd(&dJ[i], acc[i]);
+}
+

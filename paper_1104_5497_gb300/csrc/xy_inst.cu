@@ -6,6 +6,36 @@
 
 #if NPHC_INST_KIND == 0 || NPHC_INST_KIND == 1
 #include "xy_track.cuh"
+#if NPHC_INST_KIND == 1
+#include "xy_track_warp.cuh"
+
+// one path per warp (short FP64 lists), 4 warps per block
+cudaError_t NPHC_CAT(launch_xy_track_f64w_m, NPHC_INST_M)(const XYSys &sys, const XYCtl &ctl,
+                                                          const EPView &ep, const WorkList &wl,
+                                                          cudaStream_t st) {
+    constexpr int M = NPHC_INST_M, WARPS = 4;
+    if (ep.count <= 0) return cudaSuccess;
+    const size_t smem = warp_track_smem_per_warp<M>() * WARPS;
+    auto k = xy_track_warp64_kernel<M, WARPS>;
+    static bool attr_set = false;   // once per process for this instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 32 * WARPS, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t full = (int64_t)sms * (per > 0 ? per : 1);
+    const int64_t need = (ep.count + WARPS - 1) / WARPS;   // the list is at most ep.count long
+    const int grid = (int)(need < full ? need : full);
+    k<<<grid, 32 * WARPS, smem, st>>>(sys, ctl, ep, wl);
+    nphc_launch_counter(1);
+    return cudaGetLastError();
+}
+#endif
 
 #if NPHC_INST_KIND == 0
 using RT = float;
@@ -75,13 +105,26 @@ cudaError_t NPHC_CAT(launch_xy_refine_certify_m, NPHC_INST_M)(const XYSys &sys, 
     return cudaGetLastError();
 }
 
+cudaError_t NPHC_CAT(launch_xy_adjoint_m, NPHC_INST_M)(const XYSys &sys, int64_t count,
+                                                      const double *theta, const double *g_energy,
+                                                      const double *g_theta, double *dJ,
+                                                      cudaStream_t st) {
+    if (count <= 0) return cudaSuccess;
+    const int grid = (int)((count + 127) / 128);
+    xy_adjoint_kernel<NPHC_INST_M><<<grid, 128, 0, st>>>(sys, count, theta, g_energy, g_theta, dJ);
+    nphc_launch_counter(1);
+    return cudaGetLastError();
+}
+
 cudaError_t NPHC_CAT(launch_xy_classify_m, NPHC_INST_M)(const XYSys &sys, const EPView &ep,
                                                        double *theta, int32_t *index,
                                                        double *energy, double *min_eig,
+                                                       double *log_abs_det,
                                                        cudaStream_t st) {
     if (ep.count <= 0) return cudaSuccess;
     const int grid = (int)((ep.count + 127) / 128);
-    xy_classify_kernel<NPHC_INST_M><<<grid, 128, 0, st>>>(sys, ep, theta, index, energy, min_eig);
+    xy_classify_kernel<NPHC_INST_M><<<grid, 128, 0, st>>>(sys, ep, theta, index, energy, min_eig,
+                                                                   log_abs_det);
     nphc_launch_counter(1);
     return cudaGetLastError();
 }

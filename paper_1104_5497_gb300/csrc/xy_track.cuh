@@ -28,12 +28,14 @@
 // approached with the same power-law growth as paths to infinity, so no growth test
 // can separate them before t = 1).
 // FP32 pass (ctl.handoff = 1): on a step size underflow, ten consecutive rejects, a
-// crawl near t = 1 (1 - t failing to halve
-// within crawl_steps accepted steps) or its own (smaller) attempt budget, it is handed
-// to FP64 (NPHC_PATH_HANDOFF) with its (z, t, h).  FP64 tracks like the oracle: no crawl
-// test, the same step budget and minimum step.  The FP32 bound on the first correction (trust_fp32) keeps its
-// accepted steps no longer than the FP64 tolerance allows, so that it does not step
-// across a sharp turn of the path onto a neighbouring one.
+// crawl near t = 1 (1 - t failing to halve within crawl_steps accepted steps), its own
+// (smaller) attempt budget or a radius crossing within RDIV_BAND close to t = 1, a path
+// is handed to FP64 (NPHC_PATH_HANDOFF) with the (z, t, h) where it entered the end
+// zone 1 - t < CRAWL_ZONE (its current state if it never got there).  FP64 tracks like
+// the oracle: no crawl test, the same step budget and minimum step.  The FP32 bound on
+// the first correction (trust_fp32) keeps its accepted steps no longer than the FP64
+// tolerance allows, so that it does not step across a sharp turn of the path onto a
+// neighbouring one.
 #pragma once
 
 #include "xy_solve.cuh"
@@ -149,6 +151,7 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
     const GVec<R> Z0{st + (0 * NV) * nth + gtid, nth};       // accepted point
     const GVec<R> K1{st + (1 * NV) * nth + gtid, nth};       // dz/dt at Z0
     const GVec<R> AC{st + (2 * NV) * nth + gtid, nth};       // RK4 sum; next K1 in correction
+    const GVec<R> CK{st + (3 * NV) * nth + gtid, nth};       // FP32 pass: hand-off checkpoint
     const int64_t total = worklist_size(wl, ep.count);
     const int64_t cnt = ep.count;
 
@@ -163,6 +166,8 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
     }
     int64_t e = (lane >= lanes) ? -2 : -1;   // entry index; -1 idle, -2 drained
     double t = 0.0, h = 0.0, hacc = 0.0;
+    double tck = 0.0, hck = 0.0;   // checkpoint: the first accepted point with 1 - t < CRAWL_ZONE
+    bool have_ck = false;
     double tmark = 0.0;   // 1 - t recorded every CRAWL_STEPS accepted steps near t = 1
     int since = 0;
     int status = 0, run = 0, rejects = 0, attempts = 0, steps = 0, solves = 0, newton = 0;
@@ -185,6 +190,7 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                     run = 0;
                     rejects = 0;
                     attempts = 0;
+                    have_ck = false;
                     if (C.resume) {
 #pragma unroll 1
                         for (int k = 0; k < NV; k++)
@@ -348,6 +354,18 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                                  : NPHC_PATH_DIVERGED;
                 else if (t >= 1.0)
                     status = NPHC_PATH_REACHED;
+                // FP32 pass: keep the state where the path enters the end zone; a path
+                // that the pass later hands off resumes in FP64 from there, not from the
+                // point where FP32 precision ran out (which can sit off the path when the
+                // endpoint is ill-conditioned; a checkpoint moved forward by later FP32
+                // steps that still looked healthy lost solutions near the radius)
+                if (C.handoff && !have_ck && status == NPHC_PATH_RUNNING && 1.0 - t < CRAWL_ZONE) {
+#pragma unroll 6
+                    for (int k = 0; k < NV; k++) CK.set(k, Z0.get(k));
+                    tck = t;
+                    hck = hacc;
+                    have_ck = true;
+                }
                 // crawl test near t = 1: 1 - t must at least halve every CRAWL_STEPS
                 // accepted steps (paths to nonsingular endpoints finish in a few steps;
                 // a crawl means a singular endpoint, infinity, or precision exhausted)
@@ -375,14 +393,15 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                 status = C.handoff ? NPHC_PATH_HANDOFF : NPHC_PATH_STEP_BUDGET;
         }
         if (act && status != NPHC_PATH_RUNNING) {
+            const bool from_ck = status == NPHC_PATH_HANDOFF && have_ck;
 #pragma unroll 1
             for (int k = 0; k < NV; k++) {
-                const cx<R> v = Z0.get(k);
+                const cx<R> v = from_ck ? CK.get(k) : Z0.get(k);
                 ep.z_re[k * cnt + e] = (double)v.re;
                 ep.z_im[k * cnt + e] = (double)v.im;
             }
-            ep.t[e] = t;
-            ep.h[e] = status == NPHC_PATH_HANDOFF ? hacc : h;
+            ep.t[e] = from_ck ? tck : t;
+            ep.h[e] = from_ck ? hck : (status == NPHC_PATH_HANDOFF ? hacc : h);
             ep.status[e] = status;
             ep.steps[e] = steps;
             ep.solves[e] = solves;

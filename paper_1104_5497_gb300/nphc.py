@@ -94,14 +94,15 @@ def lib():
                        vp, ctypes.c_size_t, vp],
         "nphc_dedup_noalloc": [vp, ctypes.POINTER(nphc_options), ctypes.POINTER(nphc_endpoints),
                                vp, vp, vp],
-        "nphc_classify": [vp, ctypes.POINTER(nphc_endpoints), vp, vp, vp, vp, vp],
+        "nphc_classify": [vp, ctypes.POINTER(nphc_endpoints), vp, vp, vp, vp, vp, vp],
         "nphc_result_create": [vp, ctypes.POINTER(vp)],
         "nphc_solve_into": [vp, ctypes.POINTER(nphc_options), vp, vp],
         "nphc_solve": [vp, ctypes.POINTER(nphc_options), vp, ctypes.POINTER(vp)],
         "nphc_result_counts": [vp, pi64],
-        "nphc_result_copy_sps": [vp, i64, pd, pd, pi32, pd, pi64, pi64],
+        "nphc_result_copy_sps": [vp, i64, pd, pd, pi32, pd, pi64, pd, pi64],
         "nphc_result_copy_endpoints": [vp, i64, pd, pd, pi32, pi32, pi64],
         "nphc_result_endpoints": [vp, ctypes.POINTER(nphc_endpoints)],
+        "nphc_xy_adjoint": [vp, i64, vp, vp, vp, vp, vp],
         "nphc_batch_create": [i32, ctypes.POINTER(vp), ctypes.POINTER(vp)],
         "nphc_batch_solve": [vp, ctypes.POINTER(nphc_options), i32, vp],
         "nphc_batch_result": [vp, i32, ctypes.POINTER(vp)],
@@ -242,14 +243,14 @@ class Result:
         M = self.system.M
         n = ctypes.c_int64()
         _check("nphc_result_copy_sps", lib().nphc_result_copy_sps(self.handle, 0, None, None, None,
-                                                                  None, None, ctypes.byref(n)))
+                                                                  None, None, None, ctypes.byref(n)))
         k = n.value
-        th, en, al = np.zeros((k, M)), np.zeros(k), np.zeros(k)
+        th, en, al, ld = np.zeros((k, M)), np.zeros(k), np.zeros(k), np.zeros(k)
         ix, pa = np.zeros(k, np.int32), np.zeros(k, np.int64)
         _check("nphc_result_copy_sps", lib().nphc_result_copy_sps(self.handle, k, _pd(th), _pd(en),
                                                                   _pi32(ix), _pd(al), _pi64(pa),
-                                                                  ctypes.byref(n)))
-        return dict(theta=th, energy=en, index=ix, alpha=al, path=pa)
+                                                                  _pd(ld), ctypes.byref(n)))
+        return dict(theta=th, energy=en, index=ix, alpha=al, path=pa, log_abs_det=ld)
 
     def endpoints(self) -> dict:
         s = self.system
@@ -396,8 +397,26 @@ def dedup_noalloc(system: System, opts: nphc_options, ep: DeviceEndpoints, dup_l
 
 
 def classify(system: System, ep: DeviceEndpoints, theta, index, energy, min_abs_eig=None,
-             stream=None) -> None:
+             log_abs_det=None, stream=None) -> None:
     s = ep.struct()
     _check("nphc_classify", lib().nphc_classify(
         system.handle, ctypes.byref(s), theta.data_ptr(), index.data_ptr(), energy.data_ptr(),
-        None if min_abs_eig is None else min_abs_eig.data_ptr(), _stream_ptr(stream)))
+        None if min_abs_eig is None else min_abs_eig.data_ptr(),
+        None if log_abs_det is None else log_abs_det.data_ptr(), _stream_ptr(stream)))
+
+
+def xy_adjoint(system: System, theta, g_energy=None, g_theta=None, dJ=None, stream=None):
+    """nphc_xy_adjoint on device tensors: theta [count, N-1], g_energy [count],
+    g_theta [count, N-1] (float64, cuda).  Returns dJ [N, N] (accumulated into dJ if given)."""
+    import torch
+    if dJ is None:
+        dJ = torch.zeros(system.N, system.N, dtype=torch.float64, device=theta.device)
+    theta = theta.contiguous()
+    ge = None if g_energy is None else g_energy.contiguous()
+    gt = None if g_theta is None else g_theta.contiguous()
+    _check("nphc_xy_adjoint", lib().nphc_xy_adjoint(
+        system.handle, int(theta.shape[0]), theta.data_ptr(),
+        None if ge is None else ge.data_ptr(), None if gt is None else gt.data_ptr(),
+        dJ.data_ptr(), _stream_ptr(stream)))
+    return dJ
+

@@ -39,13 +39,16 @@ def test_classify_oracle_points(N, sigma, seed):
     index = torch.zeros(c, dtype=torch.int32, device="cuda")
     energy = torch.zeros(c, dtype=torch.float64, device="cuda")
     mineig = torch.zeros(c, dtype=torch.float64, device="cuda")
-    N_.classify(system, ep, theta, index, energy, mineig)
+    logdet = torch.zeros(c, dtype=torch.float64, device="cuda")
+    N_.classify(system, ep, theta, index, energy, mineig, logdet)
     torch.cuda.synchronize()
     th, ix, en, me = theta.cpu().numpy().T, index.cpu().numpy(), energy.cpu().numpy(), mineig.cpu().numpy()
+    ld = logdet.cpu().numpy()
     for i, s in enumerate(ref["sps"]):
         assert torus_dist(th[i], s["theta"]) < 1e-12, i
         assert abs(en[i] - s["energy"]) < 1e-11, (i, en[i], s["energy"])
         assert abs(me[i] - s["min_abs_eig"]) < 1e-9 * (1 + s["min_abs_eig"]), (i, me[i], s["min_abs_eig"])
+        assert abs(ld[i] - s["log_abs_det"]) < 1e-9 * (1 + abs(s["log_abs_det"])), (i, ld[i])
         assert ix[i] == s["index"], (i, ix[i], s["index"])
 
 

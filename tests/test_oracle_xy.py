@@ -141,6 +141,9 @@ def test_jacobian_hessian_determinant_identity(N, sigma):
         _, D = T.eval_jac(s["z"].real)
         ratio = np.linalg.det(D) / ((-2) ** (N - 1) * np.linalg.det(s["hessian"]))
         assert abs(ratio - 1) < 1e-9
+        # the classifier's log |det H| (sum of log |eigenvalue|) by the same identity
+        ld = np.log(abs(np.linalg.det(D))) - (N - 1) * np.log(2.0)
+        assert abs(ld - s["log_abs_det"]) < 1e-9 * max(1.0, abs(ld))
 
 
 def test_d2_norm_closed_form():
