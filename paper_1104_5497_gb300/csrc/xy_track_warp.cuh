@@ -37,7 +37,8 @@ struct WarpLayout {
     static constexpr int Q0 = P0 + M;
     static constexpr int P1 = Q0 + M;
     static constexpr int Q1 = P1 + M;
-    static constexpr int TOTAL = Q1 + M;
+    static constexpr int SC = Q1 + M;     // reflector scalars of the current Householder step
+    static constexpr int TOTAL = SC + 2;
 };
 
 template <int M>
@@ -213,25 +214,29 @@ __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, d
         if (two_rhs) P.A(k, M + 1) = b1;
     }
     __syncwarp();
-    // ---- Householder QR, one column per lane (every lane forms the reflector itself
-    // from column k, read by broadcast)
+    // ---- Householder QR, one column per lane; lane k forms the reflector of step k
+    // (FP64 work is paid per active lane: the other lanes read its scalars)
     const int ncol = two_rhs ? M + 2 : M + 1;
     bool ok = true;
 #pragma unroll 1
     for (int k = 0; k < M; k++) {
-        const cx<double> al = P.A(k, k);
-        double xn2 = 0.0;
+        if (lane == k) {
+            const cx<double> al = P.A(k, k);
+            double xn2 = 0.0;
 #pragma unroll 1
-        for (int i = k + 1; i < M; i++) xn2 += cabs2(P.A(i, k));
-        const double an = sqrt(cabs2(al) + xn2);
-        ok = ok && (an > 0.0);
-        const double beta = al.re >= 0.0 ? -an : an;
-        const double ib = 1.0 / beta;
-        const cx<double> tauc = cx<double>{(beta - al.re) * ib, al.im * ib};   // conj(tau)
-        const cx<double> sc = crecip(cx<double>{al.re - beta, al.im});
-        __syncwarp();   // every lane has read column k
+            for (int i = k + 1; i < M; i++) xn2 += cabs2(P.A(i, k));
+            const double an = sqrt(cabs2(al) + xn2);
+            const double beta = al.re >= 0.0 ? -an : an;
+            const double ib = 1.0 / beta;
+            P.at(L::SC, 0) = cx<double>{(beta - al.re) * ib, al.im * ib};   // conj(tau)
+            P.at(L::SC, 1) = crecip(cx<double>{al.re - beta, al.im});        // 1 / (al - beta)
+            P.A(k, k) = cx<double>{beta, an > 0.0 ? 1.0 : 0.0};              // flag in .im
+        }
+        __syncwarp();
+        ok = ok && P.A(k, k).im != 0.0;
+        const cx<double> tauc = P.at(L::SC, 0);
         // the reflector (1, v_{k+1}, .., v_{M-1}) replaces column k below the diagonal
-        if (lane > k && lane < M) P.A(lane, k) = cmul(P.A(lane, k), sc);
+        if (lane > k && lane < M) P.A(lane, k) = cmul(P.A(lane, k), P.at(L::SC, 1));
         __syncwarp();
         const int c = lane;
         if (c > k && c < ncol) {
@@ -244,24 +249,22 @@ __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, d
             for (int i = k + 1; i < M; i++) P.A(i, c) = csub(P.A(i, c), cmul(P.A(i, k), wv));
         }
         __syncwarp();
-        if (lane == k) P.A(k, k) = cx<double>{beta, 0.0};
+        if (lane == k) P.A(k, k).im = 0.0;   // R_kk = beta, real
         __syncwarp();
     }
-    // ---- back substitution, one row per lane
+    // ---- back substitution: lane k scales row k, lanes i < k eliminate it
 #pragma unroll 1
     for (int k = M - 1; k >= 0; k--) {
-        const double ir = 1.0 / P.A(k, k).re;
-        const cx<double> s0 = cscale(ir, P.A(k, M));
-        const cx<double> s1 = two_rhs ? cscale(ir, P.A(k, M + 1)) : cx<double>{0.0, 0.0};
+        if (lane == k) {
+            const double ir = 1.0 / P.A(k, k).re;
+            P.A(k, M) = cscale(ir, P.A(k, M));
+            if (two_rhs) P.A(k, M + 1) = cscale(ir, P.A(k, M + 1));
+        }
         __syncwarp();
-        const int i = lane;
-        if (i < k) {
-            const cx<double> Rik = P.A(i, k);
-            P.A(i, M) = csub(P.A(i, M), cmul(Rik, s0));
-            if (two_rhs) P.A(i, M + 1) = csub(P.A(i, M + 1), cmul(Rik, s1));
-        } else if (i == k) {
-            P.A(k, M) = s0;
-            if (two_rhs) P.A(k, M + 1) = s1;
+        if (lane < k) {
+            const cx<double> Rik = P.A(lane, k);
+            P.A(lane, M) = csub(P.A(lane, M), cmul(Rik, P.A(k, M)));
+            if (two_rhs) P.A(lane, M + 1) = csub(P.A(lane, M + 1), cmul(Rik, P.A(k, M + 1)));
         }
         __syncwarp();
     }

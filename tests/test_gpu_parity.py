@@ -32,7 +32,7 @@ def test_parity_n8_workload(prec):
     N_ = nphc()
     inst = I.workload_n8()
     p = N_.PREC_MIXED if prec == "mixed" else N_.PREC_FP64
-    res, counts, ref = compare_with_oracle(inst.N, inst.sigma, inst.gamma, p, extra=2)
+    res, counts, ref = compare_with_oracle(inst.N, inst.sigma, inst.gamma, p)
     assert counts["paths"] == 4 ** (inst.N - 1)
 
 
