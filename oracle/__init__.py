@@ -12,6 +12,7 @@ method is in the C file; this file only orders the calls:
     couplings  (section "A First Application": J_ij = d_ij^-sigma on the ring)
     xy_terms   (Eq. alg_dec_XY_model_poly, theta_N pinned to 0)
     track      (gamma-trick total-degree homotopy, predictor-corrector tracking)
+    endgame    (Cauchy endgame for singular endpoints: turns around t = 1)
     refine_certify (Newton refinement, Delta_sol, alpha-theory, real / non-real tests)
     dedup      (alpha-theory same/distinct tests between certified endpoints)
     xy_classify (theta = atan2(s, c), Hessian index, energy V, log |det H|)
@@ -56,6 +57,30 @@ class CertOpts(ctypes.Structure):
                 ("refine_iters", ctypes.c_int), ("alpha0", ctypes.c_double)]
 
 
+class EgOpts(ctypes.Structure):
+    _fields_ = [("r0", ctypes.c_double), ("ratio", ctypes.c_double), ("n_radii", ctypes.c_int),
+                ("samples", ctypes.c_int), ("max_cycle", ctypes.c_int),
+                ("tol_close", ctypes.c_double), ("tol_conv", ctypes.c_double),
+                ("h_min", ctypes.c_double), ("max_attempts", ctypes.c_int),
+                ("tol_res", ctypes.c_double)]
+
+
+# Cauchy endgame outcomes of nphc_oracle.c.
+(EG_CONVERGED, EG_NOT_CLOSED, EG_NOT_CONVERGED, EG_TRACK_FAILED, EG_DIVERGED,
+ EG_AT_INFINITY) = 1, 2, 3, 4, 5, 6
+
+
+def default_eg_opts(**kw) -> EgOpts:
+    """Cauchy endgame: turns around t = 1 at |1 - t| = 1/16, 1/64, ... (at most 8 radii),
+    16 samples per turn, cycle numbers up to 8; a turn closes within 1e-6 (relative), two
+    successive estimates agree within 1e-9 (relative) and the estimate solves P within the
+    solution tolerance 1e-10 (relative to max(1, ||z||^2))."""
+    o = dict(r0=0.0625, ratio=0.25, n_radii=8, samples=16, max_cycle=8, tol_close=1e-6,
+             tol_conv=1e-9, h_min=1.0 / 4096, max_attempts=4000, tol_res=1e-10)
+    o.update(kw)
+    return EgOpts(**o)
+
+
 def default_track_opts(**kw) -> TrackOpts:
     """Step control of the oracle tracker (the paper gives none; see the design notes)."""
     o = dict(h0=0.01, h_max=0.05, h_min=1e-14, eps_corr=1e-9, trust=0.1, r_div=1e4,
@@ -98,6 +123,10 @@ def lib():
         L.oracle_track.argtypes = [ctypes.c_int, ctypes.c_int, I, I, I, D, D, ctypes.c_double,
                                    ctypes.c_double, ctypes.POINTER(TrackOpts), I64, I64,
                                    ctypes.c_int, D, D, I, I, D]
+        L.oracle_endgame.argtypes = [ctypes.c_int, ctypes.c_int, I, I, I, D, D, ctypes.c_double,
+                                     ctypes.c_double, ctypes.POINTER(TrackOpts),
+                                     ctypes.POINTER(EgOpts), ctypes.POINTER(ctypes.c_int64), I64,
+                                     ctypes.c_int, D, D, I, I, D, D]
         L.oracle_sys_eval_jac.argtypes = [ctypes.c_int, ctypes.c_int, I, I, I, D, D, D, D, D, D, D, D]
         L.oracle_sys_eval_acc.argtypes = [ctypes.c_int, ctypes.c_int, I, I, I, D, D, D, D, D, D]
         L.oracle_d2_norm.argtypes = [ctypes.c_int, ctypes.c_int, I, I, I, D, D]
@@ -225,6 +254,32 @@ def track(T: Terms, gamma: complex, path0: int = 0, npaths: int | None = None,
         raise ValueError("oracle_track: invalid arguments")
     return dict(z=zre + 1j * zim, status=status, steps=steps, tend=tend,
                 path=np.arange(path0, path0 + npaths, dtype=np.int64))
+
+
+def endgame(T: Terms, gamma: complex, paths, track_opts: TrackOpts | None = None,
+            eg_opts: EgOpts | None = None, nthreads: int | None = None) -> dict:
+    """Cauchy endgame for the listed paths: tracked to t = 1 - r0, then turns around t = 1
+    (nphc_oracle.c, section "Cauchy endgame").  Returns the endpoint estimates z (path x n),
+    status (EG_*), cycle numbers, the radius of the last turn and the distance between the
+    last two estimates."""
+    n = T.n
+    paths = np.ascontiguousarray(paths, dtype=np.int64)
+    cnt = paths.shape[0]
+    track_opts = track_opts or default_track_opts()
+    eg_opts = eg_opts or default_eg_opts()
+    nthreads = nthreads or default_threads()
+    zre, zim = np.zeros((cnt, n)), np.zeros((cnt, n))
+    status, cycle = np.zeros(cnt, np.int32), np.zeros(cnt, np.int32)
+    r_last, delta = np.zeros(cnt), np.zeros(cnt)
+    rc = lib().oracle_endgame(*T.args(), float(np.real(gamma)), float(np.imag(gamma)),
+                              ctypes.byref(track_opts), ctypes.byref(eg_opts),
+                              paths.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), cnt,
+                              int(nthreads), _d(zre), _d(zim), _i(status), _i(cycle),
+                              _d(r_last), _d(delta))
+    if rc:
+        raise ValueError("oracle_endgame: invalid arguments")
+    return dict(z=zre + 1j * zim, status=status, cycle=cycle, r_last=r_last, delta=delta,
+                path=paths)
 
 
 def refine_certify(T: Terms, tr: dict, opts: CertOpts | None = None,

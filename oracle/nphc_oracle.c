@@ -435,17 +435,18 @@ static int all_finite(int n, const cplx *z) {
     return 1;
 }
 
-/* Track one path from its start point z (in) to its end (out). */
-static int track_path(const qsys *S, cplx gamma, const oracle_track_opts *o, cplx *z,
-                      int *steps_out, double *t_out, work *w) {
+/* Track one path from its start point z (in) to t_end (out): t_end = 1 for the whole
+ * path, below 1 where the Cauchy endgame takes over. */
+static int track_path(const qsys *S, cplx gamma, const oracle_track_opts *o, double t_end,
+                      cplx *z, int *steps_out, double *t_out, work *w) {
     int n = S->n, accepted = 0, attempts = 0, run = 0, status = OR_RUNNING;
     double t = 0.0, h = o->h0;
     while (status == OR_RUNNING) {
-        if (t >= 1.0) { status = OR_REACHED; break; }
+        if (t >= t_end) { status = OR_REACHED; break; }
         if (attempts >= o->max_steps) { status = OR_STEP_BUDGET; break; }
         attempts++;
         double t1 = t + h, hh = h;
-        if (t1 >= 1.0) { t1 = 1.0; hh = 1.0 - t; }
+        if (t1 >= t_end) { t1 = t_end; hh = t_end - t; }
         /* classical RK4 on dz/dt = -H_z^-1 H_t */
         int bad = dzdt(S, gamma, z, t, w, w->k1);
         if (!bad) { for (int i = 0; i < n; i++) w->zs[i] = z[i] + 0.5 * hh * w->k1[i];
@@ -513,7 +514,7 @@ static void *track_worker(void *arg) {
         for (int k = 0; k < n; k++) z[k] = ((p >> k) & 1) ? -1.0 : 1.0;
         int steps;
         double t;
-        int st = track_path(J->S, J->gamma, J->o, z, &steps, &t, &w);
+        int st = track_path(J->S, J->gamma, J->o, 1.0, z, &steps, &t, &w);
         for (int k = 0; k < n; k++) {
             J->zre[i * n + k] = creal(z[k]);
             J->zim[i * n + k] = cimag(z[k]);
@@ -539,6 +540,302 @@ int oracle_track(int n, int nterms, const int *eq, const int *va, const int *vb,
     track_job J = {&S, gamma_re + I * gamma_im, o, path0, npaths, zre, zim, status, steps, tend, 0};
     pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
     for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, track_worker, &J);
+    for (int i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
+    free(th);
+    return 0;
+}
+
+/* ------------------------------------------------------------ Cauchy endgame -- */
+/* Endpoints that are singular (several paths meeting at t = 1) stall a tracker that
+ * walks t along the real axis: H_z becomes singular at t = 1.  The paper reports that
+ * such difficulties are resolved in practice; this is the Cauchy endgame of the
+ * homotopy continuation literature (Morgan, Sommese and Wampler, 1991).  Near t = 1 a
+ * path is a Puiseux series in s = (1 - t)^(1/c), analytic in s, with c the cycle
+ * number.  Writing 1 - t = e^w, the path is continued around the circle |1 - t| = r
+ * (w = ln r + i theta, theta from 0 upward); it closes after exactly c turns, and by
+ * Cauchy's integral formula its value at s = 0 is the mean of z over one turn in s,
+ * i.e. over the c turns in t.  With K equally spaced samples per turn the mean is the
+ * trapezoid rule, exact up to the aliased term of order r^K / R^K (R the distance from
+ * t = 1 to the nearest other branch point).  The radius shrinks by `ratio` until two
+ * successive estimates agree.  Continuation between samples is the tracker's: RK4 on
+ * dz/dw, Newton's corrector at the end of each step, the same step control. */
+typedef struct {
+    double r0;          /* first radius |1 - t|; tracking from t = 0 stops at 1 - r0 */
+    double ratio;       /* radius ratio between successive turns (< 1) */
+    int n_radii;        /* most radii tried */
+    int samples;        /* K: samples per turn around t = 1 */
+    int max_cycle;      /* largest cycle number tried */
+    double tol_close;   /* a turn closes when ||z - z_start|| <= tol_close (1 + ||z_start||) */
+    double tol_conv;    /* estimates agree when ||e_k - e_{k-1}|| <= tol_conv (1 + ||e_k||) */
+    double h_min;       /* smallest step, as a fraction of one sample interval */
+    int max_attempts;   /* step attempts per path in the endgame */
+    double tol_res;     /* an estimate is a solution when ||P||_inf <= tol_res max(1, ||e||_inf^2)
+                         * (the solution tolerance Delta_sol, as for certification) */
+} oracle_eg_opts;
+
+enum {
+    OE_NONE = 0,
+    OE_CONVERGED = 1,      /* two successive estimates agree */
+    OE_NOT_CLOSED = 2,     /* no turn closed within max_cycle turns */
+    OE_NOT_CONVERGED = 3,  /* estimates still disagree at the last radius (last one kept) */
+    OE_TRACK_FAILED = 4,   /* tracking to 1 - r0, or a step of the endgame, failed */
+    OE_DIVERGED = 5,       /* ||z||_inf exceeded the divergence radius */
+    OE_AT_INFINITY = 6     /* turns close, but the path grows as the radius shrinks: a pole */
+};
+
+/* H_z(z, t) = gamma (1-t) diag(2 z) + t DP(z) at complex t (omt = 1 - t), into w->A. */
+static void hom_jac_c(const qsys *S, cplx gamma, const cplx *z, cplx t, cplx omt, work *w) {
+    int n = S->n;
+    sys_jac(S, z, w->A);
+    for (int i = 0; i < n * n; i++) w->A[i] *= t;
+    for (int i = 0; i < n; i++) w->A[i * n + i] += gamma * omt * 2.0 * z[i];
+}
+
+/* dz/dw for 1 - t = e^w: dt/dw = -e^w, so dz/dw = -H_z^-1 H_t dt/dw = e^w H_z^-1 H_t,
+ * H_t = P - gamma Q.  Returns 0 or 1 (singular H_z). */
+static int dzdw(const qsys *S, cplx gamma, const cplx *z, cplx ew, work *w, cplx *out) {
+    int n = S->n;
+    sys_eval(S, z, w->P);
+    for (int i = 0; i < n; i++) out[i] = w->P[i] - gamma * (z[i] * z[i] - 1.0);
+    hom_jac_c(S, gamma, z, 1.0 - ew, ew, w);
+    if (lu_factor(n, w->A, w->piv)) return 1;
+    lu_apply(n, w->A, w->piv, out);
+    for (int i = 0; i < n; i++) out[i] *= ew;
+    return 0;
+}
+
+/* H(z, t) at complex t with the compensated sums of hom_eval_acc. */
+static void hom_eval_acc_c(const qsys *S, cplx gamma, const cplx *z, cplx t, cplx omt,
+                           cplx *Hout, cplx *P) {
+    int n = S->n;
+    sys_eval_acc(S, z, P);
+    cplx g1 = gamma * omt;
+    double gr = creal(g1), gi = cimag(g1), tr = creal(t), ti = cimag(t);
+    for (int i = 0; i < n; i++) {
+        double xr = creal(z[i]), xi = cimag(z[i]);
+        dd qr = dd_add(dd_add(dd_two_prod(xr, xr), dd_two_prod(-xi, xi)), (dd){-1.0, 0.0});
+        dd qi = dd_two_prod(2.0 * xr, xi);
+        double pr = creal(P[i]), pi = cimag(P[i]);
+        dd hr = dd_add(dd_add(dd_mul_d(qr, gr), dd_mul_d(qi, -gi)),
+                       dd_add(dd_two_prod(tr, pr), dd_two_prod(-ti, pi)));
+        dd hi = dd_add(dd_add(dd_mul_d(qi, gr), dd_mul_d(qr, gi)),
+                       dd_add(dd_two_prod(tr, pi), dd_two_prod(ti, pr)));
+        Hout[i] = (hr.hi + hr.lo) + I * (hi.hi + hi.lo);
+    }
+}
+
+static int newton_hom_c(const qsys *S, cplx gamma, cplx *z, cplx ew, work *w, double *dn) {
+    int n = S->n;
+    cplx t = 1.0 - ew;
+    hom_eval_acc_c(S, gamma, z, t, ew, w->b, w->P);
+    for (int i = 0; i < n; i++) w->b[i] = -w->b[i];
+    hom_jac_c(S, gamma, z, t, ew, w);
+    if (lu_factor(n, w->A, w->piv)) return 1;
+    lu_apply(n, w->A, w->piv, w->b);
+    for (int i = 0; i < n; i++) z[i] += w->b[i];
+    *dn = norm2(n, w->b);
+    return 0;
+}
+
+/* e^w at the point v in [0, 1] of a sample interval: on a turn (radial == 0) w = lr +
+ * i 2 pi (j + v) / K; on the radial leg w = lr + v ln(ratio). */
+static cplx eg_ew(double lr, int radial, int j, int K, double lnratio, double v) {
+    if (radial) return exp(lr + v * lnratio);
+    return cexp(lr + I * (2.0 * M_PI * ((double)j + v) / (double)K));
+}
+
+/* Continue z across one sample interval (v from 0 to 1) with the tracker's step control
+ * in v (RK4 on dz/dv = dw/dv dz/dw, Newton at the end of each step, h halves on a reject,
+ * doubles after grow_after accepts, at most 1).  *h carries the step between intervals.
+ * Returns OE_NONE on success, else OE_TRACK_FAILED or OE_DIVERGED. */
+static int eg_interval(const qsys *S, cplx gamma, const oracle_track_opts *o,
+                       const oracle_eg_opts *e, double lr, int radial, int j, double lnratio,
+                       cplx *z, double *h, int *run, int *attempts, work *w) {
+    int n = S->n, K = e->samples;
+    cplx dw = radial ? (cplx)lnratio : I * (2.0 * M_PI / (double)K);
+    double v = 0.0;
+    while (v < 1.0) {
+        if (*attempts >= e->max_attempts) return OE_TRACK_FAILED;
+        (*attempts)++;
+        double hh = fmin(*h, 1.0 - v), v1 = v + hh;
+        if (v1 >= 1.0) { v1 = 1.0; hh = 1.0 - v; }
+        cplx hd = hh * dw;
+        int bad = dzdw(S, gamma, z, eg_ew(lr, radial, j, K, lnratio, v), w, w->k1);
+        cplx em = eg_ew(lr, radial, j, K, lnratio, v + 0.5 * hh);
+        if (!bad) { for (int i = 0; i < n; i++) w->zs[i] = z[i] + 0.5 * hd * w->k1[i];
+                    bad = dzdw(S, gamma, w->zs, em, w, w->k2); }
+        if (!bad) { for (int i = 0; i < n; i++) w->zs[i] = z[i] + 0.5 * hd * w->k2[i];
+                    bad = dzdw(S, gamma, w->zs, em, w, w->k3); }
+        cplx e1 = eg_ew(lr, radial, j, K, lnratio, v1);
+        if (!bad) { for (int i = 0; i < n; i++) w->zs[i] = z[i] + hd * w->k3[i];
+                    bad = dzdw(S, gamma, w->zs, e1, w, w->k4); }
+        int ok = 0;
+        if (!bad) {
+            for (int i = 0; i < n; i++)
+                w->zp[i] = z[i] + hd / 6.0 * (w->k1[i] + 2.0 * w->k2[i] + 2.0 * w->k3[i] + w->k4[i]);
+            double zn = norm2(n, w->zp);
+            for (int it = 0; it < o->max_newton; it++) {
+                double dn;
+                if (newton_hom_c(S, gamma, w->zp, e1, w, &dn)) break;
+                if (!all_finite(n, w->zp)) break;
+                if (it == 0 && dn > o->trust * (1.0 + zn)) break;
+                if (dn <= o->eps_corr * (1.0 + norm2(n, w->zp))) { ok = 1; break; }
+            }
+        }
+        if (ok) {
+            memcpy(z, w->zp, sizeof(cplx) * n);
+            v = v1;
+            if (++*run >= o->grow_after) { *run = 0; *h = fmin(2.0 * *h, 1.0); }
+            if (norminf(n, z) > o->r_div) return OE_DIVERGED;
+        } else {
+            *run = 0;
+            *h *= 0.5;
+            if (*h < e->h_min) return OE_TRACK_FAILED;
+        }
+    }
+    return OE_NONE;
+}
+
+static double dist2(int n, const cplx *a, const cplx *b) {
+    double s = 0;
+    for (int i = 0; i < n; i++) { cplx d = a[i] - b[i]; s += creal(d) * creal(d) + cimag(d) * cimag(d); }
+    return sqrt(s);
+}
+
+/* The endgame of one path: track from the start point to t = 1 - r0, then turns around
+ * t = 1 at radii r0, r0 ratio, r0 ratio^2, ...  A radius whose turns do not close within
+ * max_cycle turns, or where a step fails, encloses more than the endpoint's own branch
+ * point (or too sharp a neighbourhood): the path goes back to the point where it reached
+ * that radius and continues to the next one.  Two estimates from successive radii that
+ * both closed must agree and the estimate must solve P; an estimate that does not,
+ * while the distance from each radius's start point to its estimate grows, belongs to a
+ * path to infinity.  z (in: start point; out: the last estimate, or the point
+ * where it stopped).  Outputs the cycle number and radius of the last closed turns and
+ * the distance between the last two estimates. */
+static int endgame_path(const qsys *S, cplx gamma, const oracle_track_opts *o,
+                        const oracle_eg_opts *e, cplx *z, int *cycle, double *r_last,
+                        double *delta, work *w) {
+    int n = S->n, K = e->samples, steps;
+    double tend;
+    *cycle = 0; *r_last = e->r0; *delta = INFINITY;
+    int st = track_path(S, gamma, o, 1.0 - e->r0, z, &steps, &tend, w);
+    if (st == OR_DIVERGED) return OE_DIVERGED;
+    if (st != OR_REACHED) return OE_TRACK_FAILED;
+    cplx *zs = malloc(sizeof(cplx) * n), *sum = malloc(sizeof(cplx) * n),
+         *est = malloc(sizeof(cplx) * n), *prev = malloc(sizeof(cplx) * n);
+    double lnratio = log(e->ratio), h = 1.0;
+    int run = 0, attempts = 0, status = OE_NONE, have_prev = 0, last_fail = OE_NOT_CLOSED;
+    double d_prev = INFINITY;
+    for (int k = 0; k < e->n_radii && status == OE_NONE; k++) {
+        double lr = log(e->r0) + k * lnratio;
+        if (k > 0) {   /* radial leg from the previous radius */
+            int rc = eg_interval(S, gamma, o, e, lr - lnratio, 1, 0, lnratio, z, &h, &run, &attempts, w);
+            if (rc != OE_NONE) { status = rc; break; }
+        }
+        memcpy(zs, z, sizeof(cplx) * n);
+        for (int i = 0; i < n; i++) sum[i] = 0;
+        int c = 0, rc = OE_NONE;
+        for (int turn = 1; turn <= e->max_cycle && !c && rc == OE_NONE; turn++) {
+            for (int j = 0; j < K && rc == OE_NONE; j++) {
+                for (int i = 0; i < n; i++) sum[i] += z[i];   /* sample at theta = 2 pi j / K */
+                rc = eg_interval(S, gamma, o, e, lr, 0, j, lnratio, z, &h, &run, &attempts, w);
+            }
+            if (rc == OE_NONE && dist2(n, z, zs) <= e->tol_close * (1.0 + norm2(n, zs))) c = turn;
+        }
+        if (rc == OE_DIVERGED) { status = rc; break; }
+        if (rc != OE_NONE || !c) {   /* back to where the path reached this radius */
+            memcpy(z, zs, sizeof(cplx) * n);
+            h = 1.0;
+            run = 0;
+            have_prev = 0;
+            last_fail = rc != OE_NONE ? OE_TRACK_FAILED : OE_NOT_CLOSED;
+            continue;
+        }
+        *cycle = c;
+        *r_last = exp(lr);
+        for (int i = 0; i < n; i++) est[i] = sum[i] / (double)(c * K);
+        /* distance from the turns' start point to the estimate: ~ r^(1/c) towards a finite
+         * endpoint; it grows as r shrinks on a path to infinity, whose mean over a turn is
+         * the constant term of a Laurent series, the same at every radius */
+        double d = dist2(n, zs, est);
+        if (have_prev) {
+            *delta = dist2(n, est, prev);
+            if (*delta <= e->tol_conv * (1.0 + norm2(n, est))) {
+                /* agreement alone is not enough: turns that also enclose the branch point
+                 * of two paths with distinct endpoints close after two turns and average
+                 * those endpoints, the same at every radius that encloses it.  The
+                 * estimate must solve P; if it does not, a path to infinity shows growth
+                 * by at least ratio^(-1/c) per radius (c <= max_cycle), and anything else
+                 * goes on to smaller radii */
+                sys_eval_acc(S, est, w->P);
+                double zi = norminf(n, est), scale = zi > 1.0 ? zi * zi : 1.0;
+                if (norminf(n, w->P) <= e->tol_res * scale) { status = OE_CONVERGED; break; }
+                if (d > d_prev * pow(e->ratio, -0.5 / e->max_cycle)) { status = OE_AT_INFINITY; break; }
+            }
+        }
+        memcpy(prev, est, sizeof(cplx) * n);
+        d_prev = d;
+        have_prev = 1;
+    }
+    if (status == OE_NONE) status = have_prev ? OE_NOT_CONVERGED : last_fail;
+    if (status == OE_CONVERGED || status == OE_NOT_CONVERGED) memcpy(z, est, sizeof(cplx) * n);
+    free(zs); free(sum); free(est); free(prev);
+    return status;
+}
+
+typedef struct {
+    const qsys *S;
+    cplx gamma;
+    const oracle_track_opts *o;
+    const oracle_eg_opts *e;
+    const int64_t *paths;
+    int64_t npaths;
+    double *zre, *zim, *r_last, *delta;
+    int *status, *cycle;
+    int64_t next;
+} eg_job;
+
+static void *eg_worker(void *arg) {
+    eg_job *J = arg;
+    int n = J->S->n;
+    work w;
+    work_init(&w, n);
+    cplx *z = malloc(sizeof(cplx) * n);
+    for (;;) {
+        int64_t i = __atomic_fetch_add(&J->next, 1, __ATOMIC_RELAXED);
+        if (i >= J->npaths) break;
+        int64_t p = J->paths[i];
+        for (int k = 0; k < n; k++) z[k] = ((p >> k) & 1) ? -1.0 : 1.0;
+        J->status[i] = endgame_path(J->S, J->gamma, J->o, J->e, z, &J->cycle[i], &J->r_last[i],
+                                    &J->delta[i], &w);
+        for (int k = 0; k < n; k++) {
+            J->zre[i * n + k] = creal(z[k]);
+            J->zim[i * n + k] = cimag(z[k]);
+        }
+    }
+    free(z);
+    work_free(&w);
+    return NULL;
+}
+
+/* Cauchy endgame for the paths listed in paths[0 .. npaths-1] (path indices).  Outputs
+ * (path-major z [i*n + k]): the estimate of each endpoint, OE_* status, cycle number,
+ * radius of the last turn, distance between the last two estimates.  Returns 0, or 1
+ * for invalid arguments. */
+int oracle_endgame(int n, int nterms, const int *eq, const int *va, const int *vb,
+                   const double *cre, const double *cim, double gamma_re, double gamma_im,
+                   const oracle_track_opts *o, const oracle_eg_opts *e, const int64_t *paths,
+                   int64_t npaths, int nthreads, double *zre, double *zim, int *status,
+                   int *cycle, double *r_last, double *delta) {
+    if (n < 1 || n > 62 || nthreads < 1 || npaths < 0) return 1;
+    if (!(e->r0 > 0.0 && e->r0 < 1.0) || !(e->ratio > 0.0 && e->ratio < 1.0) || e->n_radii < 1 ||
+        e->samples < 2 || e->max_cycle < 1)
+        return 1;
+    qsys S = {n, nterms, eq, va, vb, cre, cim};
+    eg_job J = {&S, gamma_re + I * gamma_im, o, e, paths, npaths, zre, zim, r_last, delta,
+                status, cycle, 0};
+    pthread_t *th = malloc(sizeof(pthread_t) * nthreads);
+    for (int i = 0; i < nthreads; i++) pthread_create(&th[i], NULL, eg_worker, &J);
     for (int i = 0; i < nthreads; i++) pthread_join(th[i], NULL);
     free(th);
     return 0;
