@@ -108,6 +108,18 @@ typedef struct nphc_options {
     double refine_eps;         /* refinement stops when ||dz|| <= eps (1 + ||z||), 1e-14 */
     int block_size;            /* threads per block of the FP32 tracker; 0 = automatic */
     int blocks_per_sm;         /* resident blocks per SM of the FP32 tracker; 0 = automatic */
+    /* Cauchy endgame (nphc_endgame) */
+    int endgame;               /* nphc_solve_into runs the endgame on every path that ends
+                                  NPHC_END_SINGULAR or NPHC_END_FAILED, 0 (off) */
+    double eg_r0;              /* first radius |1 - t| of the turns around t = 1, 1/16 */
+    double eg_ratio;           /* ratio between successive radii, 1/4 */
+    int eg_radii;              /* most radii tried, 8 */
+    int eg_samples;            /* samples per turn, 16 */
+    int eg_max_cycle;          /* largest cycle number tried, 8 */
+    double eg_tol_close;       /* a turn closes when ||z - z_start|| <= tol (1 + ||z_start||), 1e-6 */
+    double eg_tol_conv;        /* two estimates agree when ||e_k - e_k-1|| <= tol (1 + ||e_k||), 1e-9 */
+    double eg_h_min;           /* smallest endgame step, in sample intervals, 1/4096 */
+    int eg_max_attempts;       /* endgame step attempts per path, 4000 */
 } nphc_options;
 
 typedef struct nphc_system nphc_system;   /* opaque; owns the device copy of the couplings */
@@ -282,6 +294,54 @@ nphc_status nphc_xy_adjoint(const nphc_system *sys, int64_t count, const double 
                             const double *g_energy, const double *g_theta, double *dJ,
                             void *stream);
 
+/* Outcome of the Cauchy endgame for one entry (nphc_endgame). */
+enum {
+    NPHC_EG_NONE = 0,           /* not run */
+    NPHC_EG_CONVERGED = 1,      /* estimates from two successive radii agree: z is the endpoint */
+    NPHC_EG_NOT_CLOSED = 2,     /* at the last radius tried no turn closed within eg_max_cycle */
+    NPHC_EG_NOT_CONVERGED = 3,  /* the estimates still disagree at the last radius; z the last one */
+    NPHC_EG_TRACK_FAILED = 4,   /* tracking to 1 - eg_r0, a radial leg, or the last radius's
+                                   steps failed */
+    NPHC_EG_DIVERGED = 5,       /* ||z||_inf exceeded the divergence radius */
+    NPHC_EG_AT_INFINITY = 6     /* the turns close, but the path grows as the radius shrinks:
+                                   it goes to infinity */
+};
+
+/* The Cauchy endgame for endpoints where several paths meet (singular solutions, for
+ * instance on the positive-dimensional solution sets of rings with N = 0 mod 4) and for
+ * paths that go to infinity too slowly to cross the divergence radius.  The paper reports
+ * that such endpoints are dealt with in practice (section "Numerical Polynomial Homotopy
+ * Continuation Method"); the method is the Cauchy endgame of Morgan, Sommese and Wampler
+ * (1991).  For each selected entry:
+ *   1. its path is tracked in FP64 from its start point to t = 1 - eg_r0 (as nphc_track
+ *      with resume = 0: z, t, h, status, steps, solves, newton are overwritten);
+ *   2. with 1 - t = e^w, the path is continued around the circle |1 - t| = r (RK4 on dz/dw,
+ *      Newton's corrector): it closes after c turns, c the cycle number (the path is a
+ *      power series in (1 - t)^(1/c)), and the mean of its eg_samples * c equally spaced
+ *      samples (the trapezoid rule for Cauchy's integral) estimates the endpoint;
+ *   3. r shrinks by eg_ratio (a leg along real t) until two estimates from successive
+ *      radii agree and the estimate e solves P within the solution tolerance
+ *      (||P(e)||_inf <= tol_sol max(1, ||e||_inf^2): NPHC_EG_CONVERGED), or eg_radii radii
+ *      are used.  A radius whose turns do not close within eg_max_cycle turns, or where a
+ *      step fails, is left from the point where the path reached it.  Estimates that
+ *      agree without solving P belong to a path to infinity when the distance from the
+ *      radius's start point to the estimate grows by more than
+ *      eg_ratio^(-1/(2 eg_max_cycle)) per radius (NPHC_EG_AT_INFINITY); otherwise the
+ *      turns enclose another pair of paths' branch point too, and r shrinks on.
+ * Writes z (the estimate for NPHC_EG_CONVERGED and NPHC_EG_NOT_CONVERGED, else the point
+ * where the endgame stopped), cycle[e] (device int32 [count]: c of the last radius whose
+ * turns closed, 0 if none), eg_status[e] (device int32 [count]: NPHC_EG_*), and adds its
+ * solves to solves[e].  cls and the certification arrays are not touched.  list /
+ * list_count select entries as in nphc_track; workspace as in nphc_track.  Both the XY
+ * ring and generic quadratic systems.  NPHC_EINVAL on NULL arrays, endgame options out
+ * of range (0 < eg_r0 < 1, 0 < eg_ratio < 1, eg_radii >= 1, 2 <= eg_samples <= 4096,
+ * eg_max_cycle >= 1, positive tolerances, eg_h_min and eg_max_attempts) or a small
+ * workspace. */
+nphc_status nphc_endgame(const nphc_system *sys, const nphc_options *opt, const nphc_endpoints *ep,
+                         const int32_t *list, const int32_t *list_count, int32_t *cycle,
+                         int32_t *eg_status, void *workspace, size_t workspace_bytes,
+                         void *stream);
+
 /* Result counters (nphc_result_counts). */
 enum {
     NPHC_COUNT_PATHS = 0,
@@ -293,7 +353,12 @@ enum {
     NPHC_COUNT_SOLVES,         /* linear solves summed over all tracking calls */
     NPHC_COUNT_LAUNCHES,       /* kernels the last nphc_solve_into launched (host count) */
     NPHC_COUNT_INDEX0,         /* + i: real SPs of Hessian index i, i = 0 .. NPHC_MAX_N-1 */
-    NPHC_NCOUNTS = NPHC_COUNT_INDEX0 + NPHC_MAX_N
+    /* with opt.endgame (zero otherwise): */
+    NPHC_COUNT_EG_RUN = NPHC_COUNT_INDEX0 + NPHC_MAX_N,   /* paths given to the endgame */
+    NPHC_COUNT_EG_CONVERGED,   /* of which NPHC_EG_CONVERGED (a finite endpoint) */
+    NPHC_COUNT_EG_MULTIPLE,    /* of which with cycle number >= 2 (a singular endpoint) */
+    NPHC_COUNT_EG_AT_INFINITY, /* NPHC_EG_AT_INFINITY or NPHC_EG_DIVERGED */
+    NPHC_NCOUNTS
 };
 
 /* Allocates device buffers for every path of sys (the result keeps a reference to no
@@ -303,7 +368,8 @@ nphc_status nphc_result_create(const nphc_system *sys, nphc_result **out);
 /* The whole method into an existing result, asynchronously on stream: track every path
  * (MIXED: FP32, then FP64 for hand-offs and for endpoints that do not certify), refine
  * and certify, deduplicate (FP64 re-track of every duplicated solution's paths, then
- * deduplicate again), classify.  No allocation, no host synchronisation. */
+ * deduplicate again), classify; with opt.endgame, the Cauchy endgame (nphc_endgame) on
+ * every path that ends singular or failed.  No allocation, no host synchronisation. */
 nphc_status nphc_solve_into(const nphc_system *sys, const nphc_options *opt, nphc_result *res,
                             void *stream);
 
@@ -322,10 +388,18 @@ nphc_status nphc_result_copy_sps(const nphc_result *res, int64_t cap, double *th
                                  double *log_abs_det, int64_t *n_out);
 
 /* Every path's endpoint (host, path-major z [cap * n]), status and class.  Any output may
- * be NULL.  *n_out = number of paths. */
+ * be NULL.  *n_out = number of paths.  With opt.endgame, entries of class
+ * NPHC_END_SINGULAR or NPHC_END_FAILED hold what nphc_endgame wrote (z the endpoint
+ * estimate, status that of the FP64 tracking to 1 - eg_r0). */
 nphc_status nphc_result_copy_endpoints(const nphc_result *res, int64_t cap, double *z_re,
                                        double *z_im, int32_t *status, int32_t *cls,
                                        int64_t *n_out);
+
+/* Every path's Cauchy endgame outcome (host int32 [cap]): cycle number and NPHC_EG_*
+ * status (NPHC_EG_NONE where the endgame did not run).  Any output may be NULL.
+ * *n_out = number of paths. */
+nphc_status nphc_result_copy_endgame(const nphc_result *res, int64_t cap, int32_t *cycle,
+                                     int32_t *eg_status, int64_t *n_out);
 
 /* ---------------------------------------------------------------------------------
  * Batches: many independent systems solved together (the paper's method per system;

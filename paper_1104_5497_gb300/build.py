@@ -22,7 +22,7 @@ LIB = os.path.join(OUT, "libnphc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 M_RANGE = range(2, 13)          # N = 3 .. 13
-KINDS = {0: "track_f32", 1: "track_f64", 2: "endgame"}
+KINDS = {0: "track_f32", 1: "track_f64", 2: "endgame", 3: "cauchy"}
 QUAD_RANGE = range(1, 13)       # generic quadratic systems, n = 1 .. 12 unknowns
 
 

@@ -102,6 +102,8 @@ struct nphc_result {
     int64_t *counts;
     double *o_theta, *o_energy, *o_alpha, *o_logdet;
     int32_t *o_index;
+    int32_t *cycle, *egst;   // Cauchy endgame outcome per path
+    int32_t *egtrack;        // status of the endgame's tracking to 1 - r0 (keeps ep.status)
     int64_t *o_path;
     void *ws;
     size_t ws_bytes;
@@ -138,6 +140,16 @@ nphc_status nphc_options_default(nphc_options *o) {
     o->grow_after = 3;
     o->refine_iters = 8;
     o->refine_eps = 1e-14;
+    o->endgame = 0;
+    o->eg_r0 = 1.0 / 16.0;
+    o->eg_ratio = 0.25;
+    o->eg_radii = 8;
+    o->eg_samples = 16;
+    o->eg_max_cycle = 8;
+    o->eg_tol_close = 1e-6;
+    o->eg_tol_conv = 1e-9;
+    o->eg_h_min = 1.0 / 4096.0;
+    o->eg_max_attempts = 4000;
     o->block_size = 0;
     o->blocks_per_sm = 0;
     return NPHC_OK;
@@ -327,6 +339,11 @@ nphc_status check_opt(const nphc_options *o) {
           o->max_newton_fp64 > 0 && o->max_steps > 0 && o->max_steps_fp32 > 0 && o->crawl_steps_fp32 >= 0 && o->grow_after > 0 &&
           o->refine_iters >= 0))
         return fail(NPHC_EINVAL, "options out of range");
+    if (!(o->eg_r0 > 0.0 && o->eg_r0 < 1.0 && o->eg_ratio > 0.0 && o->eg_ratio < 1.0 &&
+          o->eg_radii >= 1 && o->eg_samples >= 2 && o->eg_samples <= 4096 && o->eg_max_cycle >= 1 &&
+          o->eg_tol_close > 0.0 && o->eg_tol_conv > 0.0 && o->eg_h_min > 0.0 &&
+          o->eg_max_attempts > 0))
+        return fail(NPHC_EINVAL, "endgame options out of range");
     return NPHC_OK;
 }
 
@@ -360,6 +377,7 @@ XYCtl make_ctl(const nphc_options *o, bool fp32, bool resume, bool accumulate) {
     c.accumulate = accumulate ? 1 : 0;
     c.sparse = 0;
     c.crawl_steps = fp32 ? o->crawl_steps_fp32 : 0;
+    c.t_end = 1.0;
     return c;
 }
 
@@ -385,10 +403,12 @@ EPView view(const nphc_endpoints *e) {
 
 nphc_status track_impl(const nphc_system *S, const nphc_options *o, nphc_precision prec,
                        const nphc_endpoints *ep, const int32_t *list, const int32_t *list_count,
-                       bool resume, bool accumulate, void *ws, int queue_slot, cudaStream_t st) {
+                       bool resume, bool accumulate, void *ws, int queue_slot, cudaStream_t st,
+                       double t_end = 1.0) {
     const bool f32 = prec == NPHC_PREC_MIXED && !S->quad;   // generic systems: FP64
     const XYSys xs = sys_with_gamma(S, o);
     XYCtl ctl = make_ctl(o, f32, resume, accumulate);
+    ctl.t_end = t_end;
     // FP64 lists (hand-offs, re-tracks) spread over every SM: ceil(list / warps) paths
     // per warp, up to 32
     ctl.sparse = (!f32 && list != nullptr) ? 1 : 0;
@@ -415,6 +435,48 @@ nphc_status track_impl(const nphc_system *S, const nphc_options *o, nphc_precisi
         NPHC_CK(launch_xy_track_f32(S->M, xs, ctl, v, wl, 0, grid, st));
     else
         NPHC_CK(launch_xy_track_f64(S->M, xs, ctl, v, wl, 0, 0, st));
+    return NPHC_OK;
+}
+
+// The Cauchy endgame on the selected entries: FP64 tracking to 1 - eg_r0 (queue slot 6),
+// then the turns around t = 1 (queue slot 7).  The tracking writes its statuses where ep
+// says (the pipeline points them at a scratch array to keep the result's statuses).
+nphc_status endgame_impl(const nphc_system *S, const nphc_options *o, const nphc_endpoints *ep,
+                         const int32_t *list, const int32_t *list_count, int32_t *cycle,
+                         int32_t *egst, bool accumulate, void *ws, cudaStream_t st) {
+    nphc_status s = track_impl(S, o, NPHC_PREC_FP64, ep, list, list_count, false, accumulate, ws,
+                               6, st, 1.0 - o->eg_r0);
+    if (s != NPHC_OK) return s;
+    EGCtl c;
+    c.lr0 = std::log(o->eg_r0);
+    c.lnratio = std::log(o->eg_ratio);
+    c.n_radii = o->eg_radii;
+    c.samples = o->eg_samples;
+    c.max_cycle = o->eg_max_cycle;
+    c.tol_close = o->eg_tol_close;
+    c.tol_conv = o->eg_tol_conv;
+    c.tol_res = o->tol_sol;
+    c.grow_inf = std::pow(o->eg_ratio, -0.5 / o->eg_max_cycle);
+    c.hmin = o->eg_h_min;
+    c.max_attempts = o->eg_max_attempts;
+    c.eps = o->eps_fp64;
+    c.trust = o->trust;
+    c.rdiv = o->r_div;
+    c.max_newton = o->max_newton_fp64;
+    c.grow_after = o->grow_after;
+    WorkList wl;
+    wl.list = list;
+    wl.list_count = list_count;
+    wl.queue = ws_queue(ws, 7);
+    wl.state = static_cast<char *>(ws) + ws_layout(S->n, 0).state;
+    // the tracker scratch holds 4 vectors per thread for NPHC_TRACK_MAX_THREADS threads
+    wl.state_threads = (int64_t)4 * NPHC_TRACK_MAX_THREADS / NPHC_CAUCHY_STATE_VECTORS / 32 * 32;
+    NPHC_CK(cudaMemsetAsync(wl.queue, 0, sizeof(unsigned long long), st));
+    const EPView v = view(ep);
+    if (S->quad)
+        NPHC_CK(launch_quad_cauchy(S->n, quad_with_gamma(S, o), c, v, wl, cycle, egst, st));
+    else
+        NPHC_CK(launch_xy_cauchy(S->M, sys_with_gamma(S, o), c, v, wl, cycle, egst, st));
     return NPHC_OK;
 }
 
@@ -445,6 +507,19 @@ nphc_status nphc_track(const nphc_system *S, const nphc_options *o, nphc_precisi
     if (!ws || ws_bytes < ws_layout(S->n, ep->count).total) return fail(NPHC_EINVAL, "workspace too small");
     return track_impl(S, o, prec, ep, list, list_count, resume != 0, resume != 0, ws, 0,
                       (cudaStream_t)stream);
+}
+
+nphc_status nphc_endgame(const nphc_system *S, const nphc_options *o, const nphc_endpoints *ep,
+                         const int32_t *list, const int32_t *list_count, int32_t *cycle,
+                         int32_t *eg_status, void *ws, size_t ws_bytes, void *stream) {
+    nphc_status s;
+    if ((s = check_ep(S, ep, false)) != NPHC_OK) return s;
+    if ((s = check_opt(o)) != NPHC_OK) return s;
+    if (!cycle || !eg_status) return fail(NPHC_EINVAL, "cycle / eg_status arrays missing");
+    if ((list == nullptr) != (list_count == nullptr)) return fail(NPHC_EINVAL, "list without count");
+    if (!ws || ws_bytes < ws_layout(S->n, ep->count).total) return fail(NPHC_EINVAL, "workspace too small");
+    return endgame_impl(S, o, ep, list, list_count, cycle, eg_status, false, ws,
+                        (cudaStream_t)stream);
 }
 
 nphc_status nphc_refine_certify(const nphc_system *S, const nphc_options *o,
@@ -549,7 +624,10 @@ nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
         sizeof(int64_t) * P,            // 30 o_path
         L.total,                        // 31 workspace
         sizeof(double) * P,             // 32 logdet
-        sizeof(double) * P};            // 33 o_logdet
+        sizeof(double) * P,             // 33 o_logdet
+        sizeof(int32_t) * P,            // 34 cycle
+        sizeof(int32_t) * P,            // 35 egst
+        sizeof(int32_t) * P};           // 36 egtrack
     std::vector<size_t> off(sz.size());
     size_t tot = 0;
     for (size_t i = 0; i < sz.size(); i++) {
@@ -608,6 +686,9 @@ nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
     R->ws = at(31);
     R->logdet = (double *)at(32);
     R->o_logdet = (double *)at(33);
+    R->cycle = (int32_t *)at(34);
+    R->egst = (int32_t *)at(35);
+    R->egtrack = (int32_t *)at(36);
     R->ws_bytes = L.total;
     R->stream = nullptr;
     R->solved = false;
@@ -638,7 +719,18 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
     const int64_t launches0 = nphc_launch_counter(0);
     NPHC_CK(cudaMemsetAsync(R->flags, 0, sizeof(int32_t) * R->P, st));
     NPHC_CK(cudaMemsetAsync(R->lcount, 0, sizeof(int32_t) * 8, st));
+    NPHC_CK(cudaMemsetAsync(R->cycle, 0, sizeof(int32_t) * R->P, st));
+    NPHC_CK(cudaMemsetAsync(R->egst, 0, sizeof(int32_t) * R->P, st));
     const bool mixed = o->precision == NPHC_PREC_MIXED;
+    // the Cauchy endgame on the paths that end singular or failed; the result keeps its
+    // tracking statuses (the endgame's own go to a scratch array)
+    auto endgame = [&]() -> nphc_status {
+        if (!o->endgame) return NPHC_OK;
+        NPHC_CK(launch_compact(v, PRED_ENDGAME, R->flags, R->list[1], R->lcount + 6, st));
+        nphc_endpoints eg = *ep;
+        eg.status = R->egtrack;
+        return endgame_impl(S, o, &eg, R->list[1], R->lcount + 6, R->cycle, R->egst, true, R->ws, st);
+    };
     if (S->quad) {
         // generic quadratic system: FP64 tracking, refinement, certification, dedup; no
         // classification (index -1 everywhere)
@@ -650,7 +742,8 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
                                            o->refine_iters, v, R->P, l3, st));
         NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st));
         NPHC_CK(cudaMemsetAsync(R->index, 0xff, sizeof(int32_t) * R->P, st));
-        NPHC_CK(launch_counts(v, R->flags, R->index, R->counts, st));
+        if ((s = endgame())) return s;
+        NPHC_CK(launch_counts(v, R->flags, R->index, R->counts, st, R->egst, R->cycle));
         R->stream = st;
         R->solved = true;
         R->launches = nphc_launch_counter(0) - launches0;
@@ -715,7 +808,8 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
         NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st));
     }
     NPHC_CK(launch_xy_classify(S->M, xs, v, R->theta, R->index, R->energy, R->mineig, R->logdet, st));
-    NPHC_CK(launch_counts(v, R->flags, R->index, R->counts, st));
+    if ((s = endgame())) return s;
+    NPHC_CK(launch_counts(v, R->flags, R->index, R->counts, st, R->egst, R->cycle));
     R->stream = st;
     R->solved = true;
     R->launches = nphc_launch_counter(0) - launches0;
@@ -791,6 +885,19 @@ nphc_status nphc_result_copy_sps(const nphc_result *R, int64_t cap, double *thet
         if (path) path[i] = pa[j];
         if (log_abs_det) log_abs_det[i] = ld_all[j];
     }
+    return NPHC_OK;
+}
+
+nphc_status nphc_result_copy_endgame(const nphc_result *R, int64_t cap, int32_t *cycle,
+                                     int32_t *eg_status, int64_t *n_out) {
+    if (!R || !n_out || cap < 0) return fail(NPHC_EINVAL, "invalid argument");
+    if (!R->solved) return fail(NPHC_ESTATE, "no solve on this result");
+    NPHC_CK(cudaStreamSynchronize(R->stream));
+    *n_out = R->P;
+    const int64_t k = std::min<int64_t>(R->P, cap);
+    if (k == 0) return NPHC_OK;
+    if (cycle) NPHC_CK(cudaMemcpy(cycle, R->cycle, sizeof(int32_t) * k, cudaMemcpyDeviceToHost));
+    if (eg_status) NPHC_CK(cudaMemcpy(eg_status, R->egst, sizeof(int32_t) * k, cudaMemcpyDeviceToHost));
     return NPHC_OK;
 }
 

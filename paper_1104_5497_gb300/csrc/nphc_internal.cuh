@@ -135,7 +135,24 @@ struct XYCtl {                              // step control of one tracking call
     int sparse;                             // 1: spread a short list, ceil(list / warps) paths per warp
     int crawl_steps;                        // near t = 1, 1 - t must halve within this many
                                             // accepted steps (0: no crawl test)
+    double t_end;                           // tracking stops here: 1, or 1 - r0 before the
+                                            // Cauchy endgame
 };
+
+struct EGCtl {                              // the Cauchy endgame (cauchy.cuh)
+    double lr0, lnratio;                    // ln of the first radius |1 - t| and of the ratio
+    int n_radii, samples, max_cycle;        // radii, samples per turn, largest cycle number
+    double tol_close, tol_conv;             // turn closure and estimate agreement (relative)
+    double tol_res;                         // the estimate solves P: ||P||_inf <= tol max(1, ||e||^2)
+    double grow_inf;                        // growth per radius of a pole: ratio^(-1/(2 max_cycle))
+    double hmin;                            // smallest step, in sample intervals
+    int max_attempts;                       // step attempts per path
+    double eps, trust, rdiv;                // corrector tolerance, first-correction bound,
+    int max_newton, grow_after;             // divergence radius, as for FP64 tracking
+};
+
+// Scratch vectors per thread of the Cauchy endgame (the trackers keep four).
+#define NPHC_CAUCHY_STATE_VECTORS 6
 
 struct EPView {                             // device endpoint arrays (see nphc_endpoints)
     int64_t count;
@@ -203,6 +220,11 @@ cudaError_t launch_quad_refine_certify(int n, const QSys &sys, double tol_sol, d
 cudaError_t launch_xy_adjoint(int M, const XYSys &sys, int64_t count, const double *theta,
                               const double *g_energy, const double *g_theta, double *dJ,
                               cudaStream_t st);
+// The Cauchy endgame (cauchy.cuh) over the entries of wl, from points at t = 1 - r0.
+cudaError_t launch_xy_cauchy(int M, const XYSys &sys, const EGCtl &ctl, const EPView &ep,
+                             const WorkList &wl, int32_t *cyc, int32_t *egst, cudaStream_t st);
+cudaError_t launch_quad_cauchy(int n, const QSys &sys, const EGCtl &ctl, const EPView &ep,
+                               const WorkList &wl, int32_t *cyc, int32_t *egst, cudaStream_t st);
 // Host-side count of kernel launches made by this library (for the result counters).
 int64_t nphc_launch_counter(int64_t add);
 int xy_track_f32_block(int M);

@@ -23,6 +23,10 @@ __global__ void compact_kernel(const EPView ep, int pred, int32_t *flags, int32_
         // already continued in FP64 from where they entered the end zone)
         take = ep.cls[e] == NPHC_END_SINGULAR && !(flags[e] & (FLAG_FP64_CONTINUED | FLAG_RETRACKED));
         if (take) flags[e] |= FLAG_RETRACKED;
+    } else if (pred == PRED_ENDGAME) {
+        // endpoints for the Cauchy endgame: finite but not certified, or tracking failed
+        const int c = ep.cls[e];
+        take = c == NPHC_END_SINGULAR || c == NPHC_END_FAILED;
     } else if (pred == PRED_REACHED) {
         // endpoints to refine; every other path gets its final class here
         const int st = ep.status[e];
@@ -231,7 +235,7 @@ __global__ void dedup_unhashed_kernel(const EPView ep, int n, double delta0, Ded
 
 // ---------------------------------------------------------------- counters --
 __global__ void counts_kernel(const EPView ep, const int32_t *flags, const int32_t *index,
-                              int64_t *counts) {
+                              int64_t *counts, const int32_t *egst, const int32_t *cycle) {
     __shared__ unsigned long long loc[NPHC_NCOUNTS];
     for (int i = threadIdx.x; i < NPHC_NCOUNTS; i += blockDim.x) loc[i] = 0;
     __syncthreads();
@@ -256,6 +260,16 @@ __global__ void counts_kernel(const EPView ep, const int32_t *flags, const int32
         if (c == NPHC_END_REAL && index) {
             const int ix = index[e];
             if (ix >= 0 && ix < NPHC_MAX_N) atomicAdd(&loc[NPHC_COUNT_INDEX0 + ix], 1ull);
+        }
+        if (egst && egst[e] != NPHC_EG_NONE) {
+            const int g = egst[e];
+            atomicAdd(&loc[NPHC_COUNT_EG_RUN], 1ull);
+            if (g == NPHC_EG_CONVERGED) {
+                atomicAdd(&loc[NPHC_COUNT_EG_CONVERGED], 1ull);
+                if (cycle[e] >= 2) atomicAdd(&loc[NPHC_COUNT_EG_MULTIPLE], 1ull);
+            } else if (g == NPHC_EG_AT_INFINITY || g == NPHC_EG_DIVERGED) {
+                atomicAdd(&loc[NPHC_COUNT_EG_AT_INFINITY], 1ull);
+            }
         }
     }
     __syncthreads();
@@ -332,10 +346,11 @@ cudaError_t launch_dedup(const EPView &ep, int n, double delta, DedupScratch w, 
 }
 
 cudaError_t launch_counts(const EPView &ep, const int32_t *flags, const int32_t *index,
-                          int64_t *counts, cudaStream_t st) {
+                          int64_t *counts, cudaStream_t st, const int32_t *egst,
+                          const int32_t *cycle) {
     cudaError_t err = cudaMemsetAsync(counts, 0, sizeof(int64_t) * NPHC_NCOUNTS, st);
     if (err || ep.count == 0) return err;
-    counts_kernel<<<blocks_for(ep.count, 256), 256, 0, st>>>(ep, flags, index, counts);
+    counts_kernel<<<blocks_for(ep.count, 256), 256, 0, st>>>(ep, flags, index, counts, egst, cycle);
     nphc_launch_counter(1);
     return cudaGetLastError();
 }

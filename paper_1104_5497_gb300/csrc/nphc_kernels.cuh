@@ -3,7 +3,7 @@
 
 #include "nphc_internal.cuh"
 
-enum { PRED_HANDOFF = 1, PRED_UNCERTIFIED_FP32 = 2, PRED_REACHED = 3 };
+enum { PRED_HANDOFF = 1, PRED_UNCERTIFIED_FP32 = 2, PRED_REACHED = 3, PRED_ENDGAME = 4 };
 enum { FLAG_FP64_CONTINUED = 1, FLAG_RETRACKED = 2, FLAG_RETRACKED_DUP = 4 };
 
 #define DD_LEVELS 4   // grid pitches 1e-6, 1e-4, 1e-2, 1
@@ -28,8 +28,10 @@ cudaError_t launch_flag_list(const int32_t *list, const int32_t *count, int64_t 
 cudaError_t launch_dedup(const EPView &ep, int n, double delta, DedupScratch w, int32_t *list,
                          int32_t *count, cudaStream_t st, const int32_t *mlist = nullptr,
                          const int32_t *mcount = nullptr);
+// egst / cycle (may be NULL): the Cauchy endgame's outcome, for its counters.
 cudaError_t launch_counts(const EPView &ep, const int32_t *flags, const int32_t *index,
-                          int64_t *counts, cudaStream_t st);
+                          int64_t *counts, cudaStream_t st, const int32_t *egst = nullptr,
+                          const int32_t *cycle = nullptr);
 cudaError_t launch_real_list(const EPView &ep, int32_t *list, int32_t *count, cudaStream_t st);
 cudaError_t launch_iota(int64_t *path, int64_t n, cudaStream_t st);
 cudaError_t launch_gather_sps(const EPView &ep, int M, const int32_t *list, const int32_t *count,

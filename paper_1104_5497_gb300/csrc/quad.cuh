@@ -13,6 +13,7 @@
 // xy_endgame.cuh on DP.
 #pragma once
 
+#include "cauchy.cuh"
 #include "xy_endgame.cuh"
 #include "xy_track.cuh"
 
@@ -60,9 +61,26 @@ struct QuadProblem {
     static __device__ __forceinline__ void residual(const Sys &S, const SVec<double, BLOCK> &pt,
                                                     double s, double omt,
                                                     const SVec<double, BLOCK> &out, bool wr) {
+        residual_g(S, pt, s, omt, cx<double>{S.gre, S.gim}, out, wr);
+    }
+
+    template <class Out2>
+    static __device__ __forceinline__ bool solve(const Sys &S, const SMat<NV, double, BLOCK> &A,
+                                                 const SVec<double, BLOCK> &pt, double s,
+                                                 double omt, bool two_rhs,
+                                                 const SVec<double, BLOCK> &res,
+                                                 const SVec<double, BLOCK> &out1, const Out2 &out2,
+                                                 bool wr) {
+        return solve_g(S, A, pt, s, omt, cx<double>{S.gre, S.gim}, two_rhs, res, out1, out2, wr);
+    }
+
+    // the same with an explicit gamma (see XYProblem::residual_g)
+    static __device__ __forceinline__ void residual_g(const Sys &S, const SVec<double, BLOCK> &pt,
+                                                      double s, double omt, cx<double> gam,
+                                                      const SVec<double, BLOCK> &out, bool wr) {
         using E = EFT<double>;
         const ext<double> zero = {0.0, 0.0};
-        const double g1r = E::mul(omt, S.gre), g1i = E::mul(omt, S.gim);
+        const double g1r = E::mul(omt, gam.re), g1i = E::mul(omt, gam.im);
 #pragma unroll 1
         for (int i = 0; i < NV; i++) {
             ext<double> pr = zero, pi = zero;
@@ -98,13 +116,12 @@ struct QuadProblem {
 
     // H_z d = r: r = -H_t (two_rhs false) or r1 = res and r2 = -H_t (two_rhs true)
     template <class Out2>
-    static __device__ __forceinline__ bool solve(const Sys &S, const SMat<NV, double, BLOCK> &A,
-                                                 const SVec<double, BLOCK> &pt, double s,
-                                                 double omt, bool two_rhs,
-                                                 const SVec<double, BLOCK> &res,
-                                                 const SVec<double, BLOCK> &out1, const Out2 &out2,
-                                                 bool wr) {
-        const cx<double> gam = cx<double>{S.gre, S.gim};
+    static __device__ __forceinline__ bool solve_g(const Sys &S, const SMat<NV, double, BLOCK> &A,
+                                                   const SVec<double, BLOCK> &pt, double s,
+                                                   double omt, cx<double> gam, bool two_rhs,
+                                                   const SVec<double, BLOCK> &res,
+                                                   const SVec<double, BLOCK> &out1,
+                                                   const Out2 &out2, bool wr) {
         const cx<double> g2 = cscale(2.0 * omt, gam);
 #pragma unroll 1
         for (int c = 0; c < NV; c++)
@@ -249,4 +266,11 @@ __global__ void __launch_bounds__(EG_BLOCK)
     quad_refine_certify_kernel(const __grid_constant__ QSys S, double tol_sol, double refine_eps,
                                int refine_iters, const EPView ep, const WorkList wl) {
     refine_body<EGQuad<NV>>(S, tol_sol, refine_eps, refine_iters, ep, wl, 0);
+}
+
+template <int NV>
+__global__ void __launch_bounds__(32)
+    quad_cauchy_kernel(const __grid_constant__ QSys S, const __grid_constant__ EGCtl C,
+                       const EPView ep, const WorkList wl, int32_t *cyc, int32_t *egst) {
+    cauchy_body<QuadProblem<NV>>(S, C, ep, wl, cyc, egst);
 }

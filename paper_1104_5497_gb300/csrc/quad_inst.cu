@@ -60,3 +60,24 @@ cudaError_t NPHC_CAT(launch_quad_refine_certify_n, NPHC_QUAD_NV)(const QSys &sys
     nphc_launch_counter(1);
     return cudaGetLastError();
 }
+
+cudaError_t NPHC_CAT(launch_quad_cauchy_n, NPHC_QUAD_NV)(const QSys &sys, const EGCtl &ctl,
+                                                         const EPView &ep, const WorkList &wl,
+                                                         int32_t *cyc, int32_t *egst,
+                                                         cudaStream_t st) {
+    using P = QuadProblem<NPHC_QUAD_NV>;
+    if (ep.count <= 0) return cudaSuccess;
+    const size_t smem = track_smem_per_thread<P>() * P::BLOCK;
+    auto k = quad_cauchy_kernel<NPHC_QUAD_NV>;
+    int full = 0;
+    cudaError_t e = persistent_grid(k, P::BLOCK, smem, full);
+    if (e != cudaSuccess) return e;
+    const int64_t need = (ep.count + P::BLOCK - 1) / P::BLOCK;   // the list is at most ep.count long
+    const int64_t cap = wl.state_threads / P::BLOCK;
+    int64_t grid = need < full ? need : full;
+    if (grid > cap) grid = cap;
+    if (grid <= 0) return cudaErrorInvalidValue;
+    k<<<(int)grid, P::BLOCK, smem, st>>>(sys, ctl, ep, wl, cyc, egst);
+    nphc_launch_counter(1);
+    return cudaGetLastError();
+}

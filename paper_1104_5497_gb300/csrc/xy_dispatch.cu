@@ -65,3 +65,17 @@ cudaError_t launch_quad_refine_certify(int n, const QSys &sys, double tol_sol, d
     switch (n) { NPHC_FOR_EACH_QN(C) default: return cudaErrorInvalidValue; }
 #undef C
 }
+
+cudaError_t launch_xy_cauchy(int M, const XYSys &sys, const EGCtl &ctl, const EPView &ep,
+                             const WorkList &wl, int32_t *cyc, int32_t *egst, cudaStream_t st) {
+#define C(MM) case MM: return launch_xy_cauchy_m##MM(sys, ctl, ep, wl, cyc, egst, st);
+    switch (M) { NPHC_FOR_EACH_M(C) default: return cudaErrorInvalidValue; }
+#undef C
+}
+
+cudaError_t launch_quad_cauchy(int n, const QSys &sys, const EGCtl &ctl, const EPView &ep,
+                               const WorkList &wl, int32_t *cyc, int32_t *egst, cudaStream_t st) {
+#define C(NN) case NN: return launch_quad_cauchy_n##NN(sys, ctl, ep, wl, cyc, egst, st);
+    switch (n) { NPHC_FOR_EACH_QN(C) default: return cudaErrorInvalidValue; }
+#undef C
+}

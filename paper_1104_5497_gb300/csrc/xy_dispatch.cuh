@@ -24,7 +24,9 @@
     cudaError_t launch_xy_adjoint_m##MM(const XYSys &, int64_t, const double *, const double *, \
                                         const double *, double *, cudaStream_t);              \
     cudaError_t launch_xy_classify_m##MM(const XYSys &, const EPView &, double *, int32_t *, \
-                                         double *, double *, double *, cudaStream_t);
+                                         double *, double *, double *, cudaStream_t);        \
+    cudaError_t launch_xy_cauchy_m##MM(const XYSys &, const EGCtl &, const EPView &,        \
+                                       const WorkList &, int32_t *, int32_t *, cudaStream_t);
 NPHC_FOR_EACH_M(NPHC_DECL)
 #undef NPHC_DECL
 
@@ -34,6 +36,8 @@ NPHC_FOR_EACH_M(NPHC_DECL)
                                         const WorkList &, int, cudaStream_t);                 \
     cudaError_t launch_quad_refine_certify_n##NN(const QSys &, double, double, int,          \
                                                  const EPView &, int64_t, const WorkList &,  \
-                                                 cudaStream_t);
+                                                 cudaStream_t);                               \
+    cudaError_t launch_quad_cauchy_n##NN(const QSys &, const EGCtl &, const EPView &,        \
+                                         const WorkList &, int32_t *, int32_t *, cudaStream_t);
 NPHC_FOR_EACH_QN(NPHC_QDECL)
 #undef NPHC_QDECL

@@ -1,8 +1,44 @@
 // xy_inst.cu -- one ring size of one kernel family per compilation, so that the build
 // compiles the heavily unrolled kernels in parallel.  Compiled with
 //   -DNPHC_INST_M=<M>  (free sites, N = M + 1)
-//   -DNPHC_INST_KIND=0 (FP32 tracker), 1 (FP64 tracker) or 2 (FP64 endgame)
+//   -DNPHC_INST_KIND=0 (FP32 tracker), 1 (FP64 tracker), 2 (FP64 refinement,
+//   certification, classification, adjoint) or 3 (Cauchy endgame)
 #include "xy_dispatch.cuh"
+
+#if NPHC_INST_KIND == 3
+#include "cauchy.cuh"
+
+cudaError_t NPHC_CAT(launch_xy_cauchy_m, NPHC_INST_M)(const XYSys &sys, const EGCtl &ctl,
+                                                      const EPView &ep, const WorkList &wl,
+                                                      int32_t *cyc, int32_t *egst,
+                                                      cudaStream_t st) {
+    constexpr int M = NPHC_INST_M, BLK = 32;
+    using P = XYProblem<M, double, BLK>;
+    if (ep.count <= 0) return cudaSuccess;
+    const size_t smem = track_smem_per_thread<P>() * BLK;
+    auto k = xy_cauchy_kernel<M>;
+    static bool attr_set = false;   // once per process for this instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BLK, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t full = (int64_t)sms * (per > 0 ? per : 1);
+    const int64_t need = (ep.count + BLK - 1) / BLK;   // the list is at most ep.count long
+    const int64_t cap = wl.state_threads / BLK;        // the scratch holds state for this many
+    int64_t grid = need < full ? need : full;
+    if (grid > cap) grid = cap;
+    if (grid <= 0) return cudaErrorInvalidValue;
+    k<<<(int)grid, BLK, smem, st>>>(sys, ctl, ep, wl, cyc, egst);
+    nphc_launch_counter(1);
+    return cudaGetLastError();
+}
+#endif
 
 #if NPHC_INST_KIND == 0 || NPHC_INST_KIND == 1
 #include "xy_track.cuh"
@@ -73,7 +109,7 @@ cudaError_t NPHC_FN(const XYSys &sys, const XYCtl &ctl, const EPView &ep, const 
     return cudaGetLastError();
 }
 
-#else
+#elif NPHC_INST_KIND == 2
 #include "xy_endgame.cuh"
 
 cudaError_t NPHC_CAT(launch_xy_refine_certify_m, NPHC_INST_M)(const XYSys &sys, double tol_sol,

@@ -21,7 +21,8 @@
 // (xy_residual_comp: float-float in FP32, double-double in FP64).  A step is accepted when ||dz|| <= eps (1 + ||z||)
 // within max_newton iterations, and rejected when the first correction exceeds
 // trust (1 + ||z||).  Step size doubles after grow_after consecutive accepts and halves
-// on a reject; the final step lands exactly on t = 1.
+// on a reject; the final step lands exactly on t = t_end (1, or 1 - r0 before the Cauchy
+// endgame).
 //
 // A path whose ||z||_inf exceeds rdiv is taken to go to infinity, in either precision
 // (the same radius as the oracle's: genuinely finite solutions near that scale are
@@ -112,8 +113,7 @@ struct XYProblem {
 
     static __device__ __forceinline__ void residual(const Sys &S, const SVec<R, BLOCK> &pt, R s,
                                                     R omt, const SVec<R, BLOCK> &out, bool wr) {
-        xy_residual_comp<M, R, BLOCK>(JSel<R>::get(S), pt, s, omt, cx<R>{(R)S.gre, (R)S.gim}, out,
-                                      wr);
+        residual_g(S, pt, s, omt, cx<R>{(R)S.gre, (R)S.gim}, out, wr);
     }
 
     template <class Out2>
@@ -122,8 +122,26 @@ struct XYProblem {
                                                  bool two_rhs, const SVec<R, BLOCK> &res,
                                                  const SVec<R, BLOCK> &out1, const Out2 &out2,
                                                  bool wr) {
-        return xy_solve<M, R, BLOCK>(JSel<R>::get(S), A, pt, s, omt, cx<R>{(R)S.gre, (R)S.gim},
-                                     two_rhs, res, out1, out2, wr);
+        return solve_g(S, A, pt, s, omt, cx<R>{(R)S.gre, (R)S.gim}, two_rhs, res, out1, out2, wr);
+    }
+
+    // the same with an explicit gamma (per thread: the Cauchy endgame's equivalent real-t
+    // homotopy at a complex t)
+    static __device__ __forceinline__ void residual_g(const Sys &S, const SVec<R, BLOCK> &pt, R s,
+                                                      R omt, cx<R> gam,
+                                                      const SVec<R, BLOCK> &out, bool wr) {
+        xy_residual_comp<M, R, BLOCK>(JSel<R>::get(S), pt, s, omt, gam, out, wr);
+    }
+
+    template <class Out2>
+    static __device__ __forceinline__ bool solve_g(const Sys &S, const SMat<M, R, BLOCK> &A,
+                                                   const SVec<R, BLOCK> &pt, R s, R omt,
+                                                   cx<R> gam, bool two_rhs,
+                                                   const SVec<R, BLOCK> &res,
+                                                   const SVec<R, BLOCK> &out1, const Out2 &out2,
+                                                   bool wr) {
+        return xy_solve<M, R, BLOCK>(JSel<R>::get(S), A, pt, s, omt, gam, two_rhs, res, out1, out2,
+                                     wr);
     }
 };
 
@@ -229,9 +247,9 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
         // solve (only when some lane needs it), phases 1..3 = RK4 stages 2..4, phases
         // 4.. = Newton corrector iterations at t + h
         double hh = h, t1 = t + h;
-        if (t1 >= 1.0) {
-            t1 = 1.0;
-            hh = 1.0 - t;
+        if (t1 >= C.t_end) {
+            t1 = C.t_end;
+            hh = C.t_end - t;
         }
         const R hr = (R)hh;
         bool go = act && !need_k1;
@@ -352,7 +370,7 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                               (double)zi <= C.rdiv * (1.0 + RDIV_BAND))
                                  ? NPHC_PATH_HANDOFF
                                  : NPHC_PATH_DIVERGED;
-                else if (t >= 1.0)
+                else if (t >= C.t_end)
                     status = NPHC_PATH_REACHED;
                 // FP32 pass: keep the state where the path enters the end zone; a path
                 // that the pass later hands off resumes in FP64 from there, not from the

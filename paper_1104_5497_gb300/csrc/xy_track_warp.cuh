@@ -365,9 +365,9 @@ __global__ void __launch_bounds__(32 * WARPS)
         __syncwarp();
         while (status == NPHC_PATH_RUNNING) {
             double hh = h, t1 = t + h;
-            if (t1 >= 1.0) {
-                t1 = 1.0;
-                hh = 1.0 - t;
+            if (t1 >= C.t_end) {
+                t1 = C.t_end;
+                hh = C.t_end - t;
             }
             bool conv = false, bad = false;
             double zpn = 0.0;
@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(32 * WARPS)
                     h = fmin(2.0 * h, C.hmax);
                 }
                 if (zi > C.rdiv) status = NPHC_PATH_DIVERGED;
-                else if (t >= 1.0) status = NPHC_PATH_REACHED;
+                else if (t >= C.t_end) status = NPHC_PATH_REACHED;
             } else {
                 run = 0;
                 rejects++;

@@ -24,7 +24,12 @@ END_NONE, END_SINGULAR, END_REAL, END_NONREAL, END_UNDECIDED, END_DUPLICATE, END
 
 COUNT_NAMES = ["paths", "reached", "diverged", "failed", "real", "nonreal", "undecided",
                "singular", "duplicate", "handoff", "retracked", "solves", "launches"]
-NCOUNTS = len(COUNT_NAMES) + NPHC_MAX_N
+# after the index histogram (NPHC_COUNT_EG_*)
+EG_COUNT_NAMES = ["eg_run", "eg_converged", "eg_multiple", "eg_at_infinity"]
+NCOUNTS = len(COUNT_NAMES) + NPHC_MAX_N + len(EG_COUNT_NAMES)
+# Cauchy endgame outcomes (NPHC_EG_*)
+EG_NONE, EG_CONVERGED, EG_NOT_CLOSED, EG_NOT_CONVERGED, EG_TRACK_FAILED, EG_DIVERGED, \
+    EG_AT_INFINITY = range(7)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBUDGET", 5: "ESTATE"}
 
 
@@ -47,7 +52,12 @@ class nphc_options(ctypes.Structure):
                 ("crawl_steps_fp32", ctypes.c_int),
                 ("grow_after", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("refine_eps", ctypes.c_double),
-                ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int)]
+                ("block_size", ctypes.c_int), ("blocks_per_sm", ctypes.c_int),
+                ("endgame", ctypes.c_int), ("eg_r0", ctypes.c_double),
+                ("eg_ratio", ctypes.c_double), ("eg_radii", ctypes.c_int),
+                ("eg_samples", ctypes.c_int), ("eg_max_cycle", ctypes.c_int),
+                ("eg_tol_close", ctypes.c_double), ("eg_tol_conv", ctypes.c_double),
+                ("eg_h_min", ctypes.c_double), ("eg_max_attempts", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -90,6 +100,9 @@ def lib():
                        vp, vp, i32, vp, ctypes.c_size_t, vp],
         "nphc_refine_certify": [vp, ctypes.POINTER(nphc_options), ctypes.POINTER(nphc_endpoints),
                                 vp, vp, vp],
+        "nphc_endgame": [vp, ctypes.POINTER(nphc_options), ctypes.POINTER(nphc_endpoints), vp, vp,
+                         vp, vp, vp, ctypes.c_size_t, vp],
+        "nphc_result_copy_endgame": [vp, i64, pi32, pi32, pi64],
         "nphc_dedup": [vp, ctypes.POINTER(nphc_options), ctypes.POINTER(nphc_endpoints), vp, vp,
                        vp, ctypes.c_size_t, vp],
         "nphc_dedup_noalloc": [vp, ctypes.POINTER(nphc_options), ctypes.POINTER(nphc_endpoints),
@@ -237,7 +250,18 @@ class Result:
         _check("nphc_result_counts", lib().nphc_result_counts(self.handle, _pi64(c)))
         out = {k: int(c[i]) for i, k in enumerate(COUNT_NAMES)}
         out["index_hist"] = [int(v) for v in c[len(COUNT_NAMES):len(COUNT_NAMES) + self.system.M + 1]]
+        base = len(COUNT_NAMES) + NPHC_MAX_N
+        out.update({k: int(c[base + i]) for i, k in enumerate(EG_COUNT_NAMES)})
         return out
+
+    def endgame(self) -> dict:
+        """Per path: Cauchy endgame cycle number and status (EG_NONE where it did not run)."""
+        P = self.system.npaths
+        n = ctypes.c_int64()
+        cy, st = np.zeros(P, np.int32), np.zeros(P, np.int32)
+        _check("nphc_result_copy_endgame", lib().nphc_result_copy_endgame(
+            self.handle, P, _pi32(cy), _pi32(st), ctypes.byref(n)))
+        return dict(cycle=cy, status=st)
 
     def stationary_points(self) -> dict:
         M = self.system.M
@@ -370,6 +394,19 @@ def refine_certify(system: System, opts: nphc_options, ep: DeviceEndpoints, list
         system.handle, ctypes.byref(opts), ctypes.byref(s),
         None if list_ is None else list_.data_ptr(),
         None if list_count is None else list_count.data_ptr(), _stream_ptr(stream)))
+
+
+def endgame(system: System, opts: nphc_options, ep: DeviceEndpoints, workspace, cycle, eg_status,
+            list_=None, list_count=None, stream=None) -> None:
+    """nphc_endgame: FP64 tracking of the selected entries to t = 1 - eg_r0, then the Cauchy
+    endgame; writes z (estimates), cycle and eg_status (int32 device tensors [count])."""
+    s = ep.struct()
+    _check("nphc_endgame", lib().nphc_endgame(
+        system.handle, ctypes.byref(opts), ctypes.byref(s),
+        None if list_ is None else list_.data_ptr(),
+        None if list_count is None else list_count.data_ptr(), cycle.data_ptr(),
+        eg_status.data_ptr(), workspace.data_ptr(), workspace.numel() * workspace.element_size(),
+        _stream_ptr(stream)))
 
 
 def dedup(system: System, opts: nphc_options, ep: DeviceEndpoints, workspace, dup_list=None,

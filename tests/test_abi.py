@@ -94,3 +94,33 @@ def test_quadratic_system_argument_checks(N_):
         with pytest.raises(N_.NphcError) as ei:
             N_.System.quadratic(n, t["eq"], t["va"], t["vb"], t["coef"])
         assert ei.value.status == 1
+
+
+def test_endgame_argument_checks(N_):
+    """nphc_endgame rejects bad endgame options and missing outputs before any CUDA call
+    (the endpoint pointers below are never dereferenced)."""
+    import ctypes
+    s = N_.System(5, 1.0)
+    ep = N_.nphc_endpoints()
+    ep.count = 4
+    for f in ("path", "z_re", "z_im", "t", "h", "status", "steps", "solves", "newton"):
+        setattr(ep, f, 16)
+    L = N_.lib()
+    dummy = ctypes.c_void_p(16)
+    bad = [dict(eg_r0=1.5), dict(eg_r0=0.0), dict(eg_ratio=1.0), dict(eg_radii=0),
+           dict(eg_samples=1), dict(eg_samples=5000), dict(eg_max_cycle=0),
+           dict(eg_tol_close=0.0), dict(eg_tol_conv=-1.0), dict(eg_h_min=0.0),
+           dict(eg_max_attempts=0)]
+    for kw in bad:
+        o = N_.options_default(**kw)
+        rc = L.nphc_endgame(s.handle, ctypes.byref(o), ctypes.byref(ep), None, None, dummy, dummy,
+                            dummy, 1 << 40, None)
+        assert rc == 1, kw
+        assert b"endgame options" in L.nphc_last_error()
+    o = N_.options_default()
+    rc = L.nphc_endgame(s.handle, ctypes.byref(o), ctypes.byref(ep), None, None, None, dummy,
+                        dummy, 1 << 40, None)
+    assert rc == 1 and b"cycle" in L.nphc_last_error()
+    d = N_.options_default()
+    assert (d.endgame, d.eg_r0, d.eg_ratio, d.eg_radii, d.eg_samples, d.eg_max_cycle) == \
+        (0, 1 / 16, 0.25, 8, 16, 8)
