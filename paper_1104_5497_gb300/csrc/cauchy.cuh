@@ -26,10 +26,12 @@
 // so the predictor uses the trackers' solve too (same integral curve; off the path the
 // two vector fields differ by terms in H, which the corrector removes).
 //
-// Layout as the per-thread tracker (xy_track.cuh): one path per thread, lockstep phases
-// of a step (ph 0: Newton at the current point and dz/dw, for a point just taken over;
-// 1..3: RK4 stages; 4..: corrector), the matrix and two vectors in shared memory, six
-// state vectors in global scratch.
+// cauchy_body: layout as the per-thread tracker (xy_track.cuh), for any tracker policy
+// (the generic quadratic systems use it): one path per thread, lockstep phases of a step
+// (ph 0: Newton at the current point and dz/dw, for a point just taken over; 1..3: RK4
+// stages; 4..: corrector), the matrix and two vectors in shared memory, six state
+// vectors in global scratch.  The XY ring runs the same endgame with one path per warp
+// (cauchy_warp.cuh).
 #pragma once
 
 #include "xy_track.cuh"
@@ -392,11 +394,4 @@ __device__ __forceinline__ void cauchy_body(const typename P::Sys &S, const EGCt
             e = -1;
         }
     }
-}
-
-template <int M>
-__global__ void __launch_bounds__(32)
-    xy_cauchy_kernel(const __grid_constant__ XYSys S, const __grid_constant__ EGCtl C,
-                     const EPView ep, const WorkList wl, int32_t *cyc, int32_t *egst) {
-    cauchy_body<XYProblem<M, double, 32>>(S, C, ep, wl, cyc, egst);
 }

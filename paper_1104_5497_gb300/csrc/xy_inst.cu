@@ -6,17 +6,17 @@
 #include "xy_dispatch.cuh"
 
 #if NPHC_INST_KIND == 3
-#include "cauchy.cuh"
+#include "cauchy_warp.cuh"
 
+// one path per warp, 4 warps per block
 cudaError_t NPHC_CAT(launch_xy_cauchy_m, NPHC_INST_M)(const XYSys &sys, const EGCtl &ctl,
                                                       const EPView &ep, const WorkList &wl,
                                                       int32_t *cyc, int32_t *egst,
                                                       cudaStream_t st) {
-    constexpr int M = NPHC_INST_M, BLK = 32;
-    using P = XYProblem<M, double, BLK>;
+    constexpr int M = NPHC_INST_M, WARPS = 4;
     if (ep.count <= 0) return cudaSuccess;
-    const size_t smem = track_smem_per_thread<P>() * BLK;
-    auto k = xy_cauchy_kernel<M>;
+    const size_t smem = cauchy_warp_smem_per_warp<M>() * WARPS;
+    auto k = xy_cauchy_warp_kernel<M, WARPS>;
     static bool attr_set = false;   // once per process for this instantiation
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -26,15 +26,12 @@ cudaError_t NPHC_CAT(launch_xy_cauchy_m, NPHC_INST_M)(const XYSys &sys, const EG
     int dev = 0, sms = 0, per = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BLK, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 32 * WARPS, smem);
     if (e != cudaSuccess) return e;
     const int64_t full = (int64_t)sms * (per > 0 ? per : 1);
-    const int64_t need = (ep.count + BLK - 1) / BLK;   // the list is at most ep.count long
-    const int64_t cap = wl.state_threads / BLK;        // the scratch holds state for this many
-    int64_t grid = need < full ? need : full;
-    if (grid > cap) grid = cap;
-    if (grid <= 0) return cudaErrorInvalidValue;
-    k<<<(int)grid, BLK, smem, st>>>(sys, ctl, ep, wl, cyc, egst);
+    const int64_t need = (ep.count + WARPS - 1) / WARPS;   // the list is at most ep.count long
+    const int grid = (int)(need < full ? need : full);
+    k<<<grid, 32 * WARPS, smem, st>>>(sys, ctl, ep, wl, cyc, egst);
     nphc_launch_counter(1);
     return cudaGetLastError();
 }
