@@ -54,3 +54,28 @@ def test_batch_instances_match_the_oracle():
         c = batch.result(i).counts()
         assert c["real"] == (ref["cls"] == O.C_REAL).sum()
         assert c["nonreal"] == (ref["cls"] == O.C_NONREAL).sum()
+
+
+def test_batch_with_endgame_matches_single_solves():
+    """opts.endgame inside a batch (eager, captured, replayed): every instance gets the
+    endgame outcomes of its single solve (rings with N = 0 mod 4 have singular endpoints;
+    the other instances have none)."""
+    N_ = nphc()
+    rings = [(8, 1.0, np.exp(0.5j)), (4, 1.5, np.exp(1.1j)), (8, 1.5, np.exp(2.3j)), (6, 1.0, np.exp(0.5j))]
+    systems = [N_.System(N, s) for N, s, _ in rings]
+    opts = [N_.options_default(gamma=g, endgame=1) for _, _, g in rings]
+    batch = N_.Batch(systems)
+    singles = [N_.solve(s, o) for s, o in zip(systems, opts)]
+    for mode in ("eager", "capture", "replay"):
+        batch.solve(opts, graph=(mode != "eager"))
+        for i, single in enumerate(singles):
+            a, b = batch.result(i).counts(), single.counts()
+            for k in ("eg_run", "eg_converged", "eg_multiple", "eg_at_infinity", "singular", "failed"):
+                assert a[k] == b[k], (mode, i, k, a[k], b[k])
+            ea, eb = batch.result(i).endgame(), single.endgame()
+            assert np.array_equal(ea["status"], eb["status"]) and np.array_equal(ea["cycle"], eb["cycle"])
+            conv = eb["status"] == N_.EG_CONVERGED
+            za, zb = batch.result(i).endpoints()["z"][conv], single.endpoints()["z"][conv]
+            if conv.any():
+                assert np.abs(za - zb).max() <= 1e-9 * (1 + np.abs(zb).max())
+    assert singles[0].counts()["eg_converged"] > 0
