@@ -29,8 +29,8 @@
 // cauchy_body: layout as the per-thread tracker (xy_track.cuh), for any tracker policy
 // (the generic quadratic systems use it): one path per thread, lockstep phases of a step
 // (ph 0: Newton at the current point and dz/dw, for a point just taken over; 1..3: RK4
-// stages; 4..: corrector), the matrix and two vectors in shared memory, six state
-// vectors in global scratch.  The XY ring runs the same endgame with one path per warp
+// stages; 4..: corrector), the matrix and the evaluation point in shared memory (the
+// solve output shares the right-hand-side columns), six state vectors in global scratch.  The XY ring runs the same endgame with one path per warp
 // (cauchy_warp.cuh).
 #pragma once
 
@@ -89,7 +89,7 @@ __device__ __forceinline__ void cauchy_body(const typename P::Sys &S, const EGCt
     const int tid = threadIdx.x, lane = tid & 31;
     const SMat<MD, R, BLOCK> A{sm + tid};
     const SVec<R, BLOCK> ZC{sm + MD * (MD + 2) * BLOCK + tid};
-    const SVec<R, BLOCK> W1{sm + (MD * (MD + 2) + NV) * BLOCK + tid};
+    const SVec<R, BLOCK> W1{sm + MD * MD * BLOCK + tid};   // the right-hand-side columns
     const int64_t gtid = (int64_t)blockIdx.x * BLOCK + tid;
     const int64_t nth = wl.state_threads;
     cx<R> *st = reinterpret_cast<cx<R> *>(wl.state);

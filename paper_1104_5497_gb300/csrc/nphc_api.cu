@@ -108,6 +108,8 @@ struct nphc_result {
     void *ws;
     size_t ws_bytes;
     cudaStream_t stream;
+    cudaStream_t side;        // second stream of the mixed pipeline (refinement beside the
+    cudaEvent_t ev_fork, ev_join;   // FP64 continuation), forked and joined by events
     bool solved;
     int64_t launches;        // kernels launched by the last solve (host count)
 };
@@ -694,7 +696,12 @@ nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
     R->solved = false;
     e = launch_iota(R->ep.path, P, nullptr);
     if (e == cudaSuccess) e = cudaStreamSynchronize(nullptr);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&R->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&R->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&R->ev_join, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        if (R->ev_fork) cudaEventDestroy(R->ev_fork);
+        if (R->side) cudaStreamDestroy(R->side);
         cudaFree(R->block);
         delete R;
         return fail(NPHC_ECUDA, std::string("result init: ") + cudaGetErrorString(e));
@@ -760,12 +767,26 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
                                          R->P, l0, 1, st));
         NPHC_CK(launch_compact(v, PRED_HANDOFF, R->flags, R->list[0], R->lcount + 5, st));
-        if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[0], R->lcount + 5, true, true, R->ws, 1, st)))
-            return s;
-        NPHC_CK(launch_compact(v, PRED_REACHED, R->flags, R->list[3], R->lcount + 3, st));
+        // the FP64 continuation of the hand-offs is imbalanced (a few long paths; SMs idle
+        // about half its time) and touches only hand-off entries: the refinement of the
+        // endpoints the FP32 pass reached (every other entry) runs beside it on the side
+        // stream, selected by the hand-off flag so that it never reads an entry the
+        // continuation writes
+        NPHC_CK(cudaEventRecord(R->ev_fork, st));
+        NPHC_CK(cudaStreamWaitEvent(R->side, R->ev_fork, 0));
+        NPHC_CK(launch_compact(v, PRED_REACHED_DIRECT, R->flags, R->list[3], R->lcount + 3, R->side));
         WorkList l3 = {R->list[3], R->lcount + 3, nullptr, nullptr, 0};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
-                                         R->P, l3, 0, st));
+                                         R->P, l3, 0, R->side));
+        NPHC_CK(cudaEventRecord(R->ev_join, R->side));
+        if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[0], R->lcount + 5, true, true, R->ws, 1, st)))
+            return s;
+        NPHC_CK(cudaStreamWaitEvent(st, R->ev_join, 0));
+        // then the continued entries (the shortcut's certified ones included) that reached t = 1
+        NPHC_CK(launch_compact(v, PRED_REACHED_CONTINUED, R->flags, R->list[0], R->lcount + 7, st));
+        WorkList l0c = {R->list[0], R->lcount + 7, nullptr, nullptr, 0};
+        NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
+                                         R->P, l0c, 0, st));
         // FP64 re-track from t = 0 of FP32 endpoints that did not certify
         NPHC_CK(launch_compact(v, PRED_UNCERTIFIED_FP32, R->flags, R->list[1], R->lcount + 1, st));
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[1], R->lcount + 1, false, true, R->ws, 2, st)))
@@ -939,8 +960,12 @@ void nphc_result_destroy(nphc_result *R) {
     if (!R) return;
     if (R->block) {
         if (R->stream) cudaStreamSynchronize(R->stream);
+        if (R->side) cudaStreamSynchronize(R->side);
         cudaFree(R->block);
     }
+    if (R->ev_join) cudaEventDestroy(R->ev_join);
+    if (R->ev_fork) cudaEventDestroy(R->ev_fork);
+    if (R->side) cudaStreamDestroy(R->side);
     delete R;
 }
 

@@ -27,13 +27,18 @@ __global__ void compact_kernel(const EPView ep, int pred, int32_t *flags, int32_
         // endpoints for the Cauchy endgame: finite but not certified, or tracking failed
         const int c = ep.cls[e];
         take = c == NPHC_END_SINGULAR || c == NPHC_END_FAILED;
-    } else if (pred == PRED_REACHED) {
-        // endpoints to refine; every other path gets its final class here
-        const int st = ep.status[e];
-        take = st == NPHC_PATH_REACHED;
-        if (!take) {
-            ep.cls[e] = st == NPHC_PATH_DIVERGED ? NPHC_END_NONE : NPHC_END_FAILED;
-            ep.alpha[e] = ep.beta[e] = ep.gamma[e] = ep.resid[e] = INFINITY;
+    } else if (pred == PRED_REACHED || pred == PRED_REACHED_DIRECT || pred == PRED_REACHED_CONTINUED) {
+        // endpoints to refine; every other path gets its final class here.  The split forms
+        // touch only the entries on their side of the hand-off flag (the other side may be
+        // in flight on another stream)
+        const bool cont = (flags[e] & FLAG_FP64_CONTINUED) != 0;
+        if (pred == PRED_REACHED || cont == (pred == PRED_REACHED_CONTINUED)) {
+            const int st = ep.status[e];
+            take = st == NPHC_PATH_REACHED;
+            if (!take) {
+                ep.cls[e] = st == NPHC_PATH_DIVERGED ? NPHC_END_NONE : NPHC_END_FAILED;
+                ep.alpha[e] = ep.beta[e] = ep.gamma[e] = ep.resid[e] = INFINITY;
+            }
         }
     }
     if (take) list[atomicAdd(count, 1)] = (int32_t)e;

@@ -3,7 +3,14 @@
 
 #include "nphc_internal.cuh"
 
-enum { PRED_HANDOFF = 1, PRED_UNCERTIFIED_FP32 = 2, PRED_REACHED = 3, PRED_ENDGAME = 4 };
+enum {
+    PRED_HANDOFF = 1,
+    PRED_UNCERTIFIED_FP32 = 2,
+    PRED_REACHED = 3,             // reached entries to refine; every other entry gets its class
+    PRED_ENDGAME = 4,
+    PRED_REACHED_DIRECT = 5,      // PRED_REACHED over the entries without FLAG_FP64_CONTINUED
+    PRED_REACHED_CONTINUED = 6    // PRED_REACHED over the entries with FLAG_FP64_CONTINUED
+};
 enum { FLAG_FP64_CONTINUED = 1, FLAG_RETRACKED = 2, FLAG_RETRACKED_DUP = 4 };
 
 #define DD_LEVELS 4   // grid pitches 1e-6, 1e-4, 1e-2, 1

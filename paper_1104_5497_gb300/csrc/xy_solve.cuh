@@ -57,10 +57,14 @@ struct SMat {
     __device__ __forceinline__ void set(int i, int c, cx<R> v) const { p[(c * M + i) * BLOCK] = v; }
 };
 
-// Shared memory per thread: the augmented matrix plus two vectors (evaluation point,
-// solve output).
+// Shared memory per thread: the augmented matrix plus the evaluation point.  The solve's
+// output / residual vector (2M entries) shares the matrix's two right-hand-side columns
+// (also 2M entries, column-major and contiguous): the solve consumes a residual there
+// while it builds S, before it writes the right-hand sides, and it reads each solution
+// entry before it writes the output entry in the same place.  Seven 32-thread blocks
+// per SM fit at M = 9 instead of six.
 template <int M, class R>
-constexpr size_t xy_smem_per_thread() { return sizeof(cx<R>) * (size_t)(M * (M + 2) + 4 * M); }
+constexpr size_t xy_smem_per_thread() { return sizeof(cx<R>) * (size_t)(M * (M + 2) + 2 * M); }
 
 __device__ __forceinline__ void compiler_fence() { asm volatile("" ::: "memory"); }
 
@@ -210,6 +214,8 @@ __device__ __forceinline__ bool aug_qr_solve(const SMat<M, R, BLOCK> &A, bool tw
 //   two_rhs == false: r = -H_t (predictor: d = dz/dt), written to out1.
 //   two_rhs == true:  r1 = the residual vector in `res` (corrector: -H), written to out1;
 //                     r2 = -H_t, written to out2.
+// res and out1 may be the matrix's right-hand-side columns (see xy_smem_per_thread); the
+// residual's g rows, needed again after the factorisation, wait in out2 meanwhile.
 // two_rhs must be uniform across the warp.  Outputs are written only when wr.  Returns
 // false when the system is singular or the result is not finite.
 template <int M, class R, int BLOCK, class Out2>
@@ -252,6 +258,7 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
         // the diagonal's own contributions, added to row j below
         const cx<R> d0 = csub(rf0, cadd(cmul(Ajj, px0), cmul(Bjj, py0)));
         const cx<R> d1 = csub(htf, cadd(cmul(Ajj, px1), cmul(Bjj, py1)));
+        if (two_rhs && wr) out2.set(M + j, rg0);   // the residual's g row, for the recovery
 #pragma unroll
         for (int k = 0; k < M; k++) {
             // off-diagonal entries; J_jj = 0 makes the k == j term vanish
@@ -285,7 +292,7 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
         R iv;
         g_frame<R>(xj, yj, s, sg, ah, bh, iv);
         const cx<R> htg = minus_ht_g<R>(xj, yj, gam);
-        const cx<R> q0 = cscale(iv, two_rhs ? res.get(M + j) : htg);
+        const cx<R> q0 = cscale(iv, two_rhs ? out2.get(M + j) : htg);
         const cx<R> s0 = A.get(j, M);
         const cx<R> dx0 = cadd(cmulc(ah, q0), cmul(bh, s0));
         const cx<R> dy0 = csub(cmulc(bh, q0), cmul(ah, s0));

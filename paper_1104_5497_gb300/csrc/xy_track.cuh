@@ -145,11 +145,12 @@ struct XYProblem {
     }
 };
 
-// Shared memory per thread of a tracker on problem P: the augmented matrix and two
-// vectors (evaluation point, solve output).
+// Shared memory per thread of a tracker on problem P: the augmented matrix and the
+// evaluation point; the solve output / residual vector (NV entries) is the matrix's
+// right-hand-side columns (see xy_smem_per_thread).
 template <class P>
 constexpr size_t track_smem_per_thread() {
-    return sizeof(cx<typename P::R>) * (size_t)(P::MD * (P::MD + 2) + 2 * P::NV);
+    return sizeof(cx<typename P::R>) * (size_t)(P::MD * (P::MD + 2) + P::NV);
 }
 
 template <class P>
@@ -161,8 +162,9 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
     cx<R> *sm = reinterpret_cast<cx<R> *>(smraw);
     const int tid = threadIdx.x, lane = tid & 31;
     const SMat<MD, R, BLOCK> A{sm + tid};
-    const SVec<R, BLOCK> ZC{sm + MD * (MD + 2) * BLOCK + tid};        // evaluation point / iterate
-    const SVec<R, BLOCK> W1{sm + (MD * (MD + 2) + NV) * BLOCK + tid}; // solve output / residual
+    const SVec<R, BLOCK> ZC{sm + MD * (MD + 2) * BLOCK + tid};   // evaluation point / iterate
+    const SVec<R, BLOCK> W1{sm + MD * MD * BLOCK + tid};          // solve output / residual:
+                                                                  // the right-hand-side columns
     const int64_t gtid = (int64_t)blockIdx.x * BLOCK + tid;
     const int64_t nth = wl.state_threads;
     cx<R> *st = reinterpret_cast<cx<R> *>(wl.state);
