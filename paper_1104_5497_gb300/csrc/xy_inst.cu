@@ -61,7 +61,11 @@ cudaError_t NPHC_CAT(launch_xy_track_f64w_m, NPHC_INST_M)(const XYSys &sys, cons
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 32 * WARPS, smem);
     if (e != cudaSuccess) return e;
-    const int64_t full = (int64_t)sms * (per > 0 ? per : 1);
+    // two blocks (8 warps) per SM, each warp pulling paths until the list is drained: the
+    // FP64 pipe is already busy at 8 warps, and with more warps than paths each warp would
+    // take at most one path, whose SM is then chance (some SMs got twice the mean and the
+    // others idled half the launch)
+    const int64_t full = (int64_t)sms * (per < 2 ? (per > 0 ? per : 1) : 2);
     const int64_t need = (ep.count + WARPS - 1) / WARPS;   // the list is at most ep.count long
     const int grid = (int)(need < full ? need : full);
     k<<<grid, 32 * WARPS, smem, st>>>(sys, ctl, ep, wl);
