@@ -232,6 +232,14 @@ def run_mine(args):
     M = inst.N - 1
     system = nphc.System(inst.N, inst.sigma)
     opts = nphc.options_default(gamma=inst.gamma, precision=nphc.PREC_MIXED)
+    tuned = {"autotuned": False}
+    if args.autotune:   # launch shapes per (N, GPU), outside every timed region
+        from paper_1104_5497_gb300 import autotune
+        # a profiler run launches nothing extra: it takes the cached shapes of an earlier
+        # run, or the defaults
+        opts, rep_ = autotune.tune(system, opts, measure=not args.profile)
+        tuned = {"autotuned": True, "blocks_per_sm": rep_["blocks_per_sm"],
+                 "list_blocks_per_sm": rep_["list_blocks_per_sm"], "cached": rep_["cached"]}
     res = nphc.Result(system)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -293,7 +301,8 @@ def run_mine(args):
     traffic = profiled_traffic()
 
     # ---- plain FP64 on the same workload (the metric's comparison)
-    opts64 = nphc.options_default(gamma=inst.gamma, precision=nphc.PREC_FP64)
+    opts64 = nphc.options_default(gamma=inst.gamma, precision=nphc.PREC_FP64,
+                                  list_blocks_per_sm=opts.list_blocks_per_sm)
     res64 = nphc.Result(system)
     nphc.solve_into(system, opts64, res64)
     torch.cuda.synchronize()
@@ -336,7 +345,8 @@ def run_mine(args):
         line = {"metric": METRIC, "value": value, "unit": "paths/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f32+f64", "data": "synthetic", "config": workload_config(inst),
+                "dtype": "f32+f64", "data": "synthetic",
+                "config": dict(workload_config(inst), launch=tuned),
                 "certified": {"real": counts["real"], "nonreal": counts["nonreal"],
                               "index_hist": counts["index_hist"],
                               "equal_to_plain_fp64": (counts["real"] == c64["real"]
@@ -368,6 +378,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--cpu-paths", type=int, default=8192, help="oracle sample for cpu_baseline")
+    ap.add_argument("--autotune", action="store_true",
+                    help="autotuned launch shapes instead of the defaults")
     ap.add_argument("--ref-paths", type=int, default=2048, help="oracle sample per reference step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--profile", action="store_true",

@@ -120,6 +120,8 @@ typedef struct nphc_options {
     double eg_tol_conv;        /* two estimates agree when ||e_k - e_k-1|| <= tol (1 + ||e_k||), 1e-9 */
     double eg_h_min;           /* smallest endgame step, in sample intervals, 1/4096 */
     int eg_max_attempts;       /* endgame step attempts per path, 4000 */
+    int list_blocks_per_sm;    /* blocks (of 4 warps) per SM of the FP64 list tracker (hand-offs,
+                                  re-tracks; one path per warp); 0 = automatic (2) */
 } nphc_options;
 
 typedef struct nphc_system nphc_system;   /* opaque; owns the device copy of the couplings */

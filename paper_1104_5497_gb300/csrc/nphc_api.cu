@@ -14,6 +14,7 @@
 
 #include "nphc.h"
 #include "nphc_internal.cuh"
+#include "xy_dispatch.cuh"
 #include "nphc_kernels.cuh"
 
 namespace {
@@ -152,6 +153,7 @@ nphc_status nphc_options_default(nphc_options *o) {
     o->eg_tol_conv = 1e-9;
     o->eg_h_min = 1.0 / 4096.0;
     o->eg_max_attempts = 4000;
+    o->list_blocks_per_sm = 0;
     o->block_size = 0;
     o->blocks_per_sm = 0;
     return NPHC_OK;
@@ -346,6 +348,8 @@ nphc_status check_opt(const nphc_options *o) {
           o->eg_tol_close > 0.0 && o->eg_tol_conv > 0.0 && o->eg_h_min > 0.0 &&
           o->eg_max_attempts > 0))
         return fail(NPHC_EINVAL, "endgame options out of range");
+    if (o->blocks_per_sm < 0 || o->list_blocks_per_sm < 0 || o->block_size < 0)
+        return fail(NPHC_EINVAL, "launch options out of range");
     return NPHC_OK;
 }
 
@@ -432,7 +436,7 @@ nphc_status track_impl(const nphc_system *S, const nphc_options *o, nphc_precisi
     if (S->quad)
         NPHC_CK(launch_quad_track(S->n, quad_with_gamma(S, o), ctl, v, wl, 0, st));
     else if (!f32 && list != nullptr)   // short FP64 lists: one path per warp
-        NPHC_CK(launch_xy_track_f64_warp(S->M, xs, ctl, v, wl, st));
+        NPHC_CK(launch_xy_track_f64_warp_bps(S->M, xs, ctl, v, wl, o->list_blocks_per_sm, st));
     else if (f32)
         NPHC_CK(launch_xy_track_f32(S->M, xs, ctl, v, wl, 0, grid, st));
     else

@@ -17,11 +17,17 @@ cudaError_t launch_xy_track_f64(int M, const XYSys &sys, const XYCtl &ctl, const
 #undef C
 }
 
-cudaError_t launch_xy_track_f64_warp(int M, const XYSys &sys, const XYCtl &ctl, const EPView &ep,
-                                     const WorkList &wl, cudaStream_t st) {
-#define C(MM) case MM: return launch_xy_track_f64w_m##MM(sys, ctl, ep, wl, st);
+cudaError_t launch_xy_track_f64_warp_bps(int M, const XYSys &sys, const XYCtl &ctl,
+                                         const EPView &ep, const WorkList &wl, int blocks_per_sm,
+                                         cudaStream_t st) {
+#define C(MM) case MM: return launch_xy_track_f64w_m##MM(sys, ctl, ep, wl, blocks_per_sm, st);
     switch (M) { NPHC_FOR_EACH_M(C) default: return cudaErrorInvalidValue; }
 #undef C
+}
+
+cudaError_t launch_xy_track_f64_warp(int M, const XYSys &sys, const XYCtl &ctl, const EPView &ep,
+                                     const WorkList &wl, cudaStream_t st) {
+    return launch_xy_track_f64_warp_bps(M, sys, ctl, ep, wl, 0, st);
 }
 
 cudaError_t launch_xy_refine_certify(int M, const XYSys &sys, double tol_sol, double refine_eps,

@@ -17,7 +17,7 @@
     cudaError_t launch_xy_track_f64_m##MM(const XYSys &, const XYCtl &, const EPView &,     \
                                           const WorkList &, int, cudaStream_t);              \
     cudaError_t launch_xy_track_f64w_m##MM(const XYSys &, const XYCtl &, const EPView &,    \
-                                           const WorkList &, cudaStream_t);                 \
+                                           const WorkList &, int, cudaStream_t);            \
     cudaError_t launch_xy_refine_certify_m##MM(const XYSys &, double, double, int,          \
                                                const EPView &, int64_t, const WorkList &,   \
                                                int, cudaStream_t);                          \
@@ -41,3 +41,9 @@ NPHC_FOR_EACH_M(NPHC_DECL)
                                          const WorkList &, int32_t *, int32_t *, cudaStream_t);
 NPHC_FOR_EACH_QN(NPHC_QDECL)
 #undef NPHC_QDECL
+
+// The FP64 list tracker with a chosen number of blocks per SM (0: automatic); the
+// launcher of nphc_internal.cuh is this one with 0.
+cudaError_t launch_xy_track_f64_warp_bps(int M, const XYSys &sys, const XYCtl &ctl,
+                                         const EPView &ep, const WorkList &wl, int blocks_per_sm,
+                                         cudaStream_t st);

@@ -42,10 +42,11 @@ cudaError_t NPHC_CAT(launch_xy_cauchy_m, NPHC_INST_M)(const XYSys &sys, const EG
 #if NPHC_INST_KIND == 1
 #include "xy_track_warp.cuh"
 
-// one path per warp (short FP64 lists), 4 warps per block
+// one path per warp (short FP64 lists), 4 warps per block, blocks_per_sm blocks per SM
+// (0: two)
 cudaError_t NPHC_CAT(launch_xy_track_f64w_m, NPHC_INST_M)(const XYSys &sys, const XYCtl &ctl,
                                                           const EPView &ep, const WorkList &wl,
-                                                          cudaStream_t st) {
+                                                          int blocks_per_sm, cudaStream_t st) {
     constexpr int M = NPHC_INST_M, WARPS = 4;
     if (ep.count <= 0) return cudaSuccess;
     const size_t smem = warp_track_smem_per_warp<M>() * WARPS;
@@ -61,11 +62,12 @@ cudaError_t NPHC_CAT(launch_xy_track_f64w_m, NPHC_INST_M)(const XYSys &sys, cons
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, 32 * WARPS, smem);
     if (e != cudaSuccess) return e;
-    // two blocks (8 warps) per SM, each warp pulling paths until the list is drained: the
-    // FP64 pipe is already busy at 8 warps, and with more warps than paths each warp would
-    // take at most one path, whose SM is then chance (some SMs got twice the mean and the
-    // others idled half the launch)
-    const int64_t full = (int64_t)sms * (per < 2 ? (per > 0 ? per : 1) : 2);
+    // by default two blocks (8 warps) per SM, each warp pulling paths until the list is
+    // drained: the FP64 pipe is already busy at 8 warps, and with more warps than paths
+    // each warp would take at most one path, whose SM is then chance (some SMs got twice
+    // the mean and the others idled half the launch)
+    const int want = blocks_per_sm > 0 ? blocks_per_sm : 2;
+    const int64_t full = (int64_t)sms * (per < want ? (per > 0 ? per : 1) : want);
     const int64_t need = (ep.count + WARPS - 1) / WARPS;   // the list is at most ep.count long
     const int grid = (int)(need < full ? need : full);
     k<<<grid, 32 * WARPS, smem, st>>>(sys, ctl, ep, wl);

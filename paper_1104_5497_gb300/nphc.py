@@ -57,7 +57,8 @@ class nphc_options(ctypes.Structure):
                 ("eg_ratio", ctypes.c_double), ("eg_radii", ctypes.c_int),
                 ("eg_samples", ctypes.c_int), ("eg_max_cycle", ctypes.c_int),
                 ("eg_tol_close", ctypes.c_double), ("eg_tol_conv", ctypes.c_double),
-                ("eg_h_min", ctypes.c_double), ("eg_max_attempts", ctypes.c_int)]
+                ("eg_h_min", ctypes.c_double), ("eg_max_attempts", ctypes.c_int),
+                ("list_blocks_per_sm", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
