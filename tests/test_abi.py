@@ -124,3 +124,20 @@ def test_endgame_argument_checks(N_):
     d = N_.options_default()
     assert (d.endgame, d.eg_r0, d.eg_ratio, d.eg_radii, d.eg_samples, d.eg_max_cycle) == \
         (0, 1 / 16, 0.25, 8, 16, 8)
+
+
+def test_launch_options_are_checked(N_):
+    """Negative launch shapes are rejected before any CUDA call."""
+    import ctypes
+    s = N_.System(5, 1.0)
+    ep = N_.nphc_endpoints()
+    ep.count = 4
+    for f in ("path", "z_re", "z_im", "t", "h", "status", "steps", "solves", "newton"):
+        setattr(ep, f, 16)
+    L = N_.lib()
+    for kw in (dict(blocks_per_sm=-1), dict(list_blocks_per_sm=-2), dict(block_size=-1)):
+        o = N_.options_default(**kw)
+        rc = L.nphc_track(s.handle, ctypes.byref(o), N_.PREC_MIXED, ctypes.byref(ep), None, None, 0,
+                          ctypes.c_void_p(16), 1 << 40, None)
+        assert rc == 1 and b"launch options" in L.nphc_last_error(), kw
+    assert N_.options_default().list_blocks_per_sm == 0
