@@ -112,3 +112,33 @@ def test_ring_singular_endpoints_are_solutions(N):
     m = N - 1
     zr = r["z"][ok]
     assert np.abs(zr[:, :m] ** 2 + zr[:, m:] ** 2 - 1).max() < 1e-12
+
+
+def test_trapezoid_estimate_matches_closed_form():
+    """K = 2 samples per turn at the single radius r = 1/2 (no other branch point inside:
+    the discriminant's other zero and the poles lie beyond |1 - t| = 1.5).  For the double
+    root (z_1 - a)^2 the turns close after two turns and visit both roots at t = 1 - r
+    (theta = 0, 2 pi) and at t = 1 + r (theta = pi, 3 pi); by Vieta the two roots of
+    (gamma (1-t) + t) z^2 - 2 t a z + ... sum to 2 f(t), f(t) = t a / (gamma (1-t) + t), so
+    the estimate of z_1 is (f(1 - r) + f(1 + r)) / 2.  z_2 = +-sqrt(g(t)), g(t) = (gamma (1-t)
+    + t b) / (gamma (1-t) + t), is analytic inside the circle: its estimate is the mean of
+    the branch at 1 - r and at 1 + r, continued along real t."""
+    a, b, r = 0.3 + 0.2j, 2.0, 0.5
+    f = lambda t: t * a / (GAMMA * (1 - t) + t)
+    g = lambda t: (GAMMA * (1 - t) + t * b) / (GAMMA * (1 - t) + t)
+    T = S.double_root(a, b)
+    res = run(T, r0=r, n_radii=1, samples=2)
+    assert np.all(res["status"] == O.EG_NOT_CONVERGED) and np.all(res["cycle"] == 2)
+    assert np.abs(res["z"][:, 0] - (f(1 - r) + f(1 + r)) / 2).max() < 1e-11
+    ts = np.linspace(1 - r, 1 + r, 20001)
+    for p in range(4):
+        # the branch of z_2 along real t through t = 1, from the path's sign at t = 1 - r
+        w = np.sqrt(g(ts))
+        for k in range(1, len(ts)):
+            if abs(w[k] - w[k - 1]) > abs(w[k] + w[k - 1]):
+                w[k:] = -w[k:]
+        z_end = O.track(T, GAMMA, path0=p, npaths=1)["z"][0, 1]   # the path's z_2 at t = 1
+        mid = len(ts) // 2                                          # ts[mid] = 1
+        sgn = np.sign((w[mid] * np.conj(z_end)).real)
+        expect = sgn * (w[0] + w[-1]) / 2
+        assert abs(res["z"][p, 1] - expect) < 1e-10, (p, res["z"][p, 1], expect)
