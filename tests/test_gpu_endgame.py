@@ -119,3 +119,16 @@ def test_pipeline_option_on_ring_n8():
     assert c1["eg_converged"] == conv.sum()
     assert c1["eg_multiple"] == (conv & (o["cycle"] >= 2)).sum()
     assert c1["eg_at_infinity"] == np.isin(o["status"], [O.EG_AT_INFINITY, O.EG_DIVERGED]).sum()
+
+
+def test_two_sample_trapezoid_value_on_gpu():
+    """The closed-form trapezoid value of the double root (see the oracle's pin): K = 2
+    samples per turn at the single radius 1/2; the estimate of z_1 is
+    (f(1 - r) + f(1 + r)) / 2 with f(t) = t a / (gamma (1 - t) + t)."""
+    N_ = nphc()
+    a, b, r = 0.3 + 0.2j, 2.0, 0.5
+    f = lambda t: t * a / (GAMMA * (1 - t) + t)
+    g = gpu_endgame(N_, quad(N_, S.double_root(a, b)), np.arange(4), eg_r0=r, eg_radii=1,
+                    eg_samples=2)
+    assert np.all(g["status"] == N_.EG_NOT_CONVERGED) and np.all(g["cycle"] == 2)
+    assert np.abs(g["z"][:, 0] - (f(1 - r) + f(1 + r)) / 2).max() < 1e-11
