@@ -1,0 +1,84 @@
+"""The number of finite solutions, pinned by exact algebra: for rings with integer
+couplings the stationary equations (section "A First Application", theta_N = 0) are
+rebuilt here from their definition over the rationals, and the dimension of the
+quotient ring by their Groebner basis (grevlex) counts the complex solutions with
+multiplicity.  The oracle must certify exactly that many (real + non-real), none
+singular: every solution is then simple and found, and the count of non-real solutions,
+which the paper does not print, is fixed independently of any homotopy."""
+import numpy as np
+import pytest
+
+import oracle as O
+
+sp = pytest.importorskip("sympy")
+
+
+def xy_polys(N, J):
+    m = N - 1
+    c = sp.symbols(f"c0:{m}")
+    s = sp.symbols(f"s0:{m}")
+    eqs = []
+    for k in range(m):
+        f = 0
+        for j in range(N):
+            if j == k:
+                continue
+            cj = 1 if j == N - 1 else c[j]     # theta_N = 0: c_N = 1, s_N = 0
+            sj = 0 if j == N - 1 else s[j]
+            f += sp.Integer(J[k][j]) * (s[k] * cj - sj * c[k])
+        eqs.append(sp.expand(f))
+    eqs += [c[k] ** 2 + s[k] ** 2 - 1 for k in range(m)]
+    return eqs, list(c) + list(s)
+
+
+def quotient_dim(eqs, vs):
+    G = sp.groebner(eqs, *vs, order="grevlex")
+    assert G.is_zero_dimensional
+    lead = [sp.Poly(g, *vs).monoms(order="grevlex")[0] for g in G.exprs]
+    n = len(vs)
+
+    def standard(mono):
+        return not any(all(mono[i] >= l[i] for i in range(n)) for l in lead)
+
+    seen, todo = set(), [(0,) * n]
+    while todo:
+        mono = todo.pop()
+        if mono in seen or not standard(mono):
+            continue
+        seen.add(mono)
+        todo += [mono[:i] + (mono[i] + 1,) + mono[i + 1:] for i in range(n)]
+    return len(seen)
+
+
+def integer_couplings(N, seed):
+    rng = np.random.default_rng(seed)
+    J = np.zeros((N, N), dtype=int)
+    for i in range(N):
+        for j in range(i + 1, N):
+            J[i, j] = J[j, i] = int(rng.integers(1, 9))
+    return J
+
+
+CASES = [(3, np.ones((3, 3), int) - np.eye(3, dtype=int)), (3, np.array([[0, 2, 3], [2, 0, 5], [3, 5, 0]]))]
+CASES += [(4, integer_couplings(4, seed)) for seed in (0, 1, 2)]
+
+
+def check(N, J):
+    d = quotient_dim(*xy_polys(N, J.tolist()))
+    out = O.solve_system(O.xy_terms(N, J.astype(float)), np.exp(0.5j))
+    cls = out["cls"]
+    assert (cls == O.C_SINGULAR).sum() == 0 and (cls == O.C_UNDECIDED).sum() == 0
+    assert ((cls == O.C_REAL) | (cls == O.C_NONREAL)).sum() == d, (N, d, np.bincount(cls))
+    return d
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_certified_count_equals_groebner_count(case):
+    N, J = CASES[case]
+    check(N, J)
+
+
+@pytest.mark.slow
+def test_certified_count_equals_groebner_count_n5():
+    """N = 5 (8 unknowns, 256 paths; about 90 s of exact algebra)."""
+    check(5, integer_couplings(5, 0))
