@@ -1,4 +1,4 @@
-"""The number of finite solutions, pinned by exact algebra: for rings with integer
+"""The number of finite solutions, pinned by exact algebra: for rings with rational
 couplings the stationary equations (section "A First Application", theta_N = 0) are
 rebuilt here from their definition over the rationals, and the dimension of the
 quotient ring by their Groebner basis (grevlex) counts the complex solutions with
@@ -25,7 +25,7 @@ def xy_polys(N, J):
                 continue
             cj = 1 if j == N - 1 else c[j]     # theta_N = 0: c_N = 1, s_N = 0
             sj = 0 if j == N - 1 else s[j]
-            f += sp.Integer(J[k][j]) * (s[k] * cj - sj * c[k])
+            f += sp.sympify(J[k][j]) * (s[k] * cj - sj * c[k])   # exact: int or Rational
         eqs.append(sp.expand(f))
     eqs += [c[k] ** 2 + s[k] ** 2 - 1 for k in range(m)]
     return eqs, list(c) + list(s)
@@ -78,7 +78,26 @@ def test_certified_count_equals_groebner_count(case):
     check(N, J)
 
 
+def ring_couplings(N):
+    """J_ij = d_ij^-sigma at sigma = 1 (exact rationals 1/d)."""
+    return [[0 if i == j else sp.Rational(1, min(abs(i - j), N - abs(i - j))) for j in range(N)]
+            for i in range(N)]
+
+
+def test_uniform_ring_n4_has_a_positive_dimensional_solution_set():
+    """The power-law ring with N = 4 (sigma = 1): the ideal is not zero-dimensional, i.e.
+    pinning theta_N leaves a continuum of solutions; the reading that such endpoints are
+    singular, counted but never certified, rests on this."""
+    eqs, vs = xy_polys(4, ring_couplings(4))
+    assert not sp.groebner(eqs, *vs, order="grevlex").is_zero_dimensional
+
+
 @pytest.mark.slow
-def test_certified_count_equals_groebner_count_n5():
-    """N = 5 (8 unknowns, 256 paths; about 90 s of exact algebra)."""
-    check(5, integer_couplings(5, 0))
+def test_uniform_ring_n5_count_equals_groebner_count():
+    """The power-law ring with N = 5 at sigma = 1 (8 unknowns, 256 paths; ~30 s of exact
+    algebra): the oracle certifies as many solutions as the quotient ring's dimension."""
+    d = quotient_dim(*xy_polys(5, ring_couplings(5)))
+    out = O.solve_xy(5, 1.0, np.exp(0.5j))
+    cls = out["cls"]
+    assert (cls == O.C_SINGULAR).sum() == 0 and (cls == O.C_UNDECIDED).sum() == 0
+    assert ((cls == O.C_REAL) | (cls == O.C_NONREAL)).sum() == d
