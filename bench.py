@@ -162,9 +162,10 @@ def profiled_traffic():
 
 
 # --------------------------------------------------------------- the oracle --
-def oracle_sample_rate(inst, n_paths: int, seed: int = 0):
+def oracle_sample_rate(inst, n_paths: int, seed: int = 0, collect: bool = False):
     """Paths/s of the CPU oracle (track, refine, certify, dedup, classify) on a random
-    sample of n_paths paths of the workload, in contiguous chunks of 64."""
+    sample of n_paths paths of the workload, in contiguous chunks of 64.  collect: also
+    return the sample's path indices, classes and endpoints (a fifth value)."""
     import oracle as O
     J = O.couplings(inst.N, inst.sigma)
     T = O.xy_terms(inst.N, J)
@@ -173,14 +174,41 @@ def oracle_sample_rate(inst, n_paths: int, seed: int = 0):
     chunks = max(1, n_paths // 64)
     starts = rng.choice(P // 64, size=chunks, replace=False) * 64
     threads = O.default_threads()
+    kept = []
     t0 = time.perf_counter()
     for s in starts:
         out = O.solve_system(T, inst.gamma, path0=int(s), npaths=64, nthreads=threads)
         for i in np.nonzero(out["cls"] == O.C_REAL)[0]:
             z = out["z"][i]
             O.xy_classify(inst.N, J, z[:inst.N - 1].real, z[inst.N - 1:].real)
+        if collect:
+            kept.append((out["path"], out["cls"], out["z"]))
     dt = time.perf_counter() - t0
-    return chunks * 64 / dt, chunks * 64, threads, dt
+    if not collect:
+        return chunks * 64 / dt, chunks * 64, threads, dt
+    sample = {"path": np.concatenate([k[0] for k in kept]), "cls": np.concatenate([k[1] for k in kept]),
+              "z": np.concatenate([k[2] for k in kept])}
+    return chunks * 64 / dt, chunks * 64, threads, dt, sample
+
+
+def sample_parity(sample, gpu_cls, gpu_z) -> dict:
+    """The GPU solve against the oracle on the oracle's sample of paths: paths certified
+    by one and not the other, paths real in one and not the other, and the largest
+    endpoint difference (relative to 1 + |z|) over the paths both certify.  The oracle
+    deduplicates within each 64-path chunk only, so a GPU duplicate counts as certified.
+    Class numbers are shared (NPHC_END_* = the oracle's)."""
+    p = np.asarray(sample["path"], dtype=np.int64)
+    oc, gc = np.asarray(sample["cls"]), np.asarray(gpu_cls)[p]
+    o_cert = np.isin(oc, [2, 3, 4, 5])
+    g_cert = np.isin(gc, [2, 3, 4, 5])
+    both = o_cert & g_cert
+    err = 0.0
+    if both.any():
+        zo, zg = np.asarray(sample["z"])[both], np.asarray(gpu_z)[p[both]]
+        err = float((np.abs(zo - zg).max(axis=1) / (1 + np.abs(zo).max(axis=1))).max())
+    return {"paths": int(len(p)), "certified": int(both.sum()),
+            "class_mismatches": int((o_cert != g_cert).sum()),
+            "real_mismatches": int(((oc == 2) != (gc == 2)).sum()), "max_rel_err": err}
 
 
 def run_reference(args):
@@ -335,9 +363,14 @@ def run_mine(args):
     e2e_s = max_over_ranks(float(np.mean(e2e_t)), world)
 
     # ---- CPU oracle on a sample of the same workload (rank 0, N = 1 only)
-    cpu = None
+    cpu, parity = None, None
     if rank == 0 and world == 1 and not args.no_cpu:
-        r, n, cores, dt = oracle_sample_rate(inst, args.cpu_paths)
+        r, n, cores, dt, sample = oracle_sample_rate(inst, args.cpu_paths, collect=True)
+        try:   # the timed solve's endpoints against the oracle on the same sample of paths
+            ep_all = res.endpoints()
+            parity = sample_parity(sample, ep_all["cls"], ep_all["z"])
+        except Exception as exc:   # a report, never a reason to lose the bench line
+            parity = {"error": repr(exc)}
         cpu = {"value": r, "unit": "paths/s", "cores": cores, "kind": "oracle",
                "sample": f"{n} of {P} paths (random 64-path chunks), whole method, {dt:.1f} s"}
 
@@ -363,6 +396,7 @@ def run_mine(args):
                              "kernel_ms": k_ms, "flops_per_launch": flops,
                              "traffic": traffic},
                 "cpu_baseline": cpu,
+                "oracle_parity": parity,
                 "gpu_launches": launches,
                 "clocks": clk.summary(),
                 "counts": {k: v for k, v in counts.items() if k != "index_hist"}}

@@ -45,3 +45,33 @@ def test_clock_summary_without_samples(tmp_path):
 def test_replica_value_is_the_whole_job():
     assert bench.replica_value(262144, 1, 0.2) == 262144 / 0.2
     assert bench.replica_value(262144, 4, 0.2) == 4 * 262144 / 0.2
+
+
+def test_sample_parity_against_the_oracle_sample():
+    """The oracle's own sample read back as the 'GPU' result agrees exactly; planted
+    differences (a lost certification, a real/non-real swap, a moved endpoint) are
+    counted."""
+    import numpy as np
+    from paper_1104_5497_gb300 import inputs
+    inst = inputs.workload_n4()
+    P = 4 ** (inst.N - 1)
+    r, n, cores, dt, sample = bench.oracle_sample_rate(inst, 64, collect=True)
+    assert n == 64 and len(sample["path"]) == 64 and sample["z"].shape == (64, 2 * (inst.N - 1))
+    cls = np.zeros(P, np.int32)
+    z = np.zeros((P, 2 * (inst.N - 1)), complex)
+    cls[sample["path"]] = sample["cls"]
+    z[sample["path"]] = sample["z"]
+    par = bench.sample_parity(sample, cls, z)
+    assert par["class_mismatches"] == 0 and par["real_mismatches"] == 0 and par["max_rel_err"] == 0
+    assert par["certified"] == int(np.isin(sample["cls"], [2, 3, 4, 5]).sum()) > 0
+    cert = sample["path"][np.isin(sample["cls"], [2, 3])]
+    real = sample["path"][sample["cls"] == 2]
+    cls2, z2 = cls.copy(), z.copy()
+    cls2[cert[0]] = 1                       # singular on the "GPU"
+    z2[cert[-1], 0] += 1e-6
+    if len(real):
+        cls2[real[-1]] = 3                  # real -> non-real
+    par = bench.sample_parity(sample, cls2, z2)
+    assert par["class_mismatches"] == 1
+    assert par["real_mismatches"] == (1 if len(real) else 0) + int(cert[0] in real)
+    assert 1e-7 < par["max_rel_err"] < 1e-6
