@@ -56,3 +56,6 @@ def test_parity_n10_workload(prec):
         assert abs(ref["sps"][k]["energy"] - en) < 1e-10
     hist = np.bincount([s["index"] for s in ref["sps"]], minlength=inst.N)
     assert counts["index_hist"][:inst.N] == hist.tolist()
+    # and the histogram obeys Morse theory on the torus T^(N-1) (test_oracle_morse.py)
+    from test_oracle_morse import check_morse
+    check_morse(np.array(counts["index_hist"][:inst.N]), inst.N)
