@@ -117,3 +117,14 @@ def test_compensated_evaluation_is_correctly_rounded_where_plain_is_not():
         worst_plain = max(worst_plain, (np.abs(plain - ex) / ref).max())
     assert worst_acc < 4e-16
     assert worst_plain > 1e3 * worst_acc
+
+
+def test_step_budget_of_one_stops_every_path():
+    """A failure made on the host: a step budget of 1 ends every path with the budget
+    status after its first attempt (no path reaches t = 1 in one step from h0 = 0.01)."""
+    import numpy as np
+    import oracle as O
+    T = O.xy_terms(4, O.couplings(4, 1.5))
+    tr = O.track(T, np.exp(0.5j), opts=O.default_track_opts(max_steps=1))
+    assert np.all(tr["status"] == O.STEP_BUDGET)
+    assert np.all(tr["steps"] <= 1)
