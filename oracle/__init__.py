@@ -54,7 +54,8 @@ class TrackOpts(ctypes.Structure):
 
 class CertOpts(ctypes.Structure):
     _fields_ = [("tol_sol", ctypes.c_double), ("refine_eps", ctypes.c_double),
-                ("refine_iters", ctypes.c_int), ("alpha0", ctypes.c_double)]
+                ("refine_iters", ctypes.c_int), ("alpha0", ctypes.c_double),
+                ("kappa_sing", ctypes.c_double)]
 
 
 class EgOpts(ctypes.Structure):
@@ -82,16 +83,18 @@ def default_eg_opts(**kw) -> EgOpts:
 
 
 def default_track_opts(**kw) -> TrackOpts:
-    """Step control of the oracle tracker (the paper gives none; see the design notes)."""
-    o = dict(h0=0.01, h_max=0.05, h_min=1e-14, eps_corr=1e-9, trust=0.1, r_div=1e4,
+    """Step control of the oracle tracker (the paper gives none; see the design notes).
+    A path goes to infinity when ||z||_inf exceeds r_div = 1e8 before t = 1."""
+    o = dict(h0=0.01, h_max=0.05, h_min=1e-14, eps_corr=1e-9, trust=0.1, r_div=1e8,
              max_newton=3, max_steps=5000, grow_after=3)
     o.update(kw)
     return TrackOpts(**o)
 
 
 def default_cert_opts(**kw) -> CertOpts:
-    """Delta_sol = 1e-10 (the paper's solution tolerance), alpha_0 from Smale's theorem."""
-    o = dict(tol_sol=1e-10, refine_eps=1e-14, refine_iters=8, alpha0=ALPHA_CERT)
+    """Delta_sol = 1e-10 (the paper's solution tolerance), alpha_0 from Smale's theorem,
+    singular above a Frobenius condition number of 1e12 max(1, ||z||_inf^2)."""
+    o = dict(tol_sol=1e-10, refine_eps=1e-14, refine_iters=8, alpha0=ALPHA_CERT, kappa_sing=1e12)
     o.update(kw)
     return CertOpts(**o)
 

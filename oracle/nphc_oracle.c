@@ -862,12 +862,6 @@ double oracle_d2_norm(int n, int nterms, const int *eq, const int *va, const int
 }
 
 /* beta = ||DP(z)^-1 P(z)||_2 and ||DP(z)^-1||_F at z.  Returns 1 if DP(z) is singular. */
-/* KAPPA_SING: an endpoint whose Jacobian has Frobenius condition number
- * ||DP||_F ||DP^-1||_F above this is singular.  At a point of a positive-dimensional
- * solution set P vanishes to double-double precision, so beta is tiny, while rounding
- * leaves the computed DP^-1 merely huge: the soft FP64 alpha test alone can pass there. */
-#define KAPPA_SING 1e12
-
 static int beta_and_inv_norm(const qsys *S, const cplx *z, double *beta, double *invF,
                              double *cond, work *w) {
     int n = S->n;
@@ -895,7 +889,21 @@ typedef struct {
     double refine_eps;    /* Newton refinement stops when ||dz|| <= eps (1 + ||z||) */
     int refine_iters;     /* at most this many refinement steps */
     double alpha0;        /* alpha threshold: half of (13 - 3 sqrt 17) / 4 (FP64 soft test) */
+    double kappa_sing;    /* singular when ||DP||_F ||DP^-1||_F > kappa_sing max(1, ||z||_inf^2) */
 } oracle_cert_opts;
+
+/* The singularity test.  At a point of a positive-dimensional solution set P vanishes
+ * to double-double precision, so beta is tiny, while rounding leaves the computed DP^-1
+ * merely huge: the soft FP64 alpha test alone can pass there, so an endpoint whose
+ * Jacobian has a Frobenius condition number above kappa_sing is singular.  The bound
+ * grows with ||z||_inf^2, as the solution tolerance does: every equation is quadratic,
+ * the Jacobian's entries grow like ||z|| and a finite solution near the solution set at
+ * infinity has a smallest singular value that shrinks like 1 / ||z||, so an isolated
+ * solution of norm 1e6 has a condition number ~1e12 without being singular. */
+static int cond_ok(double cond, int n, const cplx *z, double kappa_sing) {
+    double zi = norminf(n, z);
+    return cond <= kappa_sing * (zi > 1.0 ? zi * zi : 1.0);
+}
 
 /* Refine and certify one endpoint.  Outputs: class, alpha, beta, residual, alpha at
  * Re z (the real test).  z is refined in place. */
@@ -926,7 +934,8 @@ static int refine_certify_one(const qsys *S, double d2, const oracle_cert_opts *
      * every equation is quadratic, so at ||z|| >> 1 its terms are ~||z||^2 and an absolute
      * 1e-10 would sit below the rounding of their sum */
     double zi = norminf(n, z), scale = zi > 1.0 ? zi * zi : 1.0;
-    if (!(res <= o->tol_sol * scale) || !(alpha < o->alpha0) || !(cond <= KAPPA_SING)) return OC_SINGULAR;
+    if (!(res <= o->tol_sol * scale) || !(alpha < o->alpha0) || !cond_ok(cond, n, z, o->kappa_sing))
+        return OC_SINGULAR;
     double im = 0;
     for (int i = 0; i < n; i++) im += cimag(z[i]) * cimag(z[i]);
     im = sqrt(im);
@@ -941,7 +950,7 @@ static int refine_certify_one(const qsys *S, double d2, const oracle_cert_opts *
         if (!beta_and_inv_norm(S, x, &beta_r, &invF_r, &cond_r, w)) {
             double ar = beta_r * invF_r * d2;
             *alpha_re_out = ar;
-            if (ar < o->alpha0 && cond_r <= KAPPA_SING) return OC_REAL;
+            if (ar < o->alpha0 && cond_ok(cond_r, n, x, o->kappa_sing)) return OC_REAL;
         }
     }
     /* non-real test: z and conj(z) have distinct associated solutions when

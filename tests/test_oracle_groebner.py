@@ -101,3 +101,43 @@ def test_uniform_ring_n5_count_equals_groebner_count():
     cls = out["cls"]
     assert (cls == O.C_SINGULAR).sum() == 0 and (cls == O.C_UNDECIDED).sum() == 0
     assert ((cls == O.C_REAL) | (cls == O.C_NONREAL)).sum() == d
+
+
+# Rings with one coupling shrunk to 2^-e (exactly representable, so the oracle sees the
+# same rational system): at J_12 = 0 a pair of solutions sits at infinity, and just
+# beside it the pair is finite with a norm ~1 / J_12 (1.6e4 .. 8.4e6 here).  These pin
+# the reading of what "goes to infinity" means: every isolated solution is found, however
+# large, when a path counts as diverging only once ||z||_inf exceeds 1e8, and the
+# singularity test scales with ||z||_inf^2 (an isolated solution of norm 1e6 has a
+# Jacobian condition number ~1e12).
+def far_case(N, seed, i, j, e):
+    if seed is None:
+        Ji = np.ones((N, N), int) - np.eye(N, dtype=int)
+    else:
+        Ji = integer_couplings(N, seed)
+    Jr = [[sp.Integer(int(v)) for v in row] for row in Ji]
+    Jr[i][j] = Jr[j][i] = sp.Rational(1, 2 ** e)
+    J = Ji.astype(float)
+    J[i, j] = J[j, i] = 2.0 ** -e
+    return Jr, J
+
+
+FAR_CASES = [(3, None, 0, 1, 15), (3, None, 0, 1, 24), (4, 0, 0, 1, 16), (4, 1, 0, 1, 16),
+             (4, 2, 1, 2, 16)]
+
+
+@pytest.mark.parametrize("case", FAR_CASES)
+def test_far_solutions_certified_count_equals_groebner_count(case):
+    N = case[0]
+    Jr, J = far_case(*case)
+    d = quotient_dim(*xy_polys(N, Jr))
+    T = O.xy_terms(N, J)
+    out = O.solve_system(T, np.exp(0.5j))
+    cls = out["cls"]
+    cert = (cls == O.C_REAL) | (cls == O.C_NONREAL)
+    assert (cls == O.C_SINGULAR).sum() == 0 and (cls == O.C_UNDECIDED).sum() == 0
+    assert cert.sum() == d, (d, np.bincount(cls))
+    assert np.abs(out["z"][cert]).max() > 1e4   # the case reaches beyond the old radius
+    # the reading this replaces (a radius of 1e4) misses the far pair
+    short = O.solve_system(T, np.exp(0.5j), track_opts=O.default_track_opts(r_div=1e4))
+    assert ((short["cls"] == O.C_REAL) | (short["cls"] == O.C_NONREAL)).sum() < d

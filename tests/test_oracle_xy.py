@@ -241,3 +241,29 @@ def test_planted_mistake_is_caught(plant):
     th_b = _brute_n5()
     same = len(th_o) == len(th_b) and all(contains(th_o, t, 1e-8) for t in th_b)
     assert not same
+
+
+def test_disordered_rings_share_one_finite_count():
+    """The disordered N = 6 rings of the 64-ring batch workload: J_ij = d_ij^-sigma
+    (1 + 0.1 g_ij) with random sigma and g are generic, and the number of isolated finite
+    solutions of a square system is the same for every generic choice of its
+    coefficients, so every ring certifies the same number (252, none singular), and two
+    gammas give the same set on the ring with the largest solutions (norm 1.3e5).  A
+    radius of 1e4 for paths to infinity certified 244 .. 252 on these rings."""
+    rings = [r for r in I.disordered_batch(64, seed=3) if r.N == 6]
+    assert len(rings) >= 8
+    counts = set()
+    for r in rings:
+        out = O.solve_xy(r.N, r.sigma, r.gamma, g=r.g, eps=r.eps)
+        assert (out["cls"] == O.C_SINGULAR).sum() == 0
+        counts.add(int(certified(out).sum()))
+    assert counts == {252}
+    far = I.disordered_batch(64, seed=3)[24]
+    zs = []
+    for gam in (far.gamma, np.exp(2.1j)):
+        out = O.solve_xy(far.N, far.sigma, gam, g=far.g, eps=far.eps)
+        zs.append(out["z"][certified(out)])
+    assert np.abs(zs[0]).max() > 1e5
+    assert len(zs[0]) == len(zs[1])
+    for z in zs[0]:
+        assert np.linalg.norm(zs[1] - z, axis=1).min() < 1e-9 * (1 + np.linalg.norm(z))
