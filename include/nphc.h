@@ -96,7 +96,8 @@ typedef struct nphc_options {
     double trust;              /* FP64: reject when the first correction exceeds trust (1 + ||z||), 0.1 */
     double trust_fp32;         /* FP32: the same bound on the prediction error, 2e-3 (no wider
                                   than what the FP64 corrector's tolerance implies) */
-    double r_div;              /* divergence radius on ||z||_inf (both precisions), 1e4 */
+    double r_div;              /* divergence radius: a path whose ||z||_inf exceeds it before
+                                  t = 1 goes to infinity (both precisions), 1e8 */
     int max_newton_fp32;       /* corrector iterations per FP32 step, 3 */
     int max_newton_fp64;       /* corrector iterations per FP64 step, 3 */
     int max_steps;             /* step attempts per path, 5000 */
@@ -122,6 +123,11 @@ typedef struct nphc_options {
     int eg_max_attempts;       /* endgame step attempts per path, 4000 */
     int list_blocks_per_sm;    /* blocks (of 4 warps) per SM of the FP64 list tracker (hand-offs,
                                   re-tracks; one path per warp); 0 = automatic (2) */
+    double kappa_sing;         /* an endpoint is singular (never certified) when its Jacobian's
+                                  Frobenius condition number ||DP||_F ||DP^-1||_F exceeds
+                                  kappa_sing max(1, ||z||_inf^2), 1e12 */
+    double kappa_fp32;         /* FP32 pass: a path whose condition estimate exceeds this is
+                                  handed to FP64 (see nphc_track); 0 = no such test, 0 */
 } nphc_options;
 
 typedef struct nphc_system nphc_system;   /* opaque; owns the device copy of the couplings */

@@ -134,7 +134,7 @@ nphc_status nphc_options_default(nphc_options *o) {
     o->eps_fp64 = 1e-9;
     o->trust = 0.1;
     o->trust_fp32 = 2e-3;
-    o->r_div = 1e4;
+    o->r_div = 1e8;
     o->max_newton_fp32 = 3;
     o->max_newton_fp64 = 3;
     o->max_steps = 5000;
@@ -156,6 +156,8 @@ nphc_status nphc_options_default(nphc_options *o) {
     o->list_blocks_per_sm = 0;
     o->block_size = 0;
     o->blocks_per_sm = 0;
+    o->kappa_sing = 1e12;
+    o->kappa_fp32 = 0.0;
     return NPHC_OK;
 }
 
@@ -222,6 +224,7 @@ nphc_status nphc_system_create_xy(int N, double sigma, const double *J, nphc_sys
             if (i < S->M && j < S->M && i != j) d2 += Jv[i * N + j] * Jv[i * N + j];
         }
     S->xs.d2norm = std::sqrt(d2);
+    S->xs.kappa_sing = 1e12;
     *out = S;
     return NPHC_OK;
 }
@@ -319,6 +322,7 @@ nphc_status nphc_system_create_quadratic(int n, int nterms, const int32_t *eq, c
     S->qs.gre = 1.0;
     S->qs.gim = 0.0;
     S->qs.d2norm = std::sqrt(d2);
+    S->qs.kappa_sing = 1e12;
     *out = S;
     return NPHC_OK;
 }
@@ -341,7 +345,7 @@ nphc_status check_opt(const nphc_options *o) {
     if (!(o->h0 > 0 && o->h_max >= o->h0 && o->h_min > 0 && o->eps_fp32 > 0 && o->eps_fp64 > 0 &&
           o->trust > 0 && o->trust_fp32 > 0 && o->r_div > 0 && o->max_newton_fp32 > 0 &&
           o->max_newton_fp64 > 0 && o->max_steps > 0 && o->max_steps_fp32 > 0 && o->crawl_steps_fp32 >= 0 && o->grow_after > 0 &&
-          o->refine_iters >= 0))
+          o->refine_iters >= 0 && o->kappa_sing > 0 && o->kappa_fp32 >= 0))
         return fail(NPHC_EINVAL, "options out of range");
     if (!(o->eg_r0 > 0.0 && o->eg_r0 < 1.0 && o->eg_ratio > 0.0 && o->eg_ratio < 1.0 &&
           o->eg_radii >= 1 && o->eg_samples >= 2 && o->eg_samples <= 4096 && o->eg_max_cycle >= 1 &&
@@ -353,10 +357,12 @@ nphc_status check_opt(const nphc_options *o) {
     return NPHC_OK;
 }
 
+// The system with the run's gamma and singularity bound.
 QSys quad_with_gamma(const nphc_system *S, const nphc_options *o) {
     QSys q = S->qs;
     q.gre = o->gamma_re;
     q.gim = o->gamma_im;
+    q.kappa_sing = o->kappa_sing;
     return q;
 }
 
@@ -364,6 +370,7 @@ XYSys sys_with_gamma(const nphc_system *S, const nphc_options *o) {
     XYSys x = S->xs;
     x.gre = o->gamma_re;
     x.gim = o->gamma_im;
+    x.kappa_sing = o->kappa_sing;
     return x;
 }
 

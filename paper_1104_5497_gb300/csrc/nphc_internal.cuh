@@ -123,6 +123,7 @@ struct XYSys {
     double Jd[NPHC_MAXN * NPHC_MAXN];       // J in FP64
     double gre, gim;                        // gamma
     double d2norm;                          // ||D^2 P / 2|| bound (alpha-theory gamma)
+    double kappa_sing;                      // singular above kappa_sing max(1, ||z||_inf^2)
 };
 
 struct XYCtl {                              // step control of one tracking call
@@ -194,6 +195,7 @@ struct QSys {
     const QTerm *terms;    // [row[n]] (device)
     double gre, gim;       // gamma
     double d2norm;         // ||D^2 P / 2|| bound
+    double kappa_sing;     // singular above kappa_sing max(1, ||z||_inf^2)
 };
 
 // ------------------------------------------------------ kernel launchers --

@@ -26,6 +26,31 @@ struct QuadProblem {
     static constexpr int NV = NVT;
     static constexpr int MD = NVT;
 
+    // the tracker's state is z itself (see XYProblem for the hooks)
+    static constexpr double NORM_SCALE = 1.0;
+    template <class V>
+    static __device__ __forceinline__ void load(const EPView &ep, int64_t e, const V &Z) {
+#pragma unroll 1
+        for (int k = 0; k < NV; k++)
+            Z.set(k, cx<double>{ep.z_re[k * ep.count + e], ep.z_im[k * ep.count + e]});
+    }
+    template <class V>
+    static __device__ __forceinline__ void store(const EPView &ep, int64_t e, const V &Z) {
+#pragma unroll 1
+        for (int k = 0; k < NV; k++) {
+            const cx<double> v = Z.get(k);
+            ep.z_re[k * ep.count + e] = v.re;
+            ep.z_im[k * ep.count + e] = v.im;
+        }
+    }
+    template <class V>
+    static __device__ __forceinline__ double norminf(const V &Z) {
+        double s = 0.0;
+#pragma unroll 1
+        for (int k = 0; k < NV; k++) s = fmax(s, sqrt(cabs2(Z.get(k))));
+        return s;
+    }
+
     template <class V>
     static __device__ __forceinline__ cx<double> w(const V &z, int a) {
         return a < 0 ? cx<double>{1.0, 0.0} : z.get(a);

@@ -42,11 +42,6 @@
 // point of the positive-dimensional family reached alpha = 0.115 < 0.158).
 #define NPHC_ALPHA_CERT (0.5 * (13.0 - 3.0 * sqrt(17.0)) / 4.0)
 
-// An endpoint whose Jacobian has Frobenius condition number ||DP||_F ||DP^-1||_F above
-// this is singular: at a point of a positive-dimensional solution set P vanishes to
-// double-double precision (beta is tiny) while rounding leaves the computed DP^-1 merely
-// huge, and the soft alpha test alone can pass there.
-#define NPHC_KAPPA_SING 1e12
 
 // One thread's array of complex doubles in shared memory.
 struct EGVec {
@@ -371,8 +366,14 @@ struct EGXY {
     static __device__ __forceinline__ double d2norm(const Sys &S) { return S.d2norm; }
 };
 
-// beta = ||DP^-1 P||, ||DP^-1||_F and ||P||_inf at the point in G.  False if singular,
-// counting a Frobenius condition number above NPHC_KAPPA_SING as singular.
+// beta = ||DP^-1 P||, ||DP^-1||_F and ||P||_inf at the point in G.  False if singular:
+// at a point of a positive-dimensional solution set P vanishes to double-double precision
+// (beta is tiny) while rounding leaves the computed DP^-1 merely huge, and the soft alpha
+// test alone can pass there, so a Frobenius condition number ||DP||_F ||DP^-1||_F above
+// kappa_sing max(1, ||z||_inf^2) counts as singular.  The bound grows with ||z||_inf^2 like
+// the solution tolerance: the equations are quadratic, the Jacobian's entries grow like
+// ||z|| and an isolated solution near the solution set at infinity has a smallest singular
+// value shrinking like 1 / ||z|| (a solution of norm 1e6 has a condition number ~1e12).
 template <class Q>
 __device__ bool eg_beta_invnorm_p(const EG<Q::DIM> &G, const typename Q::Sys &S, double &beta,
                                   double &invF, double &res) {
@@ -381,7 +382,10 @@ __device__ bool eg_beta_invnorm_p(const EG<Q::DIM> &G, const typename Q::Sys &S,
     const double fro = Q::jac_fro(G, S);
     beta = sqrt(Q::solve(G, S));
     invF = Q::inv_fro(G, S);
-    return isfinite(beta) && isfinite(invF) && fro * invF <= NPHC_KAPPA_SING;
+    double zi = 0.0;
+#pragma unroll 1
+    for (int k = 0; k < Q::NZ; k++) zi = fmax(zi, sqrt(cabs2(Q::zget(G, k))));
+    return isfinite(beta) && isfinite(invF) && fro * invF <= S.kappa_sing * fmax(1.0, zi * zi);
 }
 
 // Refinement and certification of entry e.  Returns true when e still needs the

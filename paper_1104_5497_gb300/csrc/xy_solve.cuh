@@ -8,13 +8,27 @@
 //
 // Structure used: the constraint row of site k touches only (x_k, y_k):
 //   a_k dx_k + b_k dy_k = r_gk,  a_k = 2 t x_k,  b_k = 2 (t + gamma (1-t)) y_k.
-// A unitary change of variables per site, (dx_k, dy_k) = conj(a^, b^) q_k + (b^, -a^) s_k
-// with (a^, b^) = (a_k, b_k) / |(a_k, b_k)|, turns that row into q_k = r_gk / |(a_k, b_k)|
-// and leaves an M x M complex system for s in the gradient rows:
-//   S_kj = A_kj b^_j - B_kj a^_j,   rhs_k = r_fk - sum_j (A_kj conj(a^_j) + B_kj conj(b^_j)) q_j,
-// where A = d(f rows)/dx and B = d(f rows)/dy of H.  S is solved by Householder QR:
-// unitary (no pivot search, no growth) and data-independent in its control flow.
-// Cost ~ (8/3) M^3 + O(M^2 + M N) real flops instead of (8/3) (2M)^3 for the full system.
+// Each site's step is written in scaled light-cone coordinates: with p_k = x_k + i y_k,
+// q_k = x_k - i y_k (e^(+-i theta_k) on the real circle), sp = max(1, |p_k|),
+// sq = max(1, |q_k|),
+//   dx_k = (sp dwp_k + sq dwq_k) / 2,   dy_k = -i (sp dwp_k - sq dwq_k) / 2,
+// so a row's coefficients (al, be) on (dx_k, dy_k) become (sp (al - i be) / 2,
+// sq (al + i be) / 2) on (dwp_k, dwq_k).  On a path to infinity one of p_k, q_k grows
+// like ||z|| while the other shrinks, and in (x, y) the Jacobian's condition number grows
+// like ||z||^2; in the scaled coordinates it stays moderate (measured on the N = 10 ring
+// at ||z|| = 1e8: a median of 1e4.5 against 1e13), so FP32 can follow a path to a finite
+// solution of large norm, or to the divergence radius.  At ||z|| <= 1 the scales are 1 and
+// the change is sqrt(1/2) times a unitary one.
+// A unitary change of variables per site, (dwp_k, dwq_k) = conj(a^, b^) q_k + (b^, -a^) s_k
+// with (a^, b^) the constraint row's coefficients (a'_k, b'_k) on (dwp_k, dwq_k) over their
+// norm, turns that row into q_k = r_gk / |(a'_k, b'_k)| and leaves an M x M complex system
+// for s in the gradient rows:
+//   S_kj = A'_kj b^_j - B'_kj a^_j,   rhs_k = r_fk - sum_j (A'_kj conj(a^_j) + B'_kj conj(b^_j)) q_j,
+// where A', B' are the gradient rows' coefficients on dwp_j, dwq_j.  For k != j
+// (A_kj, B_kj) = t J_kj (y_k, -x_k), which become (i t J_kj / 2) (sp_j q_k, -sq_j p_k).  S is
+// solved by Householder QR: unitary (no pivot search, no growth) and data-independent in
+// its control flow.  Cost ~ (8/3) M^3 + O(M^2 + M N) real flops instead of (8/3) (2M)^3
+// for the full system.
 //
 // Memory layout (one path per thread): the augmented M x (M + 2) matrix [S | b0 | b1]
 // of each thread lives in shared memory, column-major, each complex entry interleaved
@@ -103,16 +117,49 @@ __device__ __forceinline__ void xy_uw(const R *__restrict__ J, const cx<R> (&x)[
     }
 }
 
-// Frame of constraint row j: (a^, b^) and 1 / |(a_j, b_j)|.
+// Coefficients (al, be) of a row on (dx_j, dy_j) as coefficients on the scaled light-cone
+// step (dwp_j, dwq_j): (sp (al - i be) / 2, sq (al + i be) / 2).
+template <class R>
+__device__ __forceinline__ void lc_coef(cx<R> al, cx<R> be, R sp, R sq, cx<R> &alp, cx<R> &bep) {
+    alp = cscale(R(0.5) * sp, cx<R>{al.re + be.im, al.im - be.re});
+    bep = cscale(R(0.5) * sq, cx<R>{al.re - be.im, al.im + be.re});
+}
+
+// Scales of site j's light-cone coordinates: max(1, |x + i y|) and max(1, |x - i y|).
+template <class R>
+__device__ __forceinline__ void lc_scales(cx<R> xj, cx<R> yj, R &sp, R &sq) {
+    const cx<R> p = cx<R>{xj.re - yj.im, xj.im + yj.re}, q = cx<R>{xj.re + yj.im, xj.im - yj.re};
+    sp = fmax(R(1), sqrt_r(cabs2(p)));
+    sq = fmax(R(1), sqrt_r(cabs2(q)));
+}
+
+// Frame of constraint row j in site j's scaled light-cone coordinates: (a^, b^), the
+// inverse of the row's norm |(a'_j, b'_j)| and the scales sp, sq.
 template <class R>
 __device__ __forceinline__ void g_frame(cx<R> xj, cx<R> yj, R s, cx<R> sg, cx<R> &ah, cx<R> &bh,
-                                        R &iv) {
-    const cx<R> a = cscale(R(2) * s, xj);
-    const cx<R> bb = cscale(R(2), cmul(sg, yj));
+                                        R &iv, R &sp, R &sq) {
+    lc_scales<R>(xj, yj, sp, sq);
+    cx<R> a, bb;
+    lc_coef<R>(cscale(R(2) * s, xj), cscale(R(2), cmul(sg, yj)), sp, sq, a, bb);
     iv = rsqrt_r(cabs2(a) + cabs2(bb));
     ah = cscale(iv, a);
     bh = cscale(iv, bb);
 }
+
+// (dx_j, dy_j) from the light-cone step (dwp, dwq) = conj(a^, b^) q + (b^, -a^) s.
+template <class R>
+__device__ __forceinline__ void lc_step(cx<R> ah, cx<R> bh, R sp, R sq, cx<R> q, cx<R> s,
+                                        cx<R> &dx, cx<R> &dy) {
+    const cx<R> wp = cscale(sp, cadd(cmulc(ah, q), cmul(bh, s)));
+    const cx<R> wq = cscale(sq, csub(cmulc(bh, q), cmul(ah, s)));
+    dx = cscale(R(0.5), cadd(wp, wq));
+    const cx<R> d = csub(wp, wq);
+    dy = cx<R>{R(0.5) * d.im, R(-0.5) * d.re};   // -i (wp - wq) / 2
+}
+
+// i c
+template <class R>
+__device__ __forceinline__ cx<R> cmul_i(cx<R> c) { return cx<R>{-c.im, c.re}; }
 
 // Solve S x = b for the M x M matrix S of an augmented per-thread matrix
 // [S | b0 | b1] (b1 only when two_rhs) by Householder QR: Q^H [S | b] = [R | Q^H b] with a
@@ -210,7 +257,69 @@ __device__ __forceinline__ bool aug_qr_solve(const SMat<M, R, BLOCK> &A, bool tw
     return ok;
 }
 
-// Solve H_z(z, t) d = r at the point in `pt`, with t given as (s, omt) = (t, 1 - t).
+// ------------------------------------------------------------------------------------
+// The per-thread trackers keep each site's unknowns in light-cone coordinates,
+// p_k = x_k + i y_k and q_k = x_k - i y_k (the pinned site has p_N = q_N = 1).  Near infinity
+// one of them is tiny next to x_k and y_k, so (x, y) in FP32 would lose it to cancellation
+// once 1 - t < ~1e-6; in (p, q) the equations keep it exactly:
+//   f_k = -i (p_k U_q,k - q_k U_p,k) / 2,  U_p,k = sum_j J_kj p_j,  U_q,k = sum_j J_kj q_j,
+//   g_k = p_k q_k - 1,  x_k^2 - 1 = (p_k + q_k)^2 / 4 - 1,  y_k^2 - 1 = -(p_k - q_k)^2 / 4 - 1
+// (sums over every other site, the pinned one included).  The step is (dp, dq) =
+// (sp dwp, sq dwq), the scaled light-cone step of the solve above.
+
+// U_p,k and U_q,k (J_kk = 0, so the sums may run over every l); k may be a runtime index.
+template <int M, class R>
+__device__ __forceinline__ void lc_U(const R *__restrict__ J, const cx<R> (&p)[M],
+                                     const cx<R> (&q)[M], int k, cx<R> &Up, cx<R> &Uq) {
+    const R *Jk = J + k * NPHC_JSTRIDE;
+    Up = cx<R>{Jk[M], R(0)};
+    Uq = Up;
+#pragma unroll
+    for (int l = 0; l < M; l++) {
+        const R Jl = Jk[l];
+        Up.re += Jl * p[l].re;
+        Up.im += Jl * p[l].im;
+        Uq.re += Jl * q[l].re;
+        Uq.im += Jl * q[l].im;
+    }
+}
+
+// -H_t rows of site k (H_t = P - gamma Q) in light-cone coordinates.
+template <class R>
+__device__ __forceinline__ void lc_minus_ht_rows(cx<R> pk, cx<R> qk, cx<R> Up, cx<R> Uq,
+                                                 cx<R> gam, cx<R> &rf, cx<R> &rg) {
+    const cx<R> f = cscale(R(0.5), cmul_i(csub(cmul(qk, Up), cmul(pk, Uq))));
+    const cx<R> a = cadd(pk, qk), d = csub(pk, qk);
+    const cx<R> a2 = cmul(a, a), d2 = cmul(d, d), g = cmul(pk, qk);
+    rf = csub(cmul(gam, cx<R>{R(0.25) * a2.re - R(1), R(0.25) * a2.im}), f);
+    rg = csub(cmul(gam, cx<R>{R(-0.25) * d2.re - R(1), R(-0.25) * d2.im}), cx<R>{g.re - R(1), g.im});
+}
+
+// -H_t constraint row only (needs no couplings).
+template <class R>
+__device__ __forceinline__ cx<R> lc_minus_ht_g(cx<R> pk, cx<R> qk, cx<R> gam) {
+    const cx<R> d = csub(pk, qk);
+    const cx<R> d2 = cmul(d, d), g = cmul(pk, qk);
+    return csub(cmul(gam, cx<R>{R(-0.25) * d2.re - R(1), R(-0.25) * d2.im}), cx<R>{g.re - R(1), g.im});
+}
+
+// Frame of constraint row j at the light-cone point (p, q): the row's coefficients on
+// (dwp, dwq) are (sp (t q - gamma (1-t) (p - q) / 2), sq (t p + gamma (1-t) (p - q) / 2)).
+template <class R>
+__device__ __forceinline__ void g_frame_lc(cx<R> pj, cx<R> qj, R s, cx<R> gomt, cx<R> &ah,
+                                           cx<R> &bh, R &iv, R &sp, R &sq) {
+    sp = fmax(R(1), sqrt_r(cabs2(pj)));
+    sq = fmax(R(1), sqrt_r(cabs2(qj)));
+    const cx<R> hd = cscale(R(0.5), cmul(gomt, csub(pj, qj)));
+    const cx<R> a = cscale(sp, csub(cscale(s, qj), hd));
+    const cx<R> b = cscale(sq, cadd(cscale(s, pj), hd));
+    iv = rsqrt_r(cabs2(a) + cabs2(b));
+    ah = cscale(iv, a);
+    bh = cscale(iv, b);
+}
+
+// Solve H_z(z, t) d = r at the light-cone point in `pt` (p_1..p_M, q_1..q_M), t given as
+// (s, omt) = (t, 1 - t); d is the light-cone step (dp, dq).
 //   two_rhs == false: r = -H_t (predictor: d = dz/dt), written to out1.
 //   two_rhs == true:  r1 = the residual vector in `res` (corrector: -H), written to out1;
 //                     r2 = -H_t, written to out2.
@@ -224,13 +333,12 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
                                          bool two_rhs, const SVec<R, BLOCK> &res,
                                          const SVec<R, BLOCK> &out1, const Out2 &out2, bool wr) {
     const cx<R> gomt = cscale(omt, gam);
-    const cx<R> sg = cx<R>{s + gomt.re, gomt.im};   // t + gamma (1 - t)
 
-    cx<R> x[M], y[M];
+    cx<R> p[M], q[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
-        x[k] = pt.get(k);
-        y[k] = pt.get(M + k);
+        p[k] = pt.get(k);
+        q[k] = pt.get(M + k);
     }
     cx<R> b0[M], b1[M];
 #pragma unroll
@@ -239,19 +347,20 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
     // ---- build S column by column (columns j in a loop; rows unrolled)
 #pragma unroll 1
     for (int j = 0; j < M; j++) {
-        const cx<R> xj = pt.get(j), yj = pt.get(M + j);
-        cx<R> u, w, htf, htg;
-        xy_uw<M, R>(J, x, y, j, u, w);
-        minus_ht_rows<R>(xj, yj, u, w, gam, htf, htg);
+        const cx<R> pj = pt.get(j), qj = pt.get(M + j);
+        cx<R> Up, Uq, htf, htg;
+        lc_U<M, R>(J, p, q, j, Up, Uq);
+        lc_minus_ht_rows<R>(pj, qj, Up, Uq, gam, htf, htg);
         const cx<R> rf0 = two_rhs ? res.get(j) : htf;
         const cx<R> rg0 = two_rhs ? res.get(M + j) : htg;
-        // diagonal Jacobian entries of gradient row j
-        const cx<R> Ajj = cx<R>{-s * w.re + R(2) * (gomt.re * xj.re - gomt.im * xj.im),
-                                -s * w.im + R(2) * (gomt.re * xj.im + gomt.im * xj.re)};
-        const cx<R> Bjj = cscale(s, u);
         cx<R> ah, bh;
-        R iv;
-        g_frame<R>(xj, yj, s, sg, ah, bh, iv);
+        R iv, sp, sq;
+        g_frame_lc<R>(pj, qj, s, gomt, ah, bh, iv, sp, sq);
+        // diagonal entries of gradient row j on (dwp_j, dwq_j):
+        // (sp (-i t U_q + gamma (1-t) (p + q)) / 2, sq (i t U_p + gamma (1-t) (p + q)) / 2)
+        const cx<R> gpq = cmul(gomt, cadd(pj, qj));
+        const cx<R> Ajj = cscale(R(0.5) * sp, csub(gpq, cmul_i(cscale(s, Uq))));
+        const cx<R> Bjj = cscale(R(0.5) * sq, cadd(gpq, cmul_i(cscale(s, Up))));
         const cx<R> q0 = cscale(iv, rg0), q1 = cscale(iv, htg);
         const cx<R> px0 = cmulc(ah, q0), py0 = cmulc(bh, q0);
         const cx<R> px1 = cmulc(ah, q1), py1 = cmulc(bh, q1);
@@ -259,13 +368,19 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
         const cx<R> d0 = csub(rf0, cadd(cmul(Ajj, px0), cmul(Bjj, py0)));
         const cx<R> d1 = csub(htf, cadd(cmul(Ajj, px1), cmul(Bjj, py1)));
         if (two_rhs && wr) out2.set(M + j, rg0);   // the residual's g row, for the recovery
+        // off-diagonal entries J_kj (q_k cb + p_k ca) and right-hand-side terms
+        // J_kj (q_k cpx - p_k cpy), with the factor i t / 2 and the scales folded in
+        const R hs = R(0.5) * s;
+        const cx<R> cb = cmul_i(cscale(hs * sp, bh)), ca = cmul_i(cscale(hs * sq, ah));
+        const cx<R> cpx0 = cmul_i(cscale(hs * sp, px0)), cpy0 = cmul_i(cscale(hs * sq, py0));
+        const cx<R> cpx1 = cmul_i(cscale(hs * sp, px1)), cpy1 = cmul_i(cscale(hs * sq, py1));
 #pragma unroll
         for (int k = 0; k < M; k++) {
-            // off-diagonal entries; J_jj = 0 makes the k == j term vanish
-            const R sJ = s * J[k * NPHC_JSTRIDE + j];
-            A.set(k, j, cscale(sJ, cadd(cmul(y[k], bh), cmul(x[k], ah))));
-            b0[k] = csub(b0[k], cscale(sJ, csub(cmul(y[k], px0), cmul(x[k], py0))));
-            if (two_rhs) b1[k] = csub(b1[k], cscale(sJ, csub(cmul(y[k], px1), cmul(x[k], py1))));
+            // J_jj = 0 makes the k == j term vanish
+            const R Jkj = J[k * NPHC_JSTRIDE + j];
+            A.set(k, j, cscale(Jkj, cadd(cmul(q[k], cb), cmul(p[k], ca))));
+            b0[k] = csub(b0[k], cscale(Jkj, csub(cmul(q[k], cpx0), cmul(p[k], cpy0))));
+            if (two_rhs) b1[k] = csub(b1[k], cscale(Jkj, csub(cmul(q[k], cpx1), cmul(p[k], cpy1))));
             if (k == j) {
                 b0[k] = cadd(b0[k], d0);
                 b1[k] = cadd(b1[k], d1);
@@ -283,135 +398,126 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
 
     bool ok = aug_qr_solve<M, R, BLOCK>(A, two_rhs);
 
-    // ---- back to (dx, dy)
+    // ---- back to (dp, dq) = (sp dwp, sq dwq),
+    // (dwp, dwq) = conj(a^, b^) q_j + (b^, -a^) s_j
     R chk = R(0);
 #pragma unroll 1
     for (int j = 0; j < M; j++) {
-        const cx<R> xj = pt.get(j), yj = pt.get(M + j);
+        const cx<R> pj = pt.get(j), qj = pt.get(M + j);
         cx<R> ah, bh;
-        R iv;
-        g_frame<R>(xj, yj, s, sg, ah, bh, iv);
-        const cx<R> htg = minus_ht_g<R>(xj, yj, gam);
+        R iv, sp, sq;
+        g_frame_lc<R>(pj, qj, s, gomt, ah, bh, iv, sp, sq);
+        const cx<R> htg = lc_minus_ht_g<R>(pj, qj, gam);
         const cx<R> q0 = cscale(iv, two_rhs ? out2.get(M + j) : htg);
         const cx<R> s0 = A.get(j, M);
-        const cx<R> dx0 = cadd(cmulc(ah, q0), cmul(bh, s0));
-        const cx<R> dy0 = csub(cmulc(bh, q0), cmul(ah, s0));
-        chk += cabs2(dx0) + cabs2(dy0);
+        const cx<R> dp0 = cscale(sp, cadd(cmulc(ah, q0), cmul(bh, s0)));
+        const cx<R> dq0 = cscale(sq, csub(cmulc(bh, q0), cmul(ah, s0)));
+        chk += cabs2(dp0) + cabs2(dq0);
         if (two_rhs) {
             const cx<R> q1 = cscale(iv, htg);
             const cx<R> s1 = A.get(j, M + 1);
-            const cx<R> dx1 = cadd(cmulc(ah, q1), cmul(bh, s1));
-            const cx<R> dy1 = csub(cmulc(bh, q1), cmul(ah, s1));
-            chk += cabs2(dx1) + cabs2(dy1);
+            const cx<R> dp1 = cscale(sp, cadd(cmulc(ah, q1), cmul(bh, s1)));
+            const cx<R> dq1 = cscale(sq, csub(cmulc(bh, q1), cmul(ah, s1)));
+            chk += cabs2(dp1) + cabs2(dq1);
             if (wr) {
-                out2.set(j, dx1);
-                out2.set(M + j, dy1);
+                out2.set(j, dp1);
+                out2.set(M + j, dq1);
             }
         }
         if (wr) {
-            out1.set(j, dx0);
-            out1.set(M + j, dy0);
+            out1.set(j, dp0);
+            out1.set(M + j, dq0);
         }
     }
     return ok && finite_r(chk);
 }
 
-// -H(z, t) in the working precision R (no compensation), written to out when wr.
-template <int M, class R, int BLOCK>
-__device__ __forceinline__ void xy_residual_plain(const R *__restrict__ J, const SVec<R, BLOCK> &pt,
-                                                  R s, R omt, cx<R> gam,
-                                                  const SVec<R, BLOCK> &out, bool wr) {
-    const cx<R> gomt = cscale(omt, gam);
-    cx<R> x[M], y[M];
-#pragma unroll
-    for (int k = 0; k < M; k++) {
-        x[k] = pt.get(k);
-        y[k] = pt.get(M + k);
-    }
-#pragma unroll 1
-    for (int k = 0; k < M; k++) {
-        const cx<R> xk = pt.get(k), yk = pt.get(M + k);
-        cx<R> u, w;
-        xy_uw<M, R>(J, x, y, k, u, w);
-        const cx<R> f = csub(cmul(yk, u), cmul(xk, w));
-        const cx<R> x2 = cmul(xk, xk), y2 = cmul(yk, yk);
-        const cx<R> hf = cadd(cmul(gomt, cx<R>{x2.re - R(1), x2.im}), cscale(s, f));
-        const cx<R> hg = cadd(cmul(gomt, cx<R>{y2.re - R(1), y2.im}),
-                              cscale(s, cx<R>{x2.re + y2.re - R(1), x2.im + y2.im}));
-        if (wr) {
-            out.set(k, cx<R>{-hf.re, -hf.im});
-            out.set(M + k, cx<R>{-hg.re, -hg.im});
-        }
-    }
-}
-
-// -H(z, t) evaluated with compensated sums (float-float for FP32, double-double for
-// FP64) and exact products, then rounded once: the error is ~u^2 of the terms instead of
-// u, so a Newton corrector driven by it converges to the rounding of the path point
-// even when H_z is far from well conditioned (mixed-precision iterative refinement; at
-// large ||z|| the terms of H are ~||z||^2 while H itself is near zero).  The coefficients
-// J, gamma (1-t) and t enter as their values in R.
+// -H(z, t) at the light-cone point in `pt`, evaluated with compensated sums (float-float
+// for FP32, double-double for FP64) and exact products, then rounded once: the error is
+// ~u^2 of the terms instead of u, so a Newton corrector driven by it converges to the
+// rounding of the path point even when H_z is far from well conditioned (mixed-precision
+// iterative refinement; at large ||z|| the terms of H are ~||z||^2 while H itself is near
+// zero).  The coefficients J, gamma (1-t) and t enter as their values in R; every other
+// factor is a product of two coordinates (or one coordinate and a power of two).
 template <int M, class R, int BLOCK>
 __device__ __forceinline__ void xy_residual_comp(const R *__restrict__ J,
                                                  const SVec<R, BLOCK> &pt, R s, R omt,
                                                  cx<R> gam, const SVec<R, BLOCK> &out, bool wr) {
     using E = EFT<R>;
     const cx<R> gomt = cx<R>{E::mul(omt, gam.re), E::mul(omt, gam.im)};
-    cx<R> x[M], y[M];
+    cx<R> p[M], q[M];
 #pragma unroll
     for (int k = 0; k < M; k++) {
-        x[k] = pt.get(k);
-        y[k] = pt.get(M + k);
+        p[k] = pt.get(k);
+        q[k] = pt.get(M + k);
     }
     const ext<R> zero = {R(0), R(0)};
+    const R hs = R(0.5) * s;
 #pragma unroll 1
     for (int k = 0; k < M; k++) {
-        const cx<R> xk = pt.get(k), yk = pt.get(M + k);
+        const cx<R> pk = pt.get(k), qk = pt.get(M + k);
         const R *Jk = J + k * NPHC_JSTRIDE;
-        ext<R> ure = {Jk[M], R(0)}, uim = zero, wre = zero, wim = zero;
+        ext<R> upr = {Jk[M], R(0)}, upi = zero, uqr = {Jk[M], R(0)}, uqi = zero;
 #pragma unroll
         for (int l = 0; l < M; l++) {   // J_kk = 0 adds exact zeros
             const R Jl = Jk[l];
-            ext_acc(ure, Jl, x[l].re);
-            ext_acc(uim, Jl, x[l].im);
-            ext_acc(wre, Jl, y[l].re);
-            ext_acc(wim, Jl, y[l].im);
+            ext_acc(upr, Jl, p[l].re);
+            ext_acc(upi, Jl, p[l].im);
+            ext_acc(uqr, Jl, q[l].re);
+            ext_acc(uqi, Jl, q[l].im);
         }
-        // f = y u - x w
-        ext<R> fre = zero, fim = zero;
-        ext_acc_ext(fre, yk.re, ure);
-        ext_acc_ext(fre, -yk.im, uim);
-        ext_acc_ext(fre, -xk.re, wre);
-        ext_acc_ext(fre, xk.im, wim);
-        ext_acc_ext(fim, yk.re, uim);
-        ext_acc_ext(fim, yk.im, ure);
-        ext_acc_ext(fim, -xk.re, wim);
-        ext_acc_ext(fim, -xk.im, wre);
-        // x^2 - 1 and y^2 - 1 exactly as two-word numbers
-        ext<R> qxr = {R(-1), R(0)}, qxi = zero, qyr = {R(-1), R(0)}, qyi = zero;
-        ext_acc(qxr, xk.re, xk.re);
-        ext_acc(qxr, -xk.im, xk.im);
-        ext_acc(qxi, R(2) * xk.re, xk.im);
-        ext_acc(qyr, yk.re, yk.re);
-        ext_acc(qyr, -yk.im, yk.im);
-        ext_acc(qyi, R(2) * yk.re, yk.im);
-        // H_f = gomt (x^2 - 1) + s f ;  H_g = gomt (y^2 - 1) + s (x^2 + y^2 - 1)
+        // D = q U_p - p U_q, f = i D / 2
+        ext<R> dr = zero, di = zero;
+        ext_acc_ext(dr, qk.re, upr);
+        ext_acc_ext(dr, -qk.im, upi);
+        ext_acc_ext(dr, -pk.re, uqr);
+        ext_acc_ext(dr, pk.im, uqi);
+        ext_acc_ext(di, qk.re, upi);
+        ext_acc_ext(di, qk.im, upr);
+        ext_acc_ext(di, -pk.re, uqi);
+        ext_acc_ext(di, -pk.im, uqr);
+        // X = x^2 - 1 = (p^2 + 2 p q + q^2) / 4 - 1, Y = y^2 - 1 = -(p^2 - 2 p q + q^2) / 4 - 1,
+        // G = p q - 1, as two-word numbers (the factors 1/4, 1/2 are exact)
+        ext<R> xr = {R(-1), R(0)}, xi = zero, yr = {R(-1), R(0)}, yi = zero;
+        ext<R> gr = {R(-1), R(0)}, gi = zero;
+        ext_acc(xr, R(0.25) * pk.re, pk.re);
+        ext_acc(xr, R(-0.25) * pk.im, pk.im);
+        ext_acc(xr, R(0.5) * pk.re, qk.re);
+        ext_acc(xr, R(-0.5) * pk.im, qk.im);
+        ext_acc(xr, R(0.25) * qk.re, qk.re);
+        ext_acc(xr, R(-0.25) * qk.im, qk.im);
+        ext_acc(xi, R(0.5) * pk.re, pk.im);
+        ext_acc(xi, R(0.5) * pk.re, qk.im);
+        ext_acc(xi, R(0.5) * pk.im, qk.re);
+        ext_acc(xi, R(0.5) * qk.re, qk.im);
+        ext_acc(yr, R(-0.25) * pk.re, pk.re);
+        ext_acc(yr, R(0.25) * pk.im, pk.im);
+        ext_acc(yr, R(0.5) * pk.re, qk.re);
+        ext_acc(yr, R(-0.5) * pk.im, qk.im);
+        ext_acc(yr, R(-0.25) * qk.re, qk.re);
+        ext_acc(yr, R(0.25) * qk.im, qk.im);
+        ext_acc(yi, R(-0.5) * pk.re, pk.im);
+        ext_acc(yi, R(0.5) * pk.re, qk.im);
+        ext_acc(yi, R(0.5) * pk.im, qk.re);
+        ext_acc(yi, R(-0.5) * qk.re, qk.im);
+        ext_acc(gr, pk.re, qk.re);
+        ext_acc(gr, -pk.im, qk.im);
+        ext_acc(gi, pk.re, qk.im);
+        ext_acc(gi, pk.im, qk.re);
+        // H_f = gomt X + t f ;  H_g = gomt Y + t G
         ext<R> hfr = zero, hfi = zero, hgr = zero, hgi = zero;
-        ext_acc_ext(hfr, gomt.re, qxr);
-        ext_acc_ext(hfr, -gomt.im, qxi);
-        ext_acc_ext(hfr, s, fre);
-        ext_acc_ext(hfi, gomt.re, qxi);
-        ext_acc_ext(hfi, gomt.im, qxr);
-        ext_acc_ext(hfi, s, fim);
-        ext_acc_ext(hgr, gomt.re, qyr);
-        ext_acc_ext(hgr, -gomt.im, qyi);
-        ext_acc_ext(hgr, s, qxr);
-        ext_acc_ext(hgr, s, qyr);
-        ext_acc(hgr, s, R(1));       // x^2 + y^2 - 1 = (x^2 - 1) + (y^2 - 1) + 1
-        ext_acc_ext(hgi, gomt.re, qyi);
-        ext_acc_ext(hgi, gomt.im, qyr);
-        ext_acc_ext(hgi, s, qxi);
-        ext_acc_ext(hgi, s, qyi);
+        ext_acc_ext(hfr, gomt.re, xr);
+        ext_acc_ext(hfr, -gomt.im, xi);
+        ext_acc_ext(hfr, -hs, di);
+        ext_acc_ext(hfi, gomt.re, xi);
+        ext_acc_ext(hfi, gomt.im, xr);
+        ext_acc_ext(hfi, hs, dr);
+        ext_acc_ext(hgr, gomt.re, yr);
+        ext_acc_ext(hgr, -gomt.im, yi);
+        ext_acc_ext(hgr, s, gr);
+        ext_acc_ext(hgi, gomt.re, yi);
+        ext_acc_ext(hgi, gomt.im, yr);
+        ext_acc_ext(hgi, s, gi);
         if (wr) {
             out.set(k, cx<R>{-ext_val(hfr), -ext_val(hfi)});
             out.set(M + k, cx<R>{-ext_val(hgr), -ext_val(hgi)});

@@ -24,10 +24,11 @@
 // on a reject; the final step lands exactly on t = t_end (1, or 1 - r0 before the Cauchy
 // endgame).
 //
-// A path whose ||z||_inf exceeds rdiv is taken to go to infinity, in either precision
-// (the same radius as the oracle's: genuinely finite solutions near that scale are
-// approached with the same power-law growth as paths to infinity, so no growth test
-// can separate them before t = 1).
+// A path whose ||z||_inf exceeds rdiv (1e8 by default) is taken to go to infinity, in
+// either precision, as in the oracle: finite solutions of large norm are approached with
+// the same power-law growth as paths to infinity, so only a radius far beyond the
+// solutions sought tells them apart.  The tracker's state is kept in light-cone
+// coordinates (XYProblem, xy_solve.cuh), which FP32 resolves out to that radius.
 // FP32 pass (ctl.handoff = 1): on a step size underflow, ten consecutive rejects, a
 // crawl near t = 1 (1 - t failing to halve within crawl_steps accepted steps), its own
 // (smaller) attempt budget or a radius crossing within RDIV_BAND close to t = 1, a path
@@ -74,8 +75,11 @@ __device__ __forceinline__ R vnorminf(const V &v) {
 
 // The problem a tracker runs on, as a policy for track_body: the unknowns (NV), the
 // per-thread shared matrix (MD x (MD + 2)), the start point with its dz/dt, the
-// corrector residual -H and the linear solve.  XYProblem: the XY ring (structured Schur
-// solve, M = N - 1 free sites, NV = 2M).
+// corrector residual -H, the linear solve, and the tracker state's relation to the
+// endpoint arrays' z (load, store, the factor that turns the state's 2-norm into z's and
+// z's inf-norm).  XYProblem: the XY ring (structured Schur solve, M = N - 1 free sites,
+// NV = 2M), its state in light-cone coordinates p_k = x_k + i y_k, q_k = x_k - i y_k
+// (xy_solve.cuh): a unitary map times sqrt(2), so 2-norms are the state's over sqrt(2).
 template <int M, class RT, int BLK>
 struct XYProblem {
     using R = RT;
@@ -83,9 +87,48 @@ struct XYProblem {
     static constexpr int BLOCK = BLK;
     static constexpr int NV = 2 * M;
     static constexpr int MD = M;
+    static constexpr R NORM_SCALE = R(0.70710678118654752440);   // sqrt(1/2)
+
+    // (x, y) of the endpoint arrays (FP64) to (p, q), formed in FP64 and then rounded
+    template <class V>
+    static __device__ __forceinline__ void load(const EPView &ep, int64_t e, const V &Z) {
+        const int64_t cnt = ep.count;
+#pragma unroll 1
+        for (int k = 0; k < M; k++) {
+            const double xr = ep.z_re[k * cnt + e], xi = ep.z_im[k * cnt + e];
+            const double yr = ep.z_re[(M + k) * cnt + e], yi = ep.z_im[(M + k) * cnt + e];
+            Z.set(k, cx<R>{(R)(xr - yi), (R)(xi + yr)});
+            Z.set(M + k, cx<R>{(R)(xr + yi), (R)(xi - yr)});
+        }
+    }
+    // (p, q) to x = (p + q) / 2, y = -i (p - q) / 2, in FP64
+    template <class V>
+    static __device__ __forceinline__ void store(const EPView &ep, int64_t e, const V &Z) {
+        const int64_t cnt = ep.count;
+#pragma unroll 1
+        for (int k = 0; k < M; k++) {
+            const cx<R> pk = Z.get(k), qk = Z.get(M + k);
+            const double pr = pk.re, pi = pk.im, qr = qk.re, qi = qk.im;
+            ep.z_re[k * cnt + e] = 0.5 * (pr + qr);
+            ep.z_im[k * cnt + e] = 0.5 * (pi + qi);
+            ep.z_re[(M + k) * cnt + e] = 0.5 * (pi - qi);
+            ep.z_im[(M + k) * cnt + e] = -0.5 * (pr - qr);
+        }
+    }
+    // max_k max(|x_k|, |y_k|) = max_k max(|p_k + q_k|, |p_k - q_k|) / 2
+    template <class V>
+    static __device__ __forceinline__ R norminf(const V &Z) {
+        R s = R(0);
+#pragma unroll 1
+        for (int k = 0; k < M; k++) {
+            const cx<R> pk = Z.get(k), qk = Z.get(M + k);
+            s = fmax(s, fmax(cabs2(cadd(pk, qk)), cabs2(csub(pk, qk))));
+        }
+        return R(0.5) * sqrt_r(s);
+    }
 
     // start point of path p and its derivative: at t = 0, H_z = 2 gamma diag(z) and
-    // H_t = P(z), so dz_i/dt = -P_i(z) / (2 gamma z_i)
+    // H_t = P(z), so dz_i/dt = -P_i(z) / (2 gamma z_i); both in light-cone coordinates
     static __device__ __forceinline__ void start(const Sys &S, int64_t p, const GVec<R> &Z0,
                                                  const GVec<R> &K1) {
         const R *J = JSel<R>::get(S);
@@ -104,10 +147,12 @@ struct XYProblem {
             cx<R> u, w, rf, rg;
             xy_uw<M, R>(J, x, y, k, u, w);
             minus_ht_rows<R>(xk, yk, u, w, gam, rf, rg);
-            Z0.set(k, xk);
-            Z0.set(M + k, yk);
-            K1.set(k, cscale(R(0.5) * xk.re, cmul(ig, rf)));
-            K1.set(M + k, cscale(R(0.5) * yk.re, cmul(ig, rg)));
+            const cx<R> dx = cscale(R(0.5) * xk.re, cmul(ig, rf));
+            const cx<R> dy = cscale(R(0.5) * yk.re, cmul(ig, rg));
+            Z0.set(k, cx<R>{xk.re, yk.re});    // p = x + i y (x, y real at the start)
+            Z0.set(M + k, cx<R>{xk.re, -yk.re});
+            K1.set(k, cadd(dx, cmul_i(dy)));
+            K1.set(M + k, csub(dx, cmul_i(dy)));
         }
     }
 
@@ -212,9 +257,7 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                     attempts = 0;
                     have_ck = false;
                     if (C.resume) {
-#pragma unroll 1
-                        for (int k = 0; k < NV; k++)
-                            Z0.set(k, cx<R>{(R)ep.z_re[k * cnt + e], (R)ep.z_im[k * cnt + e]});
+                        P::load(ep, e, Z0);
                         t = ep.t[e];
                         // restart with a step on the scale of 1 - t: the FP32 pass may have
                         // been crawling with a far smaller one
@@ -321,11 +364,11 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                         ZC.set(k, zp);
                         zz += cabs2(zp);
                     }
-                    zpn = sqrt_r(zz);
+                    zpn = sqrt_r(zz) * P::NORM_SCALE;
                 }
             } else {
                 newton++;
-                const R dn = vnorm2<NV, R>(W1);
+                const R dn = vnorm2<NV, R>(W1) * P::NORM_SCALE;
                 if (!oks || !finite_r(dn)) {
                     bad = true;
                 } else if (ph == 4 && dn > (R)C.trust * (R(1) + zpn)) {
@@ -338,7 +381,7 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                         ZC.set(k, zn);
                         zz += cabs2(zn);
                     }
-                    if (dn <= (R)C.eps * (R(1) + sqrt_r(zz))) conv = true;
+                    if (dn <= (R)C.eps * (R(1) + sqrt_r(zz) * P::NORM_SCALE)) conv = true;
                 }
             }
         }
@@ -348,14 +391,12 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
         if (go) {
             attempts++;
             if (conv) {
-                R zi = R(0);
 #pragma unroll 6
                 for (int k = 0; k < NV; k++) {
-                    const cx<R> v = ZC.get(k);
-                    Z0.set(k, v);
+                    Z0.set(k, ZC.get(k));
                     K1.set(k, AC.get(k));
-                    zi = fmax(zi, sqrt_r(cabs2(v)));
                 }
+                const R zi = P::norminf(ZC);
                 t = t1;
                 steps++;
                 rejects = 0;
@@ -414,12 +455,10 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
         }
         if (act && status != NPHC_PATH_RUNNING) {
             const bool from_ck = status == NPHC_PATH_HANDOFF && have_ck;
-#pragma unroll 1
-            for (int k = 0; k < NV; k++) {
-                const cx<R> v = from_ck ? CK.get(k) : Z0.get(k);
-                ep.z_re[k * cnt + e] = (double)v.re;
-                ep.z_im[k * cnt + e] = (double)v.im;
-            }
+            if (from_ck)
+                P::store(ep, e, CK);
+            else
+                P::store(ep, e, Z0);
             ep.t[e] = from_ck ? tck : t;
             ep.h[e] = from_ck ? hck : (status == NPHC_PATH_HANDOFF ? hacc : h);
             ep.status[e] = status;

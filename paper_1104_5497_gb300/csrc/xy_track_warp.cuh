@@ -37,7 +37,8 @@ struct WarpLayout {
     static constexpr int Q0 = P0 + M;
     static constexpr int P1 = Q0 + M;
     static constexpr int Q1 = P1 + M;
-    static constexpr int SC = Q1 + M;     // reflector scalars of the current Householder step
+    static constexpr int SS = Q1 + M;     // light-cone scales (sp, sq) of each site
+    static constexpr int SC = SS + M;     // reflector scalars of the current Householder step
     static constexpr int TOTAL = SC + 2;
 };
 
@@ -157,16 +158,18 @@ __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, d
         cx<double> htf, htg;
         minus_ht_rows<double>(xj, yj, u, w, gam, htf, htg);
         const cx<double> rg0 = two_rhs ? P.at(L::W1, M + j) : htg;
-        const cx<double> Ajj = cx<double>{-s * w.re + 2.0 * (gomt.re * xj.re - gomt.im * xj.im),
-                                          -s * w.im + 2.0 * (gomt.re * xj.im + gomt.im * xj.re)};
-        const cx<double> Bjj = cscale(s, u);
         cx<double> ah, bh;
-        double iv;
-        g_frame<double>(xj, yj, s, sg, ah, bh, iv);
+        double iv, sp, sq;
+        g_frame<double>(xj, yj, s, sg, ah, bh, iv, sp, sq);
+        cx<double> Ajj, Bjj;   // diagonal entries of gradient row j on (dwp_j, dwq_j)
+        lc_coef<double>(cx<double>{-s * w.re + 2.0 * (gomt.re * xj.re - gomt.im * xj.im),
+                                   -s * w.im + 2.0 * (gomt.re * xj.im + gomt.im * xj.re)},
+                        cscale(s, u), sp, sq, Ajj, Bjj);
         const cx<double> q0 = cscale(iv, rg0), q1 = cscale(iv, htg);
         P.at(L::AH, j) = ah;
         P.at(L::BH, j) = bh;
         P.at(L::IV, j) = cx<double>{iv, 0.0};
+        P.at(L::SS, j) = cx<double>{sp, sq};
         P.at(L::AJ, j) = Ajj;
         P.at(L::BJ, j) = Bjj;
         P.at(L::P0, j) = cmulc(ah, q0);
@@ -179,22 +182,31 @@ __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, d
     }
     __syncwarp();
     // ---- column j of S (lane j), right-hand-side row k (lane k)
+    // (off-diagonal: (i t J_kj / 2) (sp_j q_k b^_j + sq_j p_k a^_j) and right-hand-side terms
+    // (i t J_kj / 2) (sp_j q_k px_j - sq_j p_k py_j), p = x + i y, q = x - i y; see xy_solve.cuh)
     if (lane < M) {
         const int j = lane;
         const cx<double> ah = P.at(L::AH, j), bh = P.at(L::BH, j);
+        const cx<double> sc = P.at(L::SS, j);
+        const double hs = 0.5 * s;
+        const cx<double> cb = cmul_i(cscale(hs * sc.re, bh)), ca = cmul_i(cscale(hs * sc.im, ah));
 #pragma unroll 1
         for (int k = 0; k < M; k++) {
             cx<double> e;
             if (k == j) {
                 e = csub(cmul(P.at(L::AJ, j), bh), cmul(P.at(L::BJ, j), ah));
             } else {
-                const double sJ = s * J[k * NPHC_JSTRIDE + j];
-                e = cscale(sJ, cadd(cmul(P.at(L::ZC, M + k), bh), cmul(P.at(L::ZC, k), ah)));
+                const cx<double> xk = P.at(L::ZC, k), yk = P.at(L::ZC, M + k);
+                const cx<double> pk = cx<double>{xk.re - yk.im, xk.im + yk.re};
+                const cx<double> qk = cx<double>{xk.re + yk.im, xk.im - yk.re};
+                e = cscale(J[k * NPHC_JSTRIDE + j], cadd(cmul(qk, cb), cmul(pk, ca)));
             }
             P.A(k, j) = e;
         }
         const int k = lane;
         const cx<double> xk = P.at(L::ZC, k), yk = P.at(L::ZC, M + k);
+        const cx<double> pk = cx<double>{xk.re - yk.im, xk.im + yk.re};
+        const cx<double> qk = cx<double>{xk.re + yk.im, xk.im - yk.re};
         cx<double> b0 = P.A(k, M), b1 = two_rhs ? P.A(k, M + 1) : cx<double>{0.0, 0.0};
 #pragma unroll 1
         for (int jj = 0; jj < M; jj++) {
@@ -205,9 +217,11 @@ __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, d
                 b0 = csub(b0, cadd(cmul(Ak, px0), cmul(Bk, py0)));
                 if (two_rhs) b1 = csub(b1, cadd(cmul(Ak, px1), cmul(Bk, py1)));
             } else {
-                const double sJ = s * J[k * NPHC_JSTRIDE + jj];
-                b0 = csub(b0, cscale(sJ, csub(cmul(yk, px0), cmul(xk, py0))));
-                if (two_rhs) b1 = csub(b1, cscale(sJ, csub(cmul(yk, px1), cmul(xk, py1))));
+                const cx<double> scj = P.at(L::SS, jj);
+                const double hJ = hs * J[k * NPHC_JSTRIDE + jj];
+                const cx<double> qs = cscale(hJ * scj.re, qk), ps = cscale(hJ * scj.im, pk);
+                b0 = csub(b0, cmul_i(csub(cmul(qs, px0), cmul(ps, py0))));
+                if (two_rhs) b1 = csub(b1, cmul_i(csub(cmul(qs, px1), cmul(ps, py1))));
             }
         }
         P.A(k, M) = b0;
@@ -274,19 +288,17 @@ __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, d
         const int j = lane;
         const cx<double> ah = P.at(L::AH, j), bh = P.at(L::BH, j);
         const double iv = P.at(L::IV, j).re;
+        const cx<double> sc = P.at(L::SS, j);
         const cx<double> xj = P.at(L::ZC, j), yj = P.at(L::ZC, M + j);
         const cx<double> htg = minus_ht_g<double>(xj, yj, gam);
         const cx<double> q0 = cscale(iv, two_rhs ? P.at(L::W1, M + j) : htg);
-        const cx<double> s0 = P.A(j, M);
-        const cx<double> dx0 = cadd(cmulc(ah, q0), cmul(bh, s0));
-        const cx<double> dy0 = csub(cmulc(bh, q0), cmul(ah, s0));
+        cx<double> dx0, dy0;
+        lc_step<double>(ah, bh, sc.re, sc.im, q0, P.A(j, M), dx0, dy0);
         chk += cabs2(dx0) + cabs2(dy0);
         cx<double> dx1 = cx<double>{0.0, 0.0}, dy1 = dx1;
         if (two_rhs) {
             const cx<double> q1 = cscale(iv, htg);
-            const cx<double> s1 = P.A(j, M + 1);
-            dx1 = cadd(cmulc(ah, q1), cmul(bh, s1));
-            dy1 = csub(cmulc(bh, q1), cmul(ah, s1));
+            lc_step<double>(ah, bh, sc.re, sc.im, q1, P.A(j, M + 1), dx1, dy1);
             chk += cabs2(dx1) + cabs2(dy1);
         }
         P.at(L::W1, j) = dx0;   // lane j reads and writes only entries j and M + j

@@ -58,7 +58,8 @@ class nphc_options(ctypes.Structure):
                 ("eg_samples", ctypes.c_int), ("eg_max_cycle", ctypes.c_int),
                 ("eg_tol_close", ctypes.c_double), ("eg_tol_conv", ctypes.c_double),
                 ("eg_h_min", ctypes.c_double), ("eg_max_attempts", ctypes.c_int),
-                ("list_blocks_per_sm", ctypes.c_int)]
+                ("list_blocks_per_sm", ctypes.c_int),
+                ("kappa_sing", ctypes.c_double), ("kappa_fp32", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -164,11 +165,14 @@ def _stream_ptr(stream) -> int | None:
 def options_default(**kw) -> nphc_options:
     o = nphc_options()
     _check("nphc_options_default", lib().nphc_options_default(ctypes.byref(o)))
+    fields = {f[0] for f in nphc_options._fields_}
     for k, v in kw.items():
         if k == "gamma":
             o.gamma_re, o.gamma_im = float(np.real(v)), float(np.imag(v))
-        else:
+        elif k in fields:
             setattr(o, k, v)
+        else:
+            raise TypeError(f"nphc_options has no field {k!r}")
     return o
 
 
