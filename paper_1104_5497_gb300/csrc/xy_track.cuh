@@ -54,6 +54,17 @@ struct JSel<double> {
 };
 
 #define CRAWL_ZONE 1e-3   // the crawl test applies once 1 - t < CRAWL_ZONE
+// A path in the end zone whose ||z||_inf exceeds FAR_NORM and grew by more than FAR_GROWTH
+// on its last accepted step is heading out (to infinity, or to a finite solution of
+// large norm it has not reached yet): its next step is at most KAPPA_FAR (1 - t), so that
+// it does not try to land on t = 1 while it still grows (such a landing always fails,
+// and halving back cost as many solves as the steps themselves).  With RK4 on a path
+// growing like (1 - t)^-a the relative error of a step of KAPPA_FAR (1 - t) is at most 5e-4
+// for a <= 1, below the FP32 trust bound.  Once the path stops growing the cap is off and
+// the step to t = 1 is tried as usual.
+#define FAR_NORM 10.0
+#define FAR_GROWTH 1.01
+#define KAPPA_FAR 0.5
 #define NEAR_END 1e-5     // FP32 radius crossings with 1 - t below this ...
 #define RDIV_BAND 1e-3    // ... and ||z||_inf within rdiv (1 + RDIV_BAND) go to FP64
 
@@ -231,12 +242,15 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
     }
     int64_t e = (lane >= lanes) ? -2 : -1;   // entry index; -1 idle, -2 drained
     double t = 0.0, h = 0.0, hacc = 0.0;
-    double tck = 0.0, hck = 0.0;   // checkpoint: the first accepted point with 1 - t < CRAWL_ZONE
+    double tck = 0.0, hck = 0.0;   // checkpoint: the last clean accepted point with 1 - t < CRAWL_ZONE
     bool have_ck = false;
+    int clean = 0;                 // accepted steps in a row without a reject between them
     double tmark = 0.0;   // 1 - t recorded every CRAWL_STEPS accepted steps near t = 1
     int since = 0;
     int status = 0, run = 0, rejects = 0, attempts = 0, steps = 0, solves = 0, newton = 0;
     bool need_k1 = false;
+    bool far = false;      // heading out: steps capped at KAPPA_FAR (1 - t)
+    double zlast = 0.0;    // ||z||_inf at the last accepted point
 
     for (;;) {
         // ---- hand new entries to idle lanes
@@ -256,6 +270,7 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                     rejects = 0;
                     attempts = 0;
                     have_ck = false;
+                    clean = 0;
                     if (C.resume) {
                         P::load(ep, e, Z0);
                         t = ep.t[e];
@@ -279,6 +294,8 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                     hacc = h;
                     tmark = 1.0 - t;
                     since = 0;
+                    far = false;
+                    zlast = 0.0;
                 } else {
                     e = -2;
                 }
@@ -291,6 +308,7 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
         // path (one Newton correction at the same t) and its dz/dt taken from the same
         // solve (only when some lane needs it), phases 1..3 = RK4 stages 2..4, phases
         // 4.. = Newton corrector iterations at t + h
+        if (far && h > KAPPA_FAR * (1.0 - t)) h = KAPPA_FAR * (1.0 - t);
         double hh = h, t1 = t + h;
         if (t1 >= C.t_end) {
             t1 = C.t_end;
@@ -397,7 +415,10 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                     K1.set(k, AC.get(k));
                 }
                 const R zi = P::norminf(ZC);
+                clean = rejects == 0 ? clean + 1 : 1;
                 t = t1;
+                far = 1.0 - t < CRAWL_ZONE && (double)zi > FAR_NORM && (double)zi > FAR_GROWTH * zlast;
+                zlast = (double)zi;
                 steps++;
                 rejects = 0;
                 hacc = h;
@@ -415,12 +436,16 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                                  : NPHC_PATH_DIVERGED;
                 else if (t >= C.t_end)
                     status = NPHC_PATH_REACHED;
-                // FP32 pass: keep the state where the path enters the end zone; a path
-                // that the pass later hands off resumes in FP64 from there, not from the
-                // point where FP32 precision ran out (which can sit off the path when the
-                // endpoint is ill-conditioned; a checkpoint moved forward by later FP32
-                // steps that still looked healthy lost solutions near the radius)
-                if (C.handoff && !have_ck && status == NPHC_PATH_RUNNING && 1.0 - t < CRAWL_ZONE) {
+                // FP32 pass: in the end zone keep the last clean point (accepted, with the
+                // step before it accepted too); a path that the pass later hands off
+                // resumes in FP64 from there, not from the point where FP32 precision ran
+                // out, which can sit off the path.  A converged FP32 point in light-cone
+                // coordinates is on its path to the corrector's tolerance; in (x, y) the
+                // small light-cone coordinate of a far point was lost to cancellation, so
+                // such points could look converged while off the path, and the checkpoint
+                // then had to stay at the end zone's entry.
+                if (C.handoff && (clean >= 2 || !have_ck) && status == NPHC_PATH_RUNNING &&
+                    1.0 - t < CRAWL_ZONE) {
 #pragma unroll 6
                     for (int k = 0; k < NV; k++) CK.set(k, Z0.get(k));
                     tck = t;

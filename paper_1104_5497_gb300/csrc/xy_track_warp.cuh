@@ -374,8 +374,11 @@ __global__ void __launch_bounds__(32 * WARPS)
             need_k1 = false;
         }
         hacc = h;
+        bool far = false;      // heading out: steps capped at KAPPA_FAR (1 - t) (xy_track.cuh)
+        double zlast = 0.0;
         __syncwarp();
         while (status == NPHC_PATH_RUNNING) {
+            if (far && h > KAPPA_FAR * (1.0 - t)) h = KAPPA_FAR * (1.0 - t);
             double hh = h, t1 = t + h;
             if (t1 >= C.t_end) {
                 t1 = C.t_end;
@@ -463,6 +466,8 @@ __global__ void __launch_bounds__(32 * WARPS)
                 zi = warp_max(zi);
                 __syncwarp();
                 t = t1;
+                far = 1.0 - t < CRAWL_ZONE && zi > FAR_NORM && zi > FAR_GROWTH * zlast;
+                zlast = zi;
                 steps++;
                 rejects = 0;
                 hacc = h;

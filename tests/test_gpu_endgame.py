@@ -89,7 +89,12 @@ def test_ring_singular_and_failed_paths_match_oracle(N):
     o = O.endgame(O.xy_terms(N, out["J"]), GAMMA, paths)
     g = gpu_endgame(N_, N_.System(N, 1.0), paths)
     compare(g, o)
-    assert np.all(np.isin(g["status"], [O.EG_CONVERGED, O.EG_AT_INFINITY]))
+    # slow paths to infinity that stall below the divergence radius may stay undecided
+    # after the last radius; their estimates do not solve P (as in the oracle's test)
+    assert np.all(np.isin(g["status"], [O.EG_CONVERGED, O.EG_AT_INFINITY, O.EG_NOT_CONVERGED]))
+    T = O.xy_terms(N, out["J"])
+    for z in g["z"][g["status"] == O.EG_NOT_CONVERGED]:
+        assert np.abs(T.eval_acc(z)).max() > 1e3 * 1e-10 * max(1.0, np.abs(z).max() ** 2)
 
 
 def test_pipeline_option_on_ring_n8():
