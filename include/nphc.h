@@ -70,7 +70,9 @@ enum {
     NPHC_PATH_MIN_STEP = 3,     /* step size fell below h_min */
     NPHC_PATH_STEP_BUDGET = 4,  /* more than max_steps step attempts */
     NPHC_PATH_NONFINITE = 5,    /* NaN or Inf in the state */
-    NPHC_PATH_HANDOFF = 6       /* FP32 tracking stopped; FP64 continues from (z, t, h) */
+    NPHC_PATH_HANDOFF = 6,      /* FP32 tracking stopped; FP64 continues from (z, t, h) */
+    NPHC_PATH_HANDOFF_COND = 7  /* FP32 tracking stopped at a step whose condition estimate
+                                   exceeded kappa_fp32; FP64 continues from (z, t, h) */
 };
 
 /* Class of one endpoint after refinement, certification and deduplication. */
@@ -126,8 +128,10 @@ typedef struct nphc_options {
     double kappa_sing;         /* an endpoint is singular (never certified) when its Jacobian's
                                   Frobenius condition number ||DP||_F ||DP^-1||_F exceeds
                                   kappa_sing max(1, ||z||_inf^2), 1e12 */
-    double kappa_fp32;         /* FP32 pass: a path whose condition estimate exceeds this is
-                                  handed to FP64 (see nphc_track); 0 = no such test, 0 */
+    double kappa_fp32;         /* FP32 pass: a step whose condition estimate exceeds this is
+                                  not taken and FP64 continues the path (NPHC_PATH_HANDOFF_COND,
+                                  see nphc_track); FP32 solves lose about kappa x 6e-8 of
+                                  their relative accuracy.  0 = no such test; 1e6 */
 } nphc_options;
 
 typedef struct nphc_system nphc_system;   /* opaque; owns the device copy of the couplings */
@@ -135,7 +139,7 @@ typedef struct nphc_result nphc_result;   /* opaque; owns device buffers for all
 
 /* Device endpoint arrays, caller-owned, for the step-by-step calls below.  count
  * entries; n = 2(N-1) components per point.  Any output pointer may be NULL where a
- * call does not write it. */
+ * call does not write it; with count = 0 every array may be NULL. */
 typedef struct nphc_endpoints {
     int64_t count;
     int64_t *path;       /* [count] path index of each entry (input) */
@@ -163,6 +167,16 @@ nphc_status nphc_options_default(nphc_options *opt);
  * N*N row-major.  NPHC_EINVAL for N outside [NPHC_MIN_N, NPHC_MAX_N], non-finite sigma,
  * asymmetric g, or a scaled coupling <= 0. */
 nphc_status nphc_xy_couplings(int N, double sigma, const double *g, double eps, double *J_out);
+
+/* The couplings' vector-Jacobian product with respect to sigma: given dL/dJ (host, N*N
+ * row-major: the gradient of a loss L with respect to every entry of the matrix that
+ * nphc_xy_couplings returns for the same arguments), writes
+ *   *dsigma = sum_{i != j} dL/dJ_ij dJ_ij/dsigma,  dJ_ij/dsigma = -ln(d_ij) J_ij
+ * (J_ij = d_ij^-sigma (1 + eps g_ij); the paper's couplings with sigma its alpha, section
+ * "A First Application").  The diagonal of dL/dJ is ignored.  Errors as for
+ * nphc_xy_couplings, and NPHC_EINVAL for a NULL dL_dJ or dsigma. */
+nphc_status nphc_xy_couplings_vjp(int N, double sigma, const double *g, double eps,
+                                  const double *dL_dJ, double *dsigma);
 
 /* Builds the polynomial system of Eq. (alg_dec_XY_model_poly) for the ring with
  * couplings J (host, N*N row-major, symmetric, zero diagonal, finite) or, when J is
@@ -215,7 +229,9 @@ nphc_status nphc_workspace_size(const nphc_system *sys, int64_t count, size_t *b
  * (classical RK4 on dz/dt = -H_z^-1 H_t) and a Newton corrector, in precision prec:
  *   FP64:  plain FP64 tracking;
  *   MIXED: FP32 tracking; a path the FP32 tracker cannot finish ends with status
- *          NPHC_PATH_HANDOFF and its (z, t, h) for an FP64 call with resume = 1.
+ *          NPHC_PATH_HANDOFF, or NPHC_PATH_HANDOFF_COND when a step's condition estimate
+ *          (max |R_kk| / min |R_kk| of the Householder factor of the step's Schur system)
+ *          exceeded opt->kappa_fp32, and its (z, t, h) for an FP64 call with resume = 1.
  * list (device int32, may be NULL) selects entries list[0 .. *list_count - 1]
  * (list_count: device int32); NULL tracks every entry.  resume = 0 starts each selected
  * path at its start point; resume = 1 continues from ep's (z, t, h).  Writes z, t, h,
@@ -262,7 +278,9 @@ nphc_status nphc_dedup(const nphc_system *sys, const nphc_options *opt, const np
  * inside the library (about 7.3 MB, part of the library's device image, present in every
  * context that loads it); the call allocates nothing and calls no allocating routine.
  *   The first call on a device (with that device current) looks up the array's device
- * address and caches it; make that first call before any stream capture.
+ * address and caches it for the device's current context; make that first call before
+ * any stream capture.  A new context on the device (after cudaDeviceReset, say) holds a
+ * new copy of the array, whose address the next call looks up again.
  *   Every call on a device shares the one array and leaves its contents behind; each
  * call clears the parts that must start at zero before use.  Calls whose work overlaps
  * on the GPU (other streams, other host threads) race on the array and give wrong
@@ -366,6 +384,7 @@ enum {
     NPHC_COUNT_EG_CONVERGED,   /* of which NPHC_EG_CONVERGED (a finite endpoint) */
     NPHC_COUNT_EG_MULTIPLE,    /* of which with cycle number >= 2 (a singular endpoint) */
     NPHC_COUNT_EG_AT_INFINITY, /* NPHC_EG_AT_INFINITY or NPHC_EG_DIVERGED */
+    NPHC_COUNT_HANDOFF_COND,   /* of NPHC_COUNT_HANDOFF: handed off by the condition test */
     NPHC_NCOUNTS
 };
 

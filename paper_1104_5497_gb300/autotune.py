@@ -127,7 +127,7 @@ def tune(system, opts, sample: int = 262144, reps: int = 3, cache: str | None = 
     N_.track(system, o, N_.PREC_MIXED, ep, ws)
     torch.cuda.synchronize()
     st = ep.tensors["status"]
-    ho = torch.nonzero(st == N_.PATH_HANDOFF).flatten().to(torch.int32)
+    ho = torch.nonzero((st == N_.PATH_HANDOFF) | (st == N_.PATH_HANDOFF_COND)).flatten().to(torch.int32)
     lists = {}
     if ho.numel() > 0:
         count = torch.tensor([ho.numel()], dtype=torch.int32, device="cuda")

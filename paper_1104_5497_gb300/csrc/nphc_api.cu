@@ -4,6 +4,8 @@
 // host; the couplings reach the kernels as launch parameters (constant bank), so a
 // system owns no device memory.  A result owns one device allocation that holds every
 // per-path array, the work lists, the counters and the deduplication scratch.
+#include <cuda.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -157,7 +159,7 @@ nphc_status nphc_options_default(nphc_options *o) {
     o->block_size = 0;
     o->blocks_per_sm = 0;
     o->kappa_sing = 1e12;
-    o->kappa_fp32 = 0.0;
+    o->kappa_fp32 = 1e6;
     return NPHC_OK;
 }
 
@@ -184,6 +186,25 @@ nphc_status nphc_xy_couplings(int N, double sigma, const double *g, double eps, 
             if (!(v > 0.0) || !std::isfinite(v)) return fail(NPHC_EINVAL, "coupling <= 0 or not finite");
             J[i * N + j] = v;
         }
+    return NPHC_OK;
+}
+
+nphc_status nphc_xy_couplings_vjp(int N, double sigma, const double *g, double eps,
+                                  const double *dL_dJ, double *dsigma) {
+    if (!dL_dJ || !dsigma) return fail(NPHC_EINVAL, "dL_dJ or dsigma is NULL");
+    if (N < NPHC_MIN_N || N > NPHC_MAX_N) return fail(NPHC_EINVAL, "N outside [3, 13]");
+    std::vector<double> J(N * N);
+    nphc_status s = nphc_xy_couplings(N, sigma, g, eps, J.data());
+    if (s != NPHC_OK) return s;
+    double acc = 0.0;
+    for (int i = 0; i < N; i++)
+        for (int j = 0; j < N; j++) {
+            if (i == j) continue;
+            const int d = std::min(std::abs(i - j), N - std::abs(i - j));
+            acc += dL_dJ[i * N + j] * (-std::log((double)d)) * J[i * N + j];
+        }
+    if (!std::isfinite(acc)) return fail(NPHC_EINVAL, "dL_dJ not finite");
+    *dsigma = acc;
     return NPHC_OK;
 }
 
@@ -391,6 +412,7 @@ XYCtl make_ctl(const nphc_options *o, bool fp32, bool resume, bool accumulate) {
     c.sparse = 0;
     c.crawl_steps = fp32 ? o->crawl_steps_fp32 : 0;
     c.t_end = 1.0;
+    c.kappa = fp32 ? o->kappa_fp32 : 0.0;
     return c;
 }
 
@@ -497,6 +519,7 @@ nphc_status check_ep(const nphc_system *S, const nphc_endpoints *ep, bool certif
     if (!S || !ep) return fail(NPHC_EINVAL, "NULL argument");
     if (ep->count < 0 || ep->count > S->npaths || ep->count > INT32_MAX)
         return fail(NPHC_EINVAL, "endpoint count out of range");
+    if (ep->count == 0) return NPHC_OK;   // nothing is read or written
     if (!ep->path || !ep->z_re || !ep->z_im || !ep->t || !ep->h || !ep->status || !ep->steps ||
         !ep->solves || !ep->newton)
         return fail(NPHC_EINVAL, "endpoint arrays missing");
@@ -1005,18 +1028,44 @@ static __device__ __align__(256) unsigned char g_dedup_noalloc_scratch[kNoallocB
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mu;
 void *g_noalloc_ptr[kNoallocMaxDevices] = {};
+CUcontext g_noalloc_ctx[kNoallocMaxDevices] = {};
 
-// Device address of the array on the current device, looked up once per device.
+// The calling thread's current driver context, through the runtime's driver entry point
+// (the library does not link the driver library itself); NULL when it cannot be queried.
+CUcontext current_context() {
+    using Fn = CUresult(CUDAAPI *)(CUcontext *);
+    static Fn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<Fn>(f);
+        else
+            cudaGetLastError();
+    });
+    CUcontext c = nullptr;
+    if (!fn || fn(&c) != CUDA_SUCCESS) return nullptr;
+    return c;
+}
+
+// Device address of the array in the current device's current context, looked up on the
+// first call in that context and cached; a new context (after cudaDeviceReset, say) holds
+// a new copy of the array and gets its own lookup.
 nphc_status noalloc_scratch(void **out) {
     int dev = -1;
     NPHC_CK(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kNoallocMaxDevices) return fail(NPHC_EINVAL, "device ordinal out of range");
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    CUcontext ctx = current_context();
+    if (!g_noalloc_ptr[dev] || !ctx || ctx != g_noalloc_ctx[dev]) {
         void *p = nullptr;
         NPHC_CK(cudaGetSymbolAddress(&p, g_dedup_noalloc_scratch));
         if (!p) return fail(NPHC_ECUDA, "cudaGetSymbolAddress returned NULL");
         g_noalloc_ptr[dev] = p;
+        g_noalloc_ctx[dev] = current_context();   // the lookup may have created the context
     }
     *out = g_noalloc_ptr[dev];
     return NPHC_OK;
@@ -1040,7 +1089,10 @@ nphc_status nphc_dedup_noalloc(const nphc_system *S, const nphc_options *o,
                                      "); use nphc_dedup with a workspace");
     void *base = nullptr;
     if ((s = noalloc_scratch(&base)) != NPHC_OK) return s;
-    if (ep->count == 0) return NPHC_OK;
+    if (ep->count == 0) {   // nothing to deduplicate; *dup_count is still an output
+        if (dup_count) NPHC_CK(cudaMemsetAsync(dup_count, 0, sizeof(int32_t), (cudaStream_t)stream));
+        return NPHC_OK;
+    }
     // Same layout as the workspace path for this count, so both paths hash alike.
     const int64_t tsize = table_size_for(ep->count);
     char *b = static_cast<char *>(base);

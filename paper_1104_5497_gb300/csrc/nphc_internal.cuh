@@ -138,6 +138,9 @@ struct XYCtl {                              // step control of one tracking call
                                             // accepted steps (0: no crawl test)
     double t_end;                           // tracking stops here: 1, or 1 - r0 before the
                                             // Cauchy endgame
+    double kappa;                           // FP32 pass: a step attempt whose solves' condition
+                                            // estimate exceeds this hands the path to FP64
+                                            // (NPHC_PATH_HANDOFF_COND); 0: no test
 };
 
 struct EGCtl {                              // the Cauchy endgame (cauchy.cuh)

@@ -16,8 +16,9 @@ __global__ void compact_kernel(const EPView ep, int pred, int32_t *flags, int32_
     if (e >= ep.count) return;
     bool take = false;
     if (pred == PRED_HANDOFF) {
-        take = ep.status[e] == NPHC_PATH_HANDOFF;
-        if (take) flags[e] |= FLAG_FP64_CONTINUED;
+        const int st = ep.status[e];
+        take = st == NPHC_PATH_HANDOFF || st == NPHC_PATH_HANDOFF_COND;
+        if (take) flags[e] |= FLAG_FP64_CONTINUED | (st == NPHC_PATH_HANDOFF_COND ? FLAG_COND : 0);
     } else if (pred == PRED_UNCERTIFIED_FP32) {
         // FP32 endpoints that do not certify are tracked again from t = 0 in FP64 (hand-offs
         // already continued in FP64 from where they entered the end zone)
@@ -259,6 +260,7 @@ __global__ void counts_kernel(const EPView ep, const int32_t *flags, const int32
         else if (c == NPHC_END_DUPLICATE) atomicAdd(&loc[NPHC_COUNT_DUPLICATE], 1ull);
         if (flags) {
             if (flags[e] & FLAG_FP64_CONTINUED) atomicAdd(&loc[NPHC_COUNT_HANDOFF], 1ull);
+            if (flags[e] & FLAG_COND) atomicAdd(&loc[NPHC_COUNT_HANDOFF_COND], 1ull);
             if (flags[e] & (FLAG_RETRACKED | FLAG_RETRACKED_DUP)) atomicAdd(&loc[NPHC_COUNT_RETRACKED], 1ull);
         }
         atomicAdd(&loc[NPHC_COUNT_SOLVES], (unsigned long long)ep.solves[e]);
@@ -333,13 +335,14 @@ cudaError_t launch_flag_list(const int32_t *list, const int32_t *count, int64_t 
 cudaError_t launch_dedup(const EPView &ep, int n, double delta, DedupScratch w, int32_t *list,
                          int32_t *count, cudaStream_t st, const int32_t *mlist,
                          const int32_t *mcount) {
-    if (ep.count == 0) return cudaSuccess;
     cudaError_t err;
+    // *count is an output of every call, an empty set included
+    if (count && (err = cudaMemsetAsync(count, 0, sizeof(int32_t), st))) return err;
+    if (ep.count == 0) return cudaSuccess;
     const size_t slots = (size_t)DD_LEVELS * w.table_size;
     if ((err = cudaMemsetAsync(w.keys, 0, sizeof(unsigned long long) * slots, st))) return err;
     if ((err = cudaMemsetAsync(w.head, 0xff, sizeof(int32_t) * slots, st))) return err;
     if ((err = cudaMemsetAsync(w.inlist, 0, sizeof(int32_t) * ep.count, st))) return err;
-    if (count && (err = cudaMemsetAsync(count, 0, sizeof(int32_t), st))) return err;
     const int g = blocks_for(ep.count, 256);
     dedup_insert_kernel<<<g, 256, 0, st>>>(ep, n, delta, w);
     nphc_launch_counter(1);

@@ -11,7 +11,7 @@ enum {
     PRED_REACHED_DIRECT = 5,      // PRED_REACHED over the entries without FLAG_FP64_CONTINUED
     PRED_REACHED_CONTINUED = 6    // PRED_REACHED over the entries with FLAG_FP64_CONTINUED
 };
-enum { FLAG_FP64_CONTINUED = 1, FLAG_RETRACKED = 2, FLAG_RETRACKED_DUP = 4 };
+enum { FLAG_FP64_CONTINUED = 1, FLAG_RETRACKED = 2, FLAG_RETRACKED_DUP = 4, FLAG_COND = 8 };
 
 #define DD_LEVELS 4   // grid pitches 1e-6, 1e-4, 1e-2, 1
 

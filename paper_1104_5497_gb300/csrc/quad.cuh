@@ -95,8 +95,9 @@ struct QuadProblem {
                                                  double omt, bool two_rhs,
                                                  const SVec<double, BLOCK> &res,
                                                  const SVec<double, BLOCK> &out1, const Out2 &out2,
-                                                 bool wr) {
-        return solve_g(S, A, pt, s, omt, cx<double>{S.gre, S.gim}, two_rhs, res, out1, out2, wr);
+                                                 bool wr, double *kest = nullptr) {
+        return solve_g(S, A, pt, s, omt, cx<double>{S.gre, S.gim}, two_rhs, res, out1, out2, wr,
+                       kest);
     }
 
     // the same with an explicit gamma (see XYProblem::residual_g)
@@ -146,7 +147,8 @@ struct QuadProblem {
                                                    double omt, cx<double> gam, bool two_rhs,
                                                    const SVec<double, BLOCK> &res,
                                                    const SVec<double, BLOCK> &out1,
-                                                   const Out2 &out2, bool wr) {
+                                                   const Out2 &out2, bool wr,
+                                                   double *kest = nullptr) {
         const cx<double> g2 = cscale(2.0 * omt, gam);
 #pragma unroll 1
         for (int c = 0; c < NV; c++)
@@ -172,7 +174,7 @@ struct QuadProblem {
             A.set(i, NV, two_rhs ? res.get(i) : mht);
             if (two_rhs) A.set(i, NV + 1, mht);
         }
-        const bool ok = aug_qr_solve<NV, double, BLOCK>(A, two_rhs);
+        const bool ok = aug_qr_solve<NV, double, BLOCK>(A, two_rhs, kest);
         double chk = 0.0;
 #pragma unroll 1
         for (int i = 0; i < NV; i++) {

@@ -399,7 +399,7 @@ __device__ bool eg_refine_certify_one(const EG<Q::DIM> &G, const typename Q::Sys
     const int64_t cnt = ep.count;
     const double alpha0 = NPHC_ALPHA_CERT;
     const int st = ep.status[e];
-    const bool sc = shortcut && st == NPHC_PATH_HANDOFF;
+    const bool sc = shortcut && (st == NPHC_PATH_HANDOFF || st == NPHC_PATH_HANDOFF_COND);
     if (!sc) {
         ep.alpha[e] = INFINITY;
         ep.beta[e] = INFINITY;

@@ -165,10 +165,14 @@ __device__ __forceinline__ cx<R> cmul_i(cx<R> c) { return cx<R>{-c.im, c.re}; }
 // [S | b0 | b1] (b1 only when two_rhs) by Householder QR: Q^H [S | b] = [R | Q^H b] with a
 // real diagonal (stored as (beta, 0) on the diagonal of S), then back substitution in
 // place: the solutions end in columns M and M + 1.  Returns false when S is singular.
+// kest (may be NULL) receives max_k |R_kk| / min_k |R_kk|, a lower bound on the condition
+// number of S that costs two comparisons per column.
 template <int M, class R, int BLOCK>
-__device__ __forceinline__ bool aug_qr_solve(const SMat<M, R, BLOCK> &A, bool two_rhs) {
+__device__ __forceinline__ bool aug_qr_solve(const SMat<M, R, BLOCK> &A, bool two_rhs,
+                                             R *kest = nullptr) {
     const int ncol = two_rhs ? M + 2 : M + 1;
     bool ok = true;
+    R rmax = R(0), rmin = R(0);
 #pragma unroll 1
     for (int k = 0; k < M; k++) {
         const int n = M - k;   // active rows k .. M-1, relative index i = 0 .. n-1
@@ -191,6 +195,8 @@ __device__ __forceinline__ bool aug_qr_solve(const SMat<M, R, BLOCK> &A, bool tw
         }
         const R an = sqrt_r(cabs2(al) + (xa + xb));
         ok = ok && (an > R(0));
+        rmax = fmax(rmax, an);
+        rmin = k == 0 ? an : fmin(rmin, an);
         const R beta = al.re >= R(0) ? -an : an;
         const R ib = recip_r(beta);
         const cx<R> tauc = cx<R>{(beta - al.re) * ib, al.im * ib};   // conj(tau)
@@ -254,6 +260,7 @@ __device__ __forceinline__ bool aug_qr_solve(const SMat<M, R, BLOCK> &A, bool tw
         }
     }
 
+    if (kest) *kest = rmin > R(0) ? rmax / rmin : R(INFINITY);
     return ok;
 }
 
@@ -331,7 +338,8 @@ template <int M, class R, int BLOCK, class Out2>
 __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, R, BLOCK> &A,
                                          const SVec<R, BLOCK> &pt, R s, R omt, cx<R> gam,
                                          bool two_rhs, const SVec<R, BLOCK> &res,
-                                         const SVec<R, BLOCK> &out1, const Out2 &out2, bool wr) {
+                                         const SVec<R, BLOCK> &out1, const Out2 &out2, bool wr,
+                                         R *kest = nullptr) {
     const cx<R> gomt = cscale(omt, gam);
 
     cx<R> p[M], q[M];
@@ -396,7 +404,7 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
         if (two_rhs) A.set(k, M + 1, b1[k]);
     }
 
-    bool ok = aug_qr_solve<M, R, BLOCK>(A, two_rhs);
+    bool ok = aug_qr_solve<M, R, BLOCK>(A, two_rhs, kest);
 
     // ---- back to (dp, dq) = (sp dwp, sq dwq),
     // (dwp, dwq) = conj(a^, b^) q_j + (b^, -a^) s_j

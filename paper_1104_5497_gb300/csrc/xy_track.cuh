@@ -177,8 +177,9 @@ struct XYProblem {
                                                  const SVec<R, BLOCK> &pt, R s, R omt,
                                                  bool two_rhs, const SVec<R, BLOCK> &res,
                                                  const SVec<R, BLOCK> &out1, const Out2 &out2,
-                                                 bool wr) {
-        return solve_g(S, A, pt, s, omt, cx<R>{(R)S.gre, (R)S.gim}, two_rhs, res, out1, out2, wr);
+                                                 bool wr, R *kest = nullptr) {
+        return solve_g(S, A, pt, s, omt, cx<R>{(R)S.gre, (R)S.gim}, two_rhs, res, out1, out2, wr,
+                       kest);
     }
 
     // the same with an explicit gamma (per thread: the Cauchy endgame's equivalent real-t
@@ -195,9 +196,9 @@ struct XYProblem {
                                                    cx<R> gam, bool two_rhs,
                                                    const SVec<R, BLOCK> &res,
                                                    const SVec<R, BLOCK> &out1, const Out2 &out2,
-                                                   bool wr) {
+                                                   bool wr, R *kest = nullptr) {
         return xy_solve<M, R, BLOCK>(JSel<R>::get(S), A, pt, s, omt, gam, two_rhs, res, out1, out2,
-                                     wr);
+                                     wr, kest);
     }
 };
 
@@ -318,6 +319,7 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
         bool go = act && !need_k1;
         bool conv = false, bad = false;
         R zpn = R(0);
+        R kstep = R(0);   // the largest condition estimate of this attempt's solves
         const int ph0 = __any_sync(0xffffffffu, act && need_k1) ? 0 : 1;
         const int nph = 4 + C.max_newton;
 #pragma unroll 1
@@ -352,9 +354,11 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
             }
             const R tr = (R)te, omt = (R)(1.0 - te);
             if (corr) P::residual(S, ZC, tr, omt, W1, w);
-            const bool oks = P::solve(S, A, ZC, tr, omt, corr, W1, W1, AC, w);
+            R kest = R(0);
+            const bool oks = P::solve(S, A, ZC, tr, omt, corr, W1, W1, AC, w, &kest);
             if (!w) continue;
             solves++;
+            kstep = fmax(kstep, kest);
             if (ph == 0) {
                 // z0 += Newton correction at t; dz/dt from the second right-hand side
 #pragma unroll 6
@@ -404,6 +408,17 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
             }
         }
         go = go && status == NPHC_PATH_RUNNING;
+
+        // ---- FP32 pass: a step whose Schur system's condition estimate exceeds kappa
+        // (kappa = 0 outside the FP32 pass) is not taken; FP64 continues the path from its
+        // last accepted point (or the end zone's clean checkpoint), where the estimate was
+        // below kappa: the FP32 solve's relative error grows like the condition number
+        // times 6e-8, and a step across an ill-conditioned stretch (two paths passing
+        // close) can land on the neighbouring path
+        if (go && C.kappa > 0.0 && !((double)kstep <= C.kappa)) {
+            status = NPHC_PATH_HANDOFF_COND;
+            go = false;
+        }
 
         // ---- accept or reject
         if (go) {
@@ -479,13 +494,14 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                 status = C.handoff ? NPHC_PATH_HANDOFF : NPHC_PATH_STEP_BUDGET;
         }
         if (act && status != NPHC_PATH_RUNNING) {
-            const bool from_ck = status == NPHC_PATH_HANDOFF && have_ck;
+            const bool handed = status == NPHC_PATH_HANDOFF || status == NPHC_PATH_HANDOFF_COND;
+            const bool from_ck = handed && have_ck;
             if (from_ck)
                 P::store(ep, e, CK);
             else
                 P::store(ep, e, Z0);
             ep.t[e] = from_ck ? tck : t;
-            ep.h[e] = from_ck ? hck : (status == NPHC_PATH_HANDOFF ? hacc : h);
+            ep.h[e] = from_ck ? hck : (handed ? hacc : h);
             ep.status[e] = status;
             ep.steps[e] = steps;
             ep.solves[e] = solves;

@@ -19,14 +19,15 @@ NPHC_MIN_N, NPHC_MAX_N = 3, 13
 PREC_FP64, PREC_MIXED = 0, 1
 
 PATH_RUNNING, PATH_REACHED, PATH_DIVERGED, PATH_MIN_STEP, PATH_STEP_BUDGET, PATH_NONFINITE, \
-    PATH_HANDOFF = range(7)
+    PATH_HANDOFF, PATH_HANDOFF_COND = range(8)
 END_NONE, END_SINGULAR, END_REAL, END_NONREAL, END_UNDECIDED, END_DUPLICATE, END_FAILED = range(7)
 
 COUNT_NAMES = ["paths", "reached", "diverged", "failed", "real", "nonreal", "undecided",
                "singular", "duplicate", "handoff", "retracked", "solves", "launches"]
-# after the index histogram (NPHC_COUNT_EG_*)
+# after the index histogram (NPHC_COUNT_EG_*, then NPHC_COUNT_HANDOFF_COND)
 EG_COUNT_NAMES = ["eg_run", "eg_converged", "eg_multiple", "eg_at_infinity"]
-NCOUNTS = len(COUNT_NAMES) + NPHC_MAX_N + len(EG_COUNT_NAMES)
+TAIL_COUNT_NAMES = ["handoff_cond"]
+NCOUNTS = len(COUNT_NAMES) + NPHC_MAX_N + len(EG_COUNT_NAMES) + len(TAIL_COUNT_NAMES)
 # Cauchy endgame outcomes (NPHC_EG_*)
 EG_NONE, EG_CONVERGED, EG_NOT_CLOSED, EG_NOT_CONVERGED, EG_TRACK_FAILED, EG_DIVERGED, \
     EG_AT_INFINITY = range(7)
@@ -90,6 +91,7 @@ def lib():
     sig = {
         "nphc_options_default": [ctypes.POINTER(nphc_options)],
         "nphc_xy_couplings": [i32, d, pd, d, pd],
+        "nphc_xy_couplings_vjp": [i32, d, pd, d, pd, pd],
         "nphc_system_create_xy": [i32, d, pd, ctypes.POINTER(vp)],
         "nphc_system_create_quadratic": [i32, i32, ctypes.POINTER(ctypes.c_int32),
                                          ctypes.POINTER(ctypes.c_int32),
@@ -185,6 +187,19 @@ def xy_couplings(N: int, sigma: float, g: np.ndarray | None = None, eps: float =
     return J
 
 
+def xy_couplings_vjp(N: int, sigma: float, dL_dJ: np.ndarray, g: np.ndarray | None = None,
+                     eps: float = 0.1) -> float:
+    """nphc_xy_couplings_vjp: dL/dsigma from dL/dJ (N x N) of the couplings."""
+    dJ = np.ascontiguousarray(dL_dJ, dtype=np.float64)
+    gg = None if g is None else np.ascontiguousarray(g, dtype=np.float64)
+    out = ctypes.c_double()
+    _check("nphc_xy_couplings_vjp", lib().nphc_xy_couplings_vjp(int(N), float(sigma),
+                                                               None if gg is None else _pd(gg),
+                                                               float(eps), _pd(dJ),
+                                                               ctypes.byref(out)))
+    return out.value
+
+
 class System:
     """nphc_system: the polynomial system of one XY ring (host-side handle)."""
 
@@ -257,6 +272,8 @@ class Result:
         out["index_hist"] = [int(v) for v in c[len(COUNT_NAMES):len(COUNT_NAMES) + self.system.M + 1]]
         base = len(COUNT_NAMES) + NPHC_MAX_N
         out.update({k: int(c[base + i]) for i, k in enumerate(EG_COUNT_NAMES)})
+        base += len(EG_COUNT_NAMES)
+        out.update({k: int(c[base + i]) for i, k in enumerate(TAIL_COUNT_NAMES)})
         return out
 
     def endgame(self) -> dict:

@@ -33,29 +33,25 @@ def certified_set(z, cls, classes):
     return z[np.isin(cls, classes)]
 
 
-def assert_same_point_sets(za, zb, rel=1e-10, extra=0):
-    """Every point of zb has a partner in za within rel (1 + |z|), and every point of za
-    one in zb except at most `extra` of them (za = GPU, zb = oracle)."""
-    assert len(zb) <= len(za) <= len(zb) + extra, (len(za), len(zb))
-    for z in zb:
-        if len(za) == 0:
-            raise AssertionError("empty GPU set")
+def assert_same_point_sets(za, zb, rel=1e-10):
+    """za (GPU) and zb (oracle) are the same set: equal sizes, and every point of zb has
+    its nearest point of za within rel (1 + |z|), each point of za the partner of exactly
+    one point of zb (a one-to-one matching)."""
+    assert len(za) == len(zb), (len(za), len(zb))
+    if len(zb) == 0:
+        return
+    partner = np.empty(len(zb), dtype=np.int64)
+    for k, z in enumerate(zb):
         d = np.linalg.norm(za - z, axis=1)
-        assert d.min() <= rel * (1 + np.linalg.norm(z)), d.min()
-    unmatched = 0
-    for z in za:
-        d = np.linalg.norm(zb - z, axis=1) if len(zb) else np.array([np.inf])
-        unmatched += d.min() > rel * (1 + np.linalg.norm(z))
-    assert unmatched <= extra, unmatched
+        partner[k] = int(d.argmin())
+        assert d[partner[k]] <= rel * (1 + np.linalg.norm(z)), d[partner[k]]
+    assert len(np.unique(partner)) == len(zb)
 
 
-def compare_with_oracle(N, sigma, gamma, prec, ref=None, extra=0):
+def compare_with_oracle(N, sigma, gamma, prec, ref=None):
     """Solve on the GPU and check: certified real and non-real sets equal the oracle's
-    (within 1e-10 relative), the real SPs carry the same theta, index and energy.  With
-    extra > 0 the GPU may hold up to `extra` certified solutions the oracle's paths
-    missed (rings with positive-dimensional families, N = 0 mod 4, where paths to the
-    singular families can jump): certification proves each extra a genuine isolated
-    nonsingular solution."""
+    (within 1e-10 relative, one to one), the real SPs carry the same theta, index and
+    energy."""
     N_ = nphc()
     system = N_.System(N, sigma)
     res = N_.solve(system, N_.options_default(gamma=gamma, precision=prec))
@@ -66,17 +62,13 @@ def compare_with_oracle(N, sigma, gamma, prec, ref=None, extra=0):
         ref = oracle_xy(N, float(sigma), float(np.real(gamma)), float(np.imag(gamma)))
     for cl_gpu, cl_or in ((N_.END_REAL, O.C_REAL), (N_.END_NONREAL, O.C_NONREAL)):
         assert_same_point_sets(certified_set(ep["z"], ep["cls"], [cl_gpu]),
-                               certified_set(ref["z"], ref["cls"], [cl_or]), extra=extra)
+                               certified_set(ref["z"], ref["cls"], [cl_or]))
     ref_th = np.array([s["theta"] for s in ref["sps"]]).reshape(len(ref["sps"]), N - 1)
-    assert len(ref_th) <= len(sps["theta"]) <= len(ref_th) + extra
-    misses = 0
+    assert len(ref_th) == len(sps["theta"])
     for th, ix, en, ld in zip(sps["theta"], sps["index"], sps["energy"], sps["log_abs_det"]):
         d = torus_dist(ref_th, th)
         k = int(d.argmin())
-        if d[k] >= 1e-9:
-            misses += 1
-            assert misses <= extra
-            continue
+        assert d[k] < 1e-9
         assert ref["sps"][k]["index"] == ix
         assert abs(ref["sps"][k]["energy"] - en) < 1e-10
         assert abs(ref["sps"][k]["log_abs_det"] - ld) < 1e-8 * (1 + abs(ld))

@@ -53,6 +53,26 @@ def test_disordered_couplings_builder(N_):
     assert np.allclose(J, B.ring_couplings(7, 1.2, g, 0.1), rtol=1e-15, atol=0)
 
 
+@pytest.mark.parametrize("disorder", [False, True])
+def test_couplings_vjp_is_the_sigma_derivative(N_, disorder):
+    """nphc_xy_couplings_vjp against central differences of nphc_xy_couplings in sigma,
+    for a random dL/dJ (diagonal ignored), with and without per-pair disorder."""
+    rng = np.random.default_rng(3)
+    N, sigma = 9, 1.3
+    g = None
+    if disorder:
+        g = rng.standard_normal((N, N))
+        g = np.triu(g, 1) + np.triu(g, 1).T
+    w = rng.standard_normal((N, N))
+    h = 1e-6
+    fd = float(((N_.xy_couplings(N, sigma + h, g, 0.1) - N_.xy_couplings(N, sigma - h, g, 0.1)) * w).sum()) / (2 * h)
+    got = N_.xy_couplings_vjp(N, sigma, w, g, 0.1)
+    assert abs(got - fd) < 1e-8 * (1 + abs(fd))
+    w0 = w.copy()
+    np.fill_diagonal(w0, 1e3)
+    assert N_.xy_couplings_vjp(N, sigma, w0, g, 0.1) == N_.xy_couplings_vjp(N, sigma, w - np.diag(np.diag(w)), g, 0.1)
+
+
 def test_invalid_arguments_are_reported(N_):
     for N in (2, 14):
         with pytest.raises(N_.NphcError) as ei:

@@ -22,11 +22,11 @@ def oracle_n10():
 
 def nearest_rel(za, zb):
     """For every point of za, the distance to its nearest point of zb relative to
-    1 + |z| (k-d tree on the real embedding)."""
+    1 + |z| (k-d tree on the real embedding), and that point's index."""
     from scipy.spatial import cKDTree
     emb = lambda z: np.concatenate([z.real, z.imag], axis=1)
-    d, _ = cKDTree(emb(zb)).query(emb(za), k=1)
-    return d / (1 + np.linalg.norm(za, axis=1))
+    d, j = cKDTree(emb(zb)).query(emb(za), k=1)
+    return d / (1 + np.linalg.norm(za, axis=1)), j
 
 
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
@@ -43,8 +43,9 @@ def test_parity_n10_workload(prec):
         za = ep["z"][ep["cls"] == cl_gpu]
         zb = ref["z"][ref["cls"] == cl_or]
         assert len(za) == len(zb), (cl_gpu, len(za), len(zb))
-        assert nearest_rel(za, zb).max() <= 1e-10
-        assert nearest_rel(zb, za).max() <= 1e-10
+        d, j = nearest_rel(zb, za)   # one to one: distinct partners within 1e-10
+        assert d.max() <= 1e-10
+        assert len(np.unique(j)) == len(zb)
     assert counts["duplicate"] == 0
     ref_th = np.array([s["theta"] for s in ref["sps"]]).reshape(len(ref["sps"]), inst.N - 1)
     assert len(sps["theta"]) == len(ref_th) == counts["real"]

@@ -106,6 +106,27 @@ def test_noalloc_dedup_smaller_set_after_larger(tracked):
         assert got[1] == ref[1] and got[2] == ref[2]
 
 
+def test_empty_set_clears_dup_count():
+    """No entries: both entry points still write *dup_count = 0 (the caller's sentinel
+    must not survive), whatever an earlier call left in the shared array."""
+    import torch
+    N_ = nphc()
+    system = N_.System(7, 1.5)
+    opts = N_.options_default()
+    ep = N_.DeviceEndpoints.empty(12, np.arange(0))
+    for noalloc in (True, False, True):
+        cnt = torch.full((1,), 12345, dtype=torch.int32, device="cuda")
+        lst = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+        if noalloc:
+            N_.dedup_noalloc(system, opts, ep, lst, cnt)
+        else:
+            ws = torch.zeros(max(1, system.workspace_size(0)), dtype=torch.uint8, device="cuda")
+            N_.dedup(system, opts, ep, ws, lst, cnt)
+        torch.cuda.synchronize()
+        assert int(cnt.item()) == 0
+        assert int(lst.item()) == -7   # the list is not written
+
+
 def test_noalloc_dedup_rejects_counts_beyond_the_limit():
     import torch
     N_ = nphc()
