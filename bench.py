@@ -11,9 +11,12 @@ Also reported on the same JSON line:
   e2e           the same metric through the C ABI with host buffers (system built from
                 host couplings, nphc_solve allocating and synchronising, stationary
                 points and counters copied back), every copy inside the timed region;
-  roofline      the FP32 path tracker (the dominant kernel): algorithmic FP32 flops per
-                launch over its CUDA-event duration, against the FP32 peak derived from
-                152 SMs x 128 lanes x 2 flops x 2.07 GHz;
+  roofline      the FP32 path tracker (the dominant kernel): the method's FP32 flops per
+                launch (structured solves and the corrector's residual as a plain
+                evaluation; the float-float overhead of the compensated residual reported
+                beside it) over its CUDA-event duration, against the FP32 FMA peak measured
+                in the same run (csrc/alu_peak.cu); fp64_tail: the FP64 continuation of the
+                FP32 pass's hand-offs against the measured FP64 FMA peak;
   cpu_baseline  the CPU oracle on a sample of the same paths, all host cores;
   plain_fp64    the same solve with every step in FP64 (the comparison the metric names);
   clocks        nvidia-smi samples taken during the timed region.
@@ -38,7 +41,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12     # derived: SMs x lanes x FMA x max clock
+NOMINAL_FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # SMs x lanes x FMA x max clock (context)
 METRIC = "certified paths/s at XY N=10 (262k paths), mixed-prec batched vs plain FP64"
 
 
@@ -119,23 +122,31 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
-def solve_flops(M: int, corrector: bool) -> float:
-    """Algorithmic FP32 flops of one structured solve as implemented (xy_solve.cuh):
-    Schur build, Householder QR, back substitution, recovery; the corrector adds the
-    second right-hand side and the compensated residual.  FMA = 2 flops; the error-free
-    transformations of the compensated residual are counted operation by operation
-    (two-product 3, two-sum 6, one float-float accumulate 11, with a low part 13)."""
-    Mf = float(M)
-    build = Mf * (43 * Mf + 115)
-    r = np.arange(M)
-    qr = float((16 * r * r + 34 * r + 24).sum())
-    back = 8 * Mf * (Mf - 1) / 2 + 3 * Mf
-    recover = 81 * Mf
-    f = build + qr + back + recover
+def solve_flops(M: int, corrector: bool) -> tuple[float, float]:
+    """FP32 flops of one structured solve of the per-thread tracker as implemented
+    (xy_solve.cuh, light-cone coordinates), as (method, overhead).  method: the Schur
+    build (couplings sums, -H_t rows, frames, M x M entries and right-hand sides), the
+    Householder QR, back substitution and recovery; a corrector solve adds the second
+    right-hand side and the residual -H counted as a plain evaluation.  overhead: what the
+    compensated (float-float) residual costs beyond that plain evaluation.  A complex
+    product is 6 flops, a complex sum 2, a complex times real 2, |z|^2 3, a square root or
+    reciprocal 1; one float-float accumulate is 10 (exact product 2, two-sum 6, two adds),
+    12 with a low part."""
+    nr = 2 if corrector else 1
+    column = M * (42 + 18 * (nr - 1)) + 219
+    build = M * column
+    qr = 0
+    for k in range(M):
+        n = M - k
+        qr += 10 + 4 * n + 6 * (n - 1) + (M - 1 - k + nr) * (16 * (n - 1) + 10)
+    back = sum(1 + 2 * nr + 8 * k * nr for k in range(M))
+    recover = M * (111 + 42 * (nr - 1))
+    method = float(build + qr + back + recover)
+    overhead = 0.0
     if corrector:
-        f += Mf * (18 * Mf + 30) + float((16 * r + 8).sum()) + back + 34 * Mf
-        f += Mf * (44 * Mf + 376)   # compensated residual
-    return f
+        method += M * (8 * M + 63)
+        overhead = float(M * (32 * M + 421))
+    return method, overhead
 
 
 def kernel_source_sha() -> str:
@@ -306,27 +317,79 @@ def run_mine(args):
     launches = counts["launches"] * args.steps
     value = replica_value(P, world, ms / 1e3)
 
+    # ---- measured FMA peaks (after the timed solves, so that their heat does not reach them)
+    from paper_1104_5497_gb300.peaks import alu_peak
+    p32, p64 = alu_peak(32), alu_peak(64)
+
+    def timed(fn):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
     # ---- the dominant kernel alone: FP32 tracker, CUDA events on the launching stream
     ep = nphc.DeviceEndpoints.empty(2 * M, np.arange(P))
     ws = torch.zeros(system.workspace_size(P), dtype=torch.uint8, device="cuda")
     nphc.track(system, opts, nphc.PREC_MIXED, ep, ws)
     torch.cuda.synchronize()
-    kt = []
-    for _ in range(max(3, args.steps)):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        nphc.track(system, opts, nphc.PREC_MIXED, ep, ws)
-        e1.record()
-        e1.synchronize()
-        kt.append(e0.elapsed_time(e1))
+    kt = [timed(lambda: nphc.track(system, opts, nphc.PREC_MIXED, ep, ws))
+          for _ in range(max(3, args.steps))]
     solves = int(ep.tensors["solves"].sum().item())
     newton = int(ep.tensors["newton"].sum().item())
-    flops = (solves - newton) * solve_flops(M, False) + newton * solve_flops(M, True)
+    fp_pred, fp_corr = solve_flops(M, False), solve_flops(M, True)
+    flops = (solves - newton) * fp_pred[0] + newton * fp_corr[0]
+    eft_flops = newton * fp_corr[1]
     k_ms = float(np.mean(kt))
     achieved = flops / (k_ms / 1e3) / 1e12
     traffic = profiled_traffic()
+
+    # ---- the FP64 continuation of the FP32 pass's hand-offs alone (one path per warp)
+    st = ep.tensors["status"]
+    hl = torch.nonzero((st == nphc.PATH_HANDOFF) | (st == nphc.PATH_HANDOFF_COND)).flatten().to(torch.int32)
+    hn = torch.tensor([hl.numel()], dtype=torch.int32, device="cuda")
+    saved = {k: v.clone() for k, v in ep.tensors.items()}
+
+    def restore():
+        for k, v in saved.items():
+            ep.tensors[k].copy_(v)
+    nphc.track(system, opts, nphc.PREC_FP64, ep, ws, hl, hn, resume=True)   # warm
+    restore()
+    torch.cuda.synchronize()
+    t64 = timed(lambda: nphc.track(system, opts, nphc.PREC_FP64, ep, ws, hl, hn, resume=True))
+    hidx = hl.long()
+    s64 = int((ep.tensors["solves"][hidx] - saved["solves"][hidx]).sum().item())
+    n64 = int((ep.tensors["newton"][hidx] - saved["newton"][hidx]).sum().item())
+    f64 = (s64 - n64) * fp_pred[0] + n64 * (fp_corr[0] + fp_corr[1])
+    del saved
+
+    # ---- what the condition test costs: the same solve without it
+    opts_nok = nphc.options_default(gamma=inst.gamma, precision=nphc.PREC_MIXED, kappa_fp32=0.0,
+                                    blocks_per_sm=opts.blocks_per_sm,
+                                    list_blocks_per_sm=opts.list_blocks_per_sm)
+    nphc.solve_into(system, opts_nok, res)
+    ms_nok = timed(lambda: nphc.solve_into(system, opts_nok, res))
+    nphc.solve_into(system, opts, res)   # leave the result of the benchmarked options
+    torch.cuda.synchronize()
+
+    # ---- the N = 12 ring (sigma = 1): 22 unknowns, 4,194,304 paths, same pipeline
+    n12 = None
+    if not args.no_n12:
+        i12 = inputs.workload_n12()
+        s12 = nphc.System(i12.N, i12.sigma)
+        o12 = nphc.options_default(gamma=i12.gamma, precision=nphc.PREC_MIXED)
+        r12 = nphc.Result(s12)
+        nphc.solve_into(s12, o12, r12)
+        ms12 = timed(lambda: nphc.solve_into(s12, o12, r12))
+        c12 = r12.counts()
+        n12 = {"workload": "XY power-law ring N=12, sigma=1 (seed 4): 22 unknowns, 4,194,304 paths",
+               "ms_per_step": ms12, "value": 4 ** (i12.N - 1) / (ms12 / 1e3), "unit": "paths/s",
+               "real": c12["real"], "nonreal": c12["nonreal"], "singular": c12["singular"],
+               "handoff": c12["handoff"]}
+        del r12, s12
 
     # ---- plain FP64 on the same workload (the metric's comparison)
     opts64 = nphc.options_default(gamma=inst.gamma, precision=nphc.PREC_FP64,
@@ -387,14 +450,29 @@ def run_mine(args):
                                                       and counts["index_hist"] == c64["index_hist"])},
                 "plain_fp64": {"value": P / (ms64 / 1e3), "unit": "paths/s", "ms_per_step": ms64,
                                "speedup_mixed_over_fp64": ms64 / ms},
+                "certified_per_s": {"solutions": (counts["real"] + counts["nonreal"]) / (ms / 1e3),
+                                    "real_sps": counts["real"] / (ms / 1e3)},
                 "e2e": {"value": replica_value(P, world, e2e_s), "unit": "paths/s",
                         "h2d_bytes_per_step": int(J_host.nbytes), "d2h_bytes_per_step": int(d2h)},
                 "roofline": {"bound": "alu", "kernel": "xy_track_kernel<9,float> (FP32 tracker)",
-                             "achieved": achieved, "peak": PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-                             "frac": achieved / PEAK_FP32_TFLOPS,
-                             "peak_note": "derived: 152 SM x 128 FP32 lanes x 2 x 2.07 GHz",
+                             "achieved": achieved, "peak": p32["tflops"], "unit": "TFLOP/s",
+                             "frac": achieved / p32["tflops"],
+                             "peak_note": "measured in this run: FP32 FMA microbenchmark (csrc/alu_peak.cu), "
+                                          f"nominal {NOMINAL_FP32_TFLOPS:.1f}",
                              "kernel_ms": k_ms, "flops_per_launch": flops,
+                             "flop_count": "method only: structured solves + plain residual evaluation",
+                             "eft_overhead_flops_per_launch": eft_flops,
+                             "frac_with_eft_overhead": (flops + eft_flops) / (k_ms / 1e3) / 1e12 / p32["tflops"],
                              "traffic": traffic},
+                "fp64_tail": {"kernel": "xy_track_warp64_kernel<9,4> (FP64 continuation of hand-offs)",
+                              "handoffs": int(hl.numel()), "ms": t64, "solves": s64,
+                              "achieved_tflops": f64 / (t64 / 1e3) / 1e12 if t64 > 0 else None,
+                              "peak_tflops": p64["tflops"], "peak_note": "measured FP64 FMA microbenchmark",
+                              "frac": (f64 / (t64 / 1e3) / 1e12) / p64["tflops"] if t64 > 0 else None},
+                "condition_test": {"kappa_fp32": opts.kappa_fp32, "handoffs": counts["handoff_cond"],
+                                   "ms_per_step_without": ms_nok},
+                "alu_peaks": {"fp32_tflops": p32["tflops"], "fp64_tflops": p64["tflops"]},
+                "n12": n12,
                 "cpu_baseline": cpu,
                 "oracle_parity": parity,
                 "gpu_launches": launches,
@@ -416,6 +494,7 @@ def main():
                     help="autotuned launch shapes instead of the defaults")
     ap.add_argument("--ref-paths", type=int, default=2048, help="oracle sample per reference step")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-n12", action="store_true", help="skip the N = 12 solve")
     ap.add_argument("--profile", action="store_true",
                     help="run only the timed solve loop (for profiler captures); no bench line")
     args = ap.parse_args()
