@@ -67,3 +67,56 @@ def test_autograd_sigma_gradient_matches_finite_differences():
         vals.append(tot)
     fd = (vals[0] - vals[1]) / (2 * h)
     assert abs(grad - fd) < 1e-6 * (1 + abs(fd)), (grad, fd)
+
+
+def test_n12_ground_state_and_lowest_saddle_gradients():
+    """The N = 12 ring at sigma = 1 (22 unknowns, 4,194,304 paths): the ground state and
+    the lowest index-1 saddle.  dE/dsigma (through ring_couplings) and dE/dJ_ij for every
+    pair (the adjoint) against central differences that follow each point by Newton's
+    method under the perturbed couplings, within 1e-6 relative (of the gradient's largest
+    entry); the ground state's gradient is zero (V = 0 at theta = 0 for every coupling)."""
+    import torch
+    from paper_1104_5497_gb300.autograd import ring_couplings, stationary_points
+    from sp_newton import grad_hess
+    nphc()
+    inst = I.workload_n12()
+    N = inst.N
+    sigma = torch.tensor(inst.sigma, dtype=torch.float64, device="cuda", requires_grad=True)
+    J = ring_couplings(N, sigma)
+    V, theta = stationary_points(J, inst.gamma)
+    assert len(V) >= 9297                     # a random-start search's lower bound
+    Vh, th = V.detach().cpu().numpy(), theta.detach().cpu().numpy()
+    J0 = O.couplings(N, inst.sigma)
+    order = np.argsort(Vh)
+    k0 = int(order[0])
+    assert abs(Vh[k0]) < 1e-12 and np.abs(np.angle(np.exp(1j * th[k0]))).max() < 1e-12
+    k1 = None
+    for k in order[1:]:
+        ev = np.linalg.eigvalsh(grad_hess(th[k], J0)[1])
+        if (ev < 0).sum() == 1:
+            k1 = int(k)
+            break
+    assert k1 is not None
+    iu = np.triu_indices(N, 1)
+    for k in (k0, k1):
+        gs, gJ = torch.autograd.grad(V[k], [sigma, J], retain_graph=True)
+        gs = float(gs)
+        gJ = gJ.cpu().numpy()[iu]
+        h = 1e-6
+
+        def e_at(Jp):
+            return energy(refine(th[k].copy(), Jp), Jp)
+        fd_s = (e_at(O.couplings(N, inst.sigma + h)) - e_at(O.couplings(N, inst.sigma - h))) / (2 * h)
+        fd_J = np.zeros(len(iu[0]))
+        for q, (i, j) in enumerate(zip(*iu)):
+            Jp, Jm = J0.copy(), J0.copy()
+            Jp[i, j] = Jp[j, i] = J0[i, j] + h
+            Jm[i, j] = Jm[j, i] = J0[i, j] - h
+            fd_J[q] = (e_at(Jp) - e_at(Jm)) / (2 * h)
+        if k == k0:
+            assert abs(gs) <= 1e-15 and np.abs(gJ).max() <= 1e-15
+            assert abs(fd_s) < 1e-9 and np.abs(fd_J).max() < 1e-9
+        else:
+            assert Vh[k] > 0
+            assert abs(gs - fd_s) <= 1e-6 * abs(fd_s), (gs, fd_s)
+            assert np.abs(gJ - fd_J).max() <= 1e-6 * np.abs(fd_J).max()
