@@ -391,6 +391,36 @@ def run_mine(args):
                "handoff": c12["handoff"]}
         del r12, s12
 
+    # ---- the 64-ring batch (N = 6..9, per-pair disorder, one gamma each; 1,847,296 paths)
+    batch = None
+    if not args.no_batch:
+        binst = inputs.workload_batch64()
+        bsys = [nphc.System(b.N, b.sigma, nphc.xy_couplings(b.N, b.sigma, b.g, b.eps)) for b in binst]
+        bopt = [nphc.options_default(gamma=b.gamma, precision=nphc.PREC_MIXED) for b in binst]
+        bpaths = sum(x.npaths for x in bsys)
+        B = nphc.Batch(bsys)
+        bt = {}
+        for name, kw in (("grouped", {}), ("grouped_graph", {"graph": True}),
+                         ("per_instance", {"per_instance": True})):
+            B.solve(bopt, **kw)
+            B.solve(bopt, **kw)   # (a graph is captured on the second solve)
+            torch.cuda.synchronize()
+            bt[name] = timed(lambda: B.solve(bopt, **kw))
+        bres = [nphc.Result(x) for x in bsys]
+
+        def singles():
+            for x, o, r in zip(bsys, bopt, bres):
+                nphc.solve_into(x, o, r)
+        singles()
+        bt["singles"] = timed(singles)
+        batch = {"workload": "64 disordered XY rings, N ~ U{6..9}, sigma ~ U[0.5, 3], J (1 + 0.1 g) per pair (seed 3)",
+                 "paths": bpaths, "value": bpaths / (bt["grouped"] / 1e3), "unit": "paths/s",
+                 "ms_per_step": bt["grouped"],
+                 "mode": "one FP32 launch per ring size over a global (instance, path) queue, eager",
+                 "grouped_graph_ms": bt["grouped_graph"], "per_instance_streams_ms": bt["per_instance"],
+                 "sum_of_single_solves_ms": bt["singles"]}
+        del B, bres
+
     # ---- plain FP64 on the same workload (the metric's comparison)
     opts64 = nphc.options_default(gamma=inst.gamma, precision=nphc.PREC_FP64,
                                   list_blocks_per_sm=opts.list_blocks_per_sm)
@@ -473,6 +503,7 @@ def run_mine(args):
                                    "ms_per_step_without": ms_nok},
                 "alu_peaks": {"fp32_tflops": p32["tflops"], "fp64_tflops": p64["tflops"]},
                 "n12": n12,
+                "batch64": batch,
                 "cpu_baseline": cpu,
                 "oracle_parity": parity,
                 "gpu_launches": launches,
@@ -495,6 +526,7 @@ def main():
     ap.add_argument("--ref-paths", type=int, default=2048, help="oracle sample per reference step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-n12", action="store_true", help="skip the N = 12 solve")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-ring batch")
     ap.add_argument("--profile", action="store_true",
                     help="run only the timed solve loop (for profiler captures); no bench line")
     args = ap.parse_args()

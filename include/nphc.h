@@ -430,28 +430,41 @@ nphc_status nphc_result_copy_endgame(const nphc_result *res, int64_t cap, int32_
 
 /* ---------------------------------------------------------------------------------
  * Batches: many independent systems solved together (the paper's method per system;
- * batching is a scheduling choice of this library).  Instance i runs the whole method
- * of nphc_solve_into on one of NPHC_BATCH_STREAMS internal streams, forked from and
- * joined back to the caller's stream with events, so that small systems fill the GPU
- * together; deduplication and classification stay per instance.
+ * batching is a scheduling choice of this library).  By default the XY rings of a batch
+ * are grouped by size, and each group's FP32 pass -- every path of every instance in it --
+ * is one persistent launch that pulls (instance, path) items from one queue, so that
+ * small rings fill the GPU together and no instance leaves a tail of idle SMs; the rest
+ * of each instance's method (hand-offs, FP64 continuation, refinement, certification,
+ * deduplication, classification) runs per instance on one of NPHC_BATCH_STREAMS internal
+ * streams once its group's pass is done.  A group runs that way when all its members are
+ * solved in mixed precision with the same FP32 step control (gamma and kappa_sing may
+ * differ); otherwise, and for generic quadratic systems, each instance runs the whole of
+ * nphc_solve_into on its stream.  Deduplication and classification stay per instance.
  * --------------------------------------------------------------------------------- */
 #define NPHC_BATCH_STREAMS 8
+#define NPHC_BATCH_GRAPH 1          /* nphc_batch_solve flag: capture / replay a CUDA graph */
+#define NPHC_BATCH_PER_INSTANCE 2   /* nphc_batch_solve flag: every instance runs the whole
+                                       solve on its stream (no group launches) */
 typedef struct nphc_batch nphc_batch;   /* opaque; owns one nphc_result per instance */
 
 /* A batch over systems[0 .. count-1] (borrowed: they must outlive the batch).  Creates
- * one result per instance (device memory as nphc_result_create) and the internal streams.
+ * one result per instance (device memory as nphc_result_create), the internal streams,
+ * and the device tables of the size groups (couplings rows, endpoint views, path offsets).
  * NPHC_EINVAL for count < 1 or a NULL system; NPHC_ENOMEM / NPHC_ECUDA on allocation. */
 nphc_status nphc_batch_create(int count, const nphc_system *const *systems, nphc_batch **out);
 
 /* Solves every instance with its options opts[i] (host array of count), asynchronously
  * on `stream`: the call returns once the work is enqueued; the caller's stream is
- * ordered after every instance.  graph = 0: eager launches.  graph != 0: the first solve
- * of the batch runs eagerly, the next one captures the whole batch (fork, every
- * instance's launches, join) into one CUDA graph in relaxed capture mode and launches
- * it, and later solves with the same options replay that graph (new options capture a
- * new one).  The caller must not capture `stream` itself around this call.
- * NPHC_EINVAL for NULL arguments or invalid options. */
-nphc_status nphc_batch_solve(nphc_batch *batch, const nphc_options *opts, int graph, void *stream);
+ * ordered after every instance.  flags: 0 = eager launches, grouped by size;
+ * NPHC_BATCH_GRAPH: the first solve of the batch runs eagerly, the next one captures the
+ * whole batch (fork, every launch, join) into one CUDA graph in relaxed capture mode and
+ * launches it, and later solves with the same options and flags replay that graph (new
+ * options capture a new one); NPHC_BATCH_PER_INSTANCE: no group launches.  When the
+ * options differ from the previous solve's, the call first waits for the batch's earlier
+ * work and rewrites the couplings table (a synchronous copy).  The caller must not
+ * capture `stream` itself around this call.  NPHC_EINVAL for NULL arguments, invalid
+ * options or unknown flags. */
+nphc_status nphc_batch_solve(nphc_batch *batch, const nphc_options *opts, int flags, void *stream);
 
 /* The result of instance i (borrowed; valid until nphc_batch_destroy).  Read it with
  * the nphc_result_* calls after the solve (they synchronise on the caller's stream). */

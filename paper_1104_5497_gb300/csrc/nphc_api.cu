@@ -744,8 +744,14 @@ nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
     return NPHC_OK;
 }
 
-nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_result *R,
-                            void *stream) {
+}  // extern "C"
+
+namespace {
+
+// The whole method into R on `stream`; with fp32_done the FP32 pass of a mixed-precision
+// solve has already run (a batch group's launch) and the pipeline starts after it.
+nphc_status solve_into_impl(const nphc_system *S, const nphc_options *o, nphc_result *R,
+                            void *stream, bool fp32_done) {
     if (!S || !R) return fail(NPHC_EINVAL, "NULL argument");
     if (R->P != S->npaths || R->N != S->N) return fail(NPHC_EINVAL, "result does not match system");
     nphc_status s;
@@ -792,7 +798,8 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
     }
     if (mixed) {
         // FP32 pass over every path
-        if ((s = track_impl(S, o, NPHC_PREC_MIXED, ep, nullptr, nullptr, false, false, R->ws, 0, st)))
+        if (!fp32_done &&
+            (s = track_impl(S, o, NPHC_PREC_MIXED, ep, nullptr, nullptr, false, false, R->ws, 0, st)))
             return s;
         // hand-offs: refinement at t = 1 straight from the hand-off point (certified ones
         // are done), then FP64 continuation of the others
@@ -869,6 +876,15 @@ nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_re
     R->solved = true;
     R->launches = nphc_launch_counter(0) - launches0;
     return NPHC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+nphc_status nphc_solve_into(const nphc_system *S, const nphc_options *o, nphc_result *R,
+                            void *stream) {
+    return solve_into_impl(S, o, R, stream, false);
 }
 
 nphc_status nphc_solve(const nphc_system *S, const nphc_options *o, void *stream, nphc_result **out) {
@@ -1117,16 +1133,34 @@ nphc_status nphc_dedup_noalloc(const nphc_system *S, const nphc_options *o,
 }  // extern "C"
 
 // ----------------------------------------------------------------- batch --
-// Independent systems solved together: instance i runs the whole method
-// (nphc_solve_into) on internal stream i % NPHC_BATCH_STREAMS, forked from the caller's
-// stream and joined back with events, so that small instances fill the GPU together.
-// The first solve of a batch runs eagerly (it also sets each kernel's attributes once);
-// with graph != 0 the second solve captures the whole fork / solve / join sequence into
-// one CUDA graph (relaxed capture mode), and later solves replay it.
+// Independent systems solved together.  Default mode: the instances are grouped by ring
+// size; each group's FP32 pass (every path of every instance in it) is one persistent
+// launch pulling (instance, path) items from one queue, on internal stream g % 8, and the
+// rest of each instance's method (hand-offs, FP64 continuation, refinement, certification,
+// dedup, classification) runs on internal stream i % NPHC_BATCH_STREAMS once its group's
+// pass is done.  NPHC_BATCH_PER_INSTANCE: every instance runs the whole of
+// nphc_solve_into on its stream.  Streams are forked from the caller's stream and joined
+// back with events.  The first solve of a batch runs eagerly (it also sets each kernel's
+// attributes once); with NPHC_BATCH_GRAPH the second solve captures the whole fork /
+// solve / join sequence into one CUDA graph (relaxed capture mode), and later solves with
+// the same options replay it.
 struct nphc_batch {
+    struct Group {
+        int M = 0;
+        std::vector<int> members;   // instance indices
+        int base = 0;               // first row of the group in the device tables
+        cudaEvent_t done = nullptr;
+    };
     std::vector<const nphc_system *> sys;
     std::vector<nphc_result *> res;
     std::vector<nphc_options> opts;   // options of the captured solve
+    std::vector<Group> groups;
+    void *tab = nullptr;              // device: XYSys[count] | EPView[count] | int64_t[count + groups]
+    XYSys *d_sys = nullptr;
+    EPView *d_ep = nullptr;
+    int64_t *d_off = nullptr;
+    std::vector<nphc_options> tab_opts;   // options the XYSys rows were written with
+    bool tab_valid = false;
     cudaStream_t streams[NPHC_BATCH_STREAMS] = {};
     cudaStream_t origin = nullptr;    // the captured stream (the caller's may be the legacy one)
     cudaEvent_t start = nullptr, done = nullptr;
@@ -1134,17 +1168,95 @@ struct nphc_batch {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int solves = 0;
+    int mode = -1;                    // flags of the captured solve
     int64_t launches = 0;
 };
 
 namespace {
 
-nphc_status batch_enqueue(nphc_batch *B, const nphc_options *opts, cudaStream_t st) {
+bool same_options(const std::vector<nphc_options> &a, const nphc_options *b) {
+    for (size_t i = 0; i < a.size(); i++)
+        if (std::memcmp(&a[i], &b[i], sizeof(nphc_options)) != 0) return false;
+    return true;
+}
+
+// A group's FP32 pass can be one launch when every member is an XY ring solved in mixed
+// precision with the same FP32 step control (gamma and kappa_sing live in each member's
+// couplings row).
+bool group_batchable(const nphc_batch *B, const nphc_batch::Group &G, const nphc_options *opts) {
+    const XYCtl c0 = make_ctl(&opts[G.members[0]], true, false, false);
+    for (int i : G.members) {
+        if (B->sys[i]->quad || opts[i].precision != NPHC_PREC_MIXED) return false;
+        const XYCtl c = make_ctl(&opts[i], true, false, false);
+        if (std::memcmp(&c, &c0, sizeof(XYCtl)) != 0) return false;
+        if (opts[i].blocks_per_sm != opts[G.members[0]].blocks_per_sm) return false;
+    }
+    return true;
+}
+
+// Writes every instance's couplings row (with its own gamma and kappa_sing) to the device
+// table when the options changed since the last write.  The rows are read by the group
+// launches of earlier solves, so every stream of the batch is drained first.
+nphc_status batch_tables(nphc_batch *B, const nphc_options *opts, cudaStream_t st) {
+    if (B->tab_valid && same_options(B->tab_opts, opts)) return NPHC_OK;
+    const size_t n = B->sys.size();
+    std::vector<XYSys> rows(n);
+    for (const auto &G : B->groups)
+        for (size_t r = 0; r < G.members.size(); r++) {
+            const int i = G.members[r];
+            rows[G.base + r] = sys_with_gamma(B->sys[i], &opts[i]);
+        }
+    NPHC_CK(cudaStreamSynchronize(st));
+    NPHC_CK(cudaStreamSynchronize(B->origin));
+    for (int k = 0; k < NPHC_BATCH_STREAMS; k++) NPHC_CK(cudaStreamSynchronize(B->streams[k]));
+    NPHC_CK(cudaMemcpy(B->d_sys, rows.data(), sizeof(XYSys) * n, cudaMemcpyHostToDevice));
+    B->tab_opts.assign(opts, opts + n);
+    B->tab_valid = true;
+    return NPHC_OK;
+}
+
+nphc_status batch_enqueue(nphc_batch *B, const nphc_options *opts, int mode, cudaStream_t st) {
     NPHC_CK(cudaEventRecord(B->fork, st));
     for (int k = 0; k < NPHC_BATCH_STREAMS; k++) NPHC_CK(cudaStreamWaitEvent(B->streams[k], B->fork, 0));
+    std::vector<int> group_of(B->sys.size(), -1);   // -1: the instance runs the whole solve
+    if (!(mode & NPHC_BATCH_PER_INSTANCE)) {
+        for (size_t g = 0; g < B->groups.size(); g++) {
+            const nphc_batch::Group &G = B->groups[g];
+            if (!group_batchable(B, G, opts)) continue;
+            nphc_result *R0 = B->res[G.members[0]];
+            const nphc_options *o0 = &opts[G.members[0]];
+            cudaStream_t gs = B->streams[g % NPHC_BATCH_STREAMS];
+            XYCtl ctl = make_ctl(o0, true, false, false);
+            WorkList wl;
+            wl.list = nullptr;
+            wl.list_count = nullptr;
+            wl.queue = ws_queue(R0->ws, 0);
+            wl.state = static_cast<char *>(R0->ws) + ws_layout(R0->n, 0).state;
+            wl.state_threads = NPHC_TRACK_MAX_THREADS;
+            BatchGroup bg;
+            bg.sys = B->d_sys + G.base;
+            bg.ep = B->d_ep + G.base;
+            bg.off = B->d_off + G.base + g;
+            bg.n = (int)G.members.size();
+            bg.total = 0;
+            for (int i : G.members) bg.total += B->sys[i]->npaths;
+            int grid = 0;
+            if (o0->blocks_per_sm > 0) {
+                int dev = 0, sms = 0;
+                NPHC_CK(cudaGetDevice(&dev));
+                NPHC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+                grid = sms * o0->blocks_per_sm;
+            }
+            NPHC_CK(cudaMemsetAsync(wl.queue, 0, sizeof(unsigned long long), gs));
+            NPHC_CK(launch_xy_track_f32_batch(G.M, bg, ctl, wl, grid, gs));
+            NPHC_CK(cudaEventRecord(G.done, gs));
+            for (int i : G.members) group_of[i] = (int)g;
+        }
+    }
     for (size_t i = 0; i < B->sys.size(); i++) {
-        nphc_status s = nphc_solve_into(B->sys[i], &opts[i], B->res[i],
-                                        B->streams[i % NPHC_BATCH_STREAMS]);
+        cudaStream_t is = B->streams[i % NPHC_BATCH_STREAMS];
+        if (group_of[i] >= 0) NPHC_CK(cudaStreamWaitEvent(is, B->groups[group_of[i]].done, 0));
+        nphc_status s = solve_into_impl(B->sys[i], &opts[i], B->res[i], is, group_of[i] >= 0);
         if (s != NPHC_OK) return s;
     }
     for (int k = 0; k < NPHC_BATCH_STREAMS; k++) {
@@ -1152,12 +1264,6 @@ nphc_status batch_enqueue(nphc_batch *B, const nphc_options *opts, cudaStream_t 
         NPHC_CK(cudaStreamWaitEvent(st, B->join[k], 0));
     }
     return NPHC_OK;
-}
-
-bool same_options(const std::vector<nphc_options> &a, const nphc_options *b) {
-    for (size_t i = 0; i < a.size(); i++)
-        if (std::memcmp(&a[i], &b[i], sizeof(nphc_options)) != 0) return false;
-    return true;
 }
 
 }  // namespace
@@ -1182,6 +1288,9 @@ void nphc_batch_destroy(nphc_batch *B) {
     }
     if (B->start) cudaEventDestroy(B->start);
     if (B->done) cudaEventDestroy(B->done);
+    for (auto &G : B->groups)
+        if (G.done) cudaEventDestroy(G.done);
+    if (B->tab) cudaFree(B->tab);
     for (nphc_result *R : B->res) nphc_result_destroy(R);
     delete B;
 }
@@ -1215,23 +1324,78 @@ nphc_status nphc_batch_create(int count, const nphc_system *const *systems, nphc
         B->sys.push_back(systems[i]);
         B->res.push_back(R);
     }
+    // groups of XY rings by size (generic quadratic systems always run alone)
+    for (int i = 0; i < count; i++) {
+        if (systems[i]->quad) continue;
+        auto it = std::find_if(B->groups.begin(), B->groups.end(),
+                               [&](const nphc_batch::Group &G) { return G.M == systems[i]->M; });
+        if (it == B->groups.end()) {
+            B->groups.emplace_back();
+            B->groups.back().M = systems[i]->M;
+            it = B->groups.end() - 1;
+        }
+        it->members.push_back(i);
+    }
+    int row = 0;
+    for (auto &G : B->groups) {
+        G.base = row;
+        row += (int)G.members.size();
+        if (cudaEventCreateWithFlags(&G.done, cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(NPHC_ECUDA, "batch events"));
+    }
+    // device tables: couplings rows (written per solve), endpoint views, path offsets
+    const size_t nrow = (size_t)(row > 0 ? row : 1), ng = B->groups.size();
+    const size_t b_sys = align256(sizeof(XYSys) * nrow), b_ep = align256(sizeof(EPView) * nrow);
+    const size_t b_off = align256(sizeof(int64_t) * (nrow + ng + 1));
+    cudaError_t e = cudaMalloc(&B->tab, b_sys + b_ep + b_off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(e == cudaErrorMemoryAllocation ? NPHC_ENOMEM : NPHC_ECUDA,
+                         std::string("batch tables: ") + cudaGetErrorString(e)));
+    }
+    B->d_sys = reinterpret_cast<XYSys *>(B->tab);
+    B->d_ep = reinterpret_cast<EPView *>(static_cast<char *>(B->tab) + b_sys);
+    B->d_off = reinterpret_cast<int64_t *>(static_cast<char *>(B->tab) + b_sys + b_ep);
+    std::vector<EPView> eps(nrow);
+    std::vector<int64_t> off;
+    for (const auto &G : B->groups) {
+        int64_t acc = 0;
+        for (size_t r = 0; r < G.members.size(); r++) {
+            const int i = G.members[r];
+            eps[G.base + r] = view(&B->res[i]->ep);
+            off.push_back(acc);
+            acc += systems[i]->npaths;
+        }
+        off.push_back(acc);   // group g's offsets start at row base + g
+    }
+    if (row > 0) {
+        e = cudaMemcpy(B->d_ep, eps.data(), sizeof(EPView) * row, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(B->d_off, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return bail(fail(NPHC_ECUDA, std::string("batch tables: ") + cudaGetErrorString(e)));
+    }
     *out = B;
     return NPHC_OK;
 }
 
-nphc_status nphc_batch_solve(nphc_batch *B, const nphc_options *opts, int graph, void *stream) {
+nphc_status nphc_batch_solve(nphc_batch *B, const nphc_options *opts, int flags, void *stream) {
     if (!B || !opts) return fail(NPHC_EINVAL, "NULL argument");
+    if (flags & ~(NPHC_BATCH_GRAPH | NPHC_BATCH_PER_INSTANCE)) return fail(NPHC_EINVAL, "unknown batch flags");
     for (size_t i = 0; i < B->sys.size(); i++) {
         nphc_status s = check_opt(&opts[i]);
         if (s != NPHC_OK) return s;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    if (B->exec && !same_options(B->opts, opts)) {   // new options: capture again
+    const int mode = flags & NPHC_BATCH_PER_INSTANCE;
+    if (B->exec && (!same_options(B->opts, opts) || B->mode != mode)) {   // capture again
         cudaGraphExecDestroy(B->exec);
         cudaGraphDestroy(B->graph);
         B->exec = nullptr;
         B->graph = nullptr;
     }
+    nphc_status s;
+    if (!mode && (s = batch_tables(B, opts, st)) != NPHC_OK) return s;
+    const bool graph = (flags & NPHC_BATCH_GRAPH) != 0;
     if (graph && B->exec) {
         NPHC_CK(cudaGraphLaunch(B->exec, st));
         nphc_launch_counter(B->launches);
@@ -1242,7 +1406,7 @@ nphc_status nphc_batch_solve(nphc_batch *B, const nphc_options *opts, int graph,
         NPHC_CK(cudaStreamSynchronize(B->origin));
         const int64_t l0 = nphc_launch_counter(0);
         NPHC_CK(cudaStreamBeginCapture(B->origin, cudaStreamCaptureModeRelaxed));
-        nphc_status s = batch_enqueue(B, opts, B->origin);
+        s = batch_enqueue(B, opts, mode, B->origin);
         cudaGraph_t g = nullptr;
         const cudaError_t e = cudaStreamEndCapture(B->origin, &g);
         if (s != NPHC_OK) {
@@ -1254,10 +1418,10 @@ nphc_status nphc_batch_solve(nphc_batch *B, const nphc_options *opts, int graph,
         NPHC_CK(cudaGraphInstantiate(&B->exec, g, 0));
         B->launches = nphc_launch_counter(0) - l0;
         B->opts.assign(opts, opts + B->sys.size());
+        B->mode = mode;
         NPHC_CK(cudaGraphLaunch(B->exec, st));
     } else {
-        nphc_status s = batch_enqueue(B, opts, st);
-        if (s != NPHC_OK) return s;
+        if ((s = batch_enqueue(B, opts, mode, st)) != NPHC_OK) return s;
     }
     for (nphc_result *R : B->res) R->stream = st;   // results are read after the join
     B->solves++;

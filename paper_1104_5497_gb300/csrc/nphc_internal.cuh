@@ -201,12 +201,25 @@ struct QSys {
     double kappa_sing;     // singular above kappa_sing max(1, ||z||_inf^2)
 };
 
+// One group of a batch: instances of one ring size whose FP32 pass runs as one launch
+// (device tables; off[g] = paths of instances 0 .. g-1 of the group, off[n] the total).
+struct BatchGroup {
+    const XYSys *sys;
+    const EPView *ep;
+    const int64_t *off;
+    int n;
+    int64_t total;   // off[n], on the host
+};
+
 // ------------------------------------------------------ kernel launchers --
 // Implemented per precision / ring size in the .cu files; return cudaGetLastError().
 cudaError_t launch_xy_track_f32(int M, const XYSys &sys, const XYCtl &ctl, const EPView &ep,
                                 const WorkList &wl, int block, int grid, cudaStream_t st);
 cudaError_t launch_xy_track_f64(int M, const XYSys &sys, const XYCtl &ctl, const EPView &ep,
                                 const WorkList &wl, int block, int grid, cudaStream_t st);
+// The FP32 pass over every path of a batch group (ring size M), one persistent launch.
+cudaError_t launch_xy_track_f32_batch(int M, const BatchGroup &bg, const XYCtl &ctl,
+                                      const WorkList &wl, int grid, cudaStream_t st);
 // FP64 tracking with one path per warp (xy_track_warp.cuh), for short lists.
 cudaError_t launch_xy_track_f64_warp(int M, const XYSys &sys, const XYCtl &ctl, const EPView &ep,
                                      const WorkList &wl, cudaStream_t st);

@@ -285,7 +285,7 @@ template <int NV>
 __global__ void __launch_bounds__(32)
     quad_track_kernel(const __grid_constant__ QSys S, const __grid_constant__ XYCtl C,
                       const EPView ep, const WorkList wl) {
-    track_body<QuadProblem<NV>>(S, C, ep, wl);
+    track_body<QuadProblem<NV>>(SingleSrc<QSys>{S, ep, wl}, C, wl);
 }
 
 template <int NV>

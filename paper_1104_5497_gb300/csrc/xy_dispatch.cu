@@ -9,6 +9,13 @@ cudaError_t launch_xy_track_f32(int M, const XYSys &sys, const XYCtl &ctl, const
 #undef C
 }
 
+cudaError_t launch_xy_track_f32_batch(int M, const BatchGroup &bg, const XYCtl &ctl,
+                                      const WorkList &wl, int grid, cudaStream_t st) {
+#define C(MM) case MM: return launch_xy_track_f32_batch_m##MM(bg, ctl, wl, grid, st);
+    switch (M) { NPHC_FOR_EACH_M(C) default: return cudaErrorInvalidValue; }
+#undef C
+}
+
 cudaError_t launch_xy_track_f64(int M, const XYSys &sys, const XYCtl &ctl, const EPView &ep,
                                 const WorkList &wl, int block, int grid, cudaStream_t st) {
     (void)block;

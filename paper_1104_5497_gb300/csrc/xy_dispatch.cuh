@@ -14,6 +14,8 @@
 #define NPHC_DECL(MM)                                                                         \
     cudaError_t launch_xy_track_f32_m##MM(const XYSys &, const XYCtl &, const EPView &,     \
                                           const WorkList &, int, cudaStream_t);              \
+    cudaError_t launch_xy_track_f32_batch_m##MM(const BatchGroup &, const XYCtl &,          \
+                                                const WorkList &, int, cudaStream_t);        \
     cudaError_t launch_xy_track_f64_m##MM(const XYSys &, const XYCtl &, const EPView &,     \
                                           const WorkList &, int, cudaStream_t);              \
     cudaError_t launch_xy_track_f64w_m##MM(const XYSys &, const XYCtl &, const EPView &,    \

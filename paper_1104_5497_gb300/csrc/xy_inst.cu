@@ -112,6 +112,41 @@ cudaError_t NPHC_FN(const XYSys &sys, const XYCtl &ctl, const EPView &ep, const 
     return cudaGetLastError();
 }
 
+#if NPHC_INST_KIND == 0
+// The FP32 pass of a batch group: one persistent grid over every path of the group's
+// instances (one queue), at most every SM filled.
+cudaError_t NPHC_CAT(launch_xy_track_f32_batch_m, NPHC_INST_M)(const BatchGroup &bg,
+                                                               const XYCtl &ctl,
+                                                               const WorkList &wl, int grid,
+                                                               cudaStream_t st) {
+    constexpr int M = NPHC_INST_M;
+    if (bg.total <= 0) return cudaSuccess;
+    const size_t smem = xy_smem_per_thread<M, RT>() * BLK;
+    auto k = xy_track_batch_kernel<M, RT, BLK>;
+    static bool attr_set = false;   // once per process for this instantiation
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, BLK, smem);
+    if (e != cudaSuccess) return e;
+    const int full = sms * (per > 0 ? per : 1);
+    if (grid <= 0 || grid > full) grid = full;
+    const int64_t need = (bg.total + BLK - 1) / BLK;   // no more threads than paths
+    if (grid > need) grid = (int)need;
+    const int cap = (int)(wl.state_threads / BLK);
+    if (grid > cap) grid = cap;
+    if (grid <= 0) return cudaErrorInvalidValue;
+    k<<<grid, BLK, smem, st>>>(bg.sys, bg.ep, bg.off, bg.n, ctl, wl);
+    nphc_launch_counter(1);
+    return cudaGetLastError();
+}
+#endif
+
 #elif NPHC_INST_KIND == 2
 #include "xy_endgame.cuh"
 

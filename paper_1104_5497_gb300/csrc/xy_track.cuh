@@ -210,9 +210,49 @@ constexpr size_t track_smem_per_thread() {
     return sizeof(cx<typename P::R>) * (size_t)(P::MD * (P::MD + 2) + P::NV);
 }
 
-template <class P>
-__device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl &C,
-                                           const EPView &ep, const WorkList &wl) {
+// Where a tracker's entries come from.  SingleSrc: one system and its endpoint arrays,
+// optionally through a work list.  BatchSrc: instances of one ring size (a batch), their
+// entries numbered one after another: item i of the launch's queue is entry i - off[g]
+// of instance g, off[g] <= i < off[g + 1], whose couplings and endpoint arrays are
+// sys[g] and ep[g] (device tables).
+template <class Sys>
+struct SingleSrc {
+    const Sys &S;
+    const EPView &ep;
+    const WorkList &wl;
+    __device__ __forceinline__ int64_t total() const { return worklist_size(wl, ep.count); }
+    __device__ __forceinline__ void take(int64_t i, int &g, int64_t &e) const {
+        g = 0;
+        e = worklist_entry(wl, i);
+    }
+    __device__ __forceinline__ const Sys &sys(int) const { return S; }
+    __device__ __forceinline__ const EPView &eps(int) const { return ep; }
+};
+
+template <class Sys>
+struct BatchSrc {
+    const Sys *__restrict__ S;
+    const EPView *__restrict__ ep;
+    const int64_t *__restrict__ off;   // [n + 1] prefix sums of the instances' path counts
+    int n;
+    __device__ __forceinline__ int64_t total() const { return off[n]; }
+    __device__ __forceinline__ void take(int64_t i, int &g, int64_t &e) const {
+        int lo = 0, hi = n - 1;   // the last g with off[g] <= i
+#pragma unroll 1
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= i) lo = mid;
+            else hi = mid - 1;
+        }
+        g = lo;
+        e = i - off[lo];
+    }
+    __device__ __forceinline__ const Sys &sys(int g) const { return S[g]; }
+    __device__ __forceinline__ const EPView &eps(int g) const { return ep[g]; }
+};
+
+template <class P, class Src>
+__device__ __forceinline__ void track_body(const Src &src, const XYCtl &C, const WorkList &wl) {
     using R = typename P::R;
     constexpr int BLOCK = P::BLOCK, NV = P::NV, MD = P::MD;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -229,8 +269,7 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
     const GVec<R> K1{st + (1 * NV) * nth + gtid, nth};       // dz/dt at Z0
     const GVec<R> AC{st + (2 * NV) * nth + gtid, nth};       // RK4 sum; next K1 in correction
     const GVec<R> CK{st + (3 * NV) * nth + gtid, nth};       // FP32 pass: hand-off checkpoint
-    const int64_t total = worklist_size(wl, ep.count);
-    const int64_t cnt = ep.count;
+    const int64_t total = src.total();
 
     // short lists: at most `lanes` paths per warp, so that the list spreads over every SM
     // instead of filling the first warps 32 at a time (FP64 continuation of a few
@@ -242,6 +281,7 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
         lanes = per < 1 ? 1 : (per > 32 ? 32 : (int)per);
     }
     int64_t e = (lane >= lanes) ? -2 : -1;   // entry index; -1 idle, -2 drained
+    int g = 0;                                // instance of the entry (batches)
     double t = 0.0, h = 0.0, hacc = 0.0;
     double tck = 0.0, hck = 0.0;   // checkpoint: the last clean accepted point with 1 - t < CRAWL_ZONE
     bool have_ck = false;
@@ -265,7 +305,8 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
             if (idle) {
                 const int64_t i = (int64_t)base + __popc(need & ((1u << lane) - 1u));
                 if (i < total) {
-                    e = worklist_entry(wl, i);
+                    src.take(i, g, e);
+                    const EPView &ep = src.eps(g);
                     status = NPHC_PATH_RUNNING;
                     run = 0;
                     rejects = 0;
@@ -284,7 +325,7 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                         newton = ep.newton[e];
                         need_k1 = true;
                     } else {
-                        P::start(S, ep.path[e], Z0, K1);
+                        P::start(src.sys(g), ep.path[e], Z0, K1);
                         t = 0.0;
                         h = C.h0;
                         steps = C.accumulate ? ep.steps[e] : 0;
@@ -353,9 +394,9 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                 }
             }
             const R tr = (R)te, omt = (R)(1.0 - te);
-            if (corr) P::residual(S, ZC, tr, omt, W1, w);
+            if (corr) P::residual(src.sys(g), ZC, tr, omt, W1, w);
             R kest = R(0);
-            const bool oks = P::solve(S, A, ZC, tr, omt, corr, W1, W1, AC, w, &kest);
+            const bool oks = P::solve(src.sys(g), A, ZC, tr, omt, corr, W1, W1, AC, w, &kest);
             if (!w) continue;
             solves++;
             kstep = fmax(kstep, kest);
@@ -494,6 +535,7 @@ __device__ __forceinline__ void track_body(const typename P::Sys &S, const XYCtl
                 status = C.handoff ? NPHC_PATH_HANDOFF : NPHC_PATH_STEP_BUDGET;
         }
         if (act && status != NPHC_PATH_RUNNING) {
+            const EPView &ep = src.eps(g);
             const bool handed = status == NPHC_PATH_HANDOFF || status == NPHC_PATH_HANDOFF_COND;
             const bool from_ck = handed && have_ck;
             if (from_ck)
@@ -515,5 +557,15 @@ template <int M, class R, int BLOCK>
 __global__ void __launch_bounds__(BLOCK)
     xy_track_kernel(const __grid_constant__ XYSys S, const __grid_constant__ XYCtl C,
                     const EPView ep, const WorkList wl) {
-    track_body<XYProblem<M, R, BLOCK>>(S, C, ep, wl);
+    track_body<XYProblem<M, R, BLOCK>>(SingleSrc<XYSys>{S, ep, wl}, C, wl);
+}
+
+// The FP32 pass of a batch: every path of every instance of one ring size in one
+// persistent launch, pulled from one queue (BatchSrc).
+template <int M, class R, int BLOCK>
+__global__ void __launch_bounds__(BLOCK)
+    xy_track_batch_kernel(const XYSys *__restrict__ sys, const EPView *__restrict__ eps,
+                          const int64_t *__restrict__ off, int n,
+                          const __grid_constant__ XYCtl C, const WorkList wl) {
+    track_body<XYProblem<M, R, BLOCK>>(BatchSrc<XYSys>{sys, eps, off, n}, C, wl);
 }

@@ -32,6 +32,7 @@ NCOUNTS = len(COUNT_NAMES) + NPHC_MAX_N + len(EG_COUNT_NAMES) + len(TAIL_COUNT_N
 EG_NONE, EG_CONVERGED, EG_NOT_CLOSED, EG_NOT_CONVERGED, EG_TRACK_FAILED, EG_DIVERGED, \
     EG_AT_INFINITY = range(7)
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "EBUDGET", 5: "ESTATE"}
+BATCH_GRAPH, BATCH_PER_INSTANCE = 1, 2   # nphc_batch_solve flags
 
 
 class NphcError(RuntimeError):
@@ -329,10 +330,13 @@ class Batch:
         _check("nphc_batch_create", lib().nphc_batch_create(len(self.systems), arr, ctypes.byref(h)))
         self.handle = h
 
-    def solve(self, opts, graph: bool = False, stream=None) -> None:
-        """nphc_batch_solve: opts is one nphc_options per instance."""
+    def solve(self, opts, graph: bool = False, per_instance: bool = False, stream=None) -> None:
+        """nphc_batch_solve: opts is one nphc_options per instance; graph captures / replays a
+        CUDA graph (NPHC_BATCH_GRAPH); per_instance runs every instance's whole solve on its
+        stream instead of one FP32 launch per ring size (NPHC_BATCH_PER_INSTANCE)."""
         arr = (nphc_options * len(self.systems))(*opts)
-        _check("nphc_batch_solve", lib().nphc_batch_solve(self.handle, arr, int(bool(graph)),
+        flags = (BATCH_GRAPH if graph else 0) | (BATCH_PER_INSTANCE if per_instance else 0)
+        _check("nphc_batch_solve", lib().nphc_batch_solve(self.handle, arr, flags,
                                                          _stream_ptr(stream)))
 
     def result(self, i: int) -> Result:

@@ -1,12 +1,13 @@
 """Batches of independent systems (nphc_batch_*): the 64-instance disordered workload
-(N = 6..9, one gamma per instance) solved together, eagerly and through one captured CUDA
-graph, gives every instance the same results as solving it alone; a subset is checked
-against the oracle."""
+(N = 6..9, one gamma per instance) solved together -- one FP32 launch per ring size over a
+global (instance, path) queue, or every instance on its own stream -- eagerly and through
+one captured CUDA graph, gives every instance the same results as solving it alone;
+every instance with N <= 7 is checked against the oracle point by point."""
 import numpy as np
 import pytest
 
 import oracle as O
-from gpu_common import nphc
+from gpu_common import assert_same_point_sets, certified_set, nphc
 from paper_1104_5497_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -24,7 +25,8 @@ def certified(res, N_):
     return z[np.lexsort(np.round(np.concatenate([z.real, z.imag], axis=1).T, 8))]
 
 
-def test_batch64_matches_single_solves_and_graph_replays():
+@pytest.mark.parametrize("per_instance", [False, True])
+def test_batch64_matches_single_solves_and_graph_replays(per_instance):
     N_ = nphc()
     insts = I.workload_batch64()
     assert len(insts) == 64
@@ -32,8 +34,8 @@ def test_batch64_matches_single_solves_and_graph_replays():
     opts = [N_.options_default(gamma=inst.gamma) for inst in insts]
     batch = N_.Batch(systems)
     for mode in ("eager", "capture", "replay"):
-        batch.solve(opts, graph=(mode != "eager"))
-        for i in (0, 5, 17, 33, 63):
+        batch.solve(opts, graph=(mode != "eager"), per_instance=per_instance)
+        for i in (0, 5, 17, 33, 40, 63):
             single = N_.solve(systems[i], opts[i])
             a, b = batch.result(i).counts(), single.counts()
             for k in ("paths", "real", "nonreal", "duplicate", "index_hist"):
@@ -44,16 +46,23 @@ def test_batch64_matches_single_solves_and_graph_replays():
 
 
 def test_batch_instances_match_the_oracle():
+    """Every instance of the 64-ring workload with N <= 7 (27 rings, grouped launches
+    and a captured graph): the certified real and non-real sets equal the oracle's, one to
+    one within 1e-10 relative."""
     N_ = nphc()
-    insts = [inst for inst in I.workload_batch64() if inst.N <= 7][:4]
+    insts = [inst for inst in I.workload_batch64() if inst.N <= 7]
+    assert len(insts) >= 20
     systems = [instance_system(N_, inst) for inst in insts]
+    opts = [N_.options_default(gamma=inst.gamma) for inst in insts]
     batch = N_.Batch(systems)
-    batch.solve([N_.options_default(gamma=inst.gamma) for inst in insts], graph=True)
+    batch.solve(opts)
+    batch.solve(opts, graph=True)
     for i, inst in enumerate(insts):
         ref = O.solve_xy(inst.N, inst.sigma, inst.gamma, g=inst.g, eps=inst.eps)
-        c = batch.result(i).counts()
-        assert c["real"] == (ref["cls"] == O.C_REAL).sum()
-        assert c["nonreal"] == (ref["cls"] == O.C_NONREAL).sum()
+        ep = batch.result(i).endpoints()
+        for cl_gpu, cl_or in ((N_.END_REAL, O.C_REAL), (N_.END_NONREAL, O.C_NONREAL)):
+            assert_same_point_sets(certified_set(ep["z"], ep["cls"], [cl_gpu]),
+                                   certified_set(ref["z"], ref["cls"], [cl_or]))
 
 
 def test_batch_with_endgame_matches_single_solves():
