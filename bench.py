@@ -271,14 +271,18 @@ def run_mine(args):
     M = inst.N - 1
     system = nphc.System(inst.N, inst.sigma)
     opts = nphc.options_default(gamma=inst.gamma, precision=nphc.PREC_MIXED)
+    opts_default = opts
     tuned = {"autotuned": False}
-    if args.autotune:   # launch shapes per (N, GPU), outside every timed region
+    if not args.no_autotune:   # per (N, GPU), outside every timed region
         from paper_1104_5497_gb300 import autotune
-        # a profiler run launches nothing extra: it takes the cached shapes of an earlier
+        # a profiler run launches nothing extra: it takes the cached choice of an earlier
         # run, or the defaults
         opts, rep_ = autotune.tune(system, opts, measure=not args.profile)
-        tuned = {"autotuned": True, "blocks_per_sm": rep_["blocks_per_sm"],
-                 "list_blocks_per_sm": rep_["list_blocks_per_sm"], "cached": rep_["cached"]}
+        tuned = {"autotuned": True, "cached": rep_["cached"]}
+        for k in ("blocks_per_sm", "list_blocks_per_sm", "threads_per_path", "max_newton_fp32",
+                  "eps_fp32", "step_gate"):
+            if k in rep_:
+                tuned[k] = rep_[k]
     res = nphc.Result(system)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -366,10 +370,18 @@ def run_mine(args):
     f64 = (s64 - n64) * fp_pred[0] + n64 * (fp_corr[0] + fp_corr[1])
     del saved
 
+    # ---- the same solve with the library's default options (no autotuning)
+    ms_untuned = None
+    if tuned["autotuned"]:
+        nphc.solve_into(system, opts_default, res)
+        ms_untuned = float(np.mean([timed(lambda: nphc.solve_into(system, opts_default, res))
+                                    for _ in range(3)]))
+
     # ---- what the condition test costs: the same solve without it
-    opts_nok = nphc.options_default(gamma=inst.gamma, precision=nphc.PREC_MIXED, kappa_fp32=0.0,
-                                    blocks_per_sm=opts.blocks_per_sm,
-                                    list_blocks_per_sm=opts.list_blocks_per_sm)
+    import ctypes
+    opts_nok = nphc.nphc_options()
+    ctypes.memmove(ctypes.byref(opts_nok), ctypes.byref(opts), ctypes.sizeof(opts_nok))
+    opts_nok.kappa_fp32 = 0.0
     nphc.solve_into(system, opts_nok, res)
     ms_nok = timed(lambda: nphc.solve_into(system, opts_nok, res))
     nphc.solve_into(system, opts, res)   # leave the result of the benchmarked options
@@ -440,20 +452,24 @@ def run_mine(args):
 
     # ---- end to end through the C ABI with host buffers
     J_host = nphc.xy_couplings(inst.N, inst.sigma)
-    e2e_t, d2h = [], 0
-    for k in range(args.warmup + args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        s2 = nphc.System(inst.N, inst.sigma, J_host)
-        r2 = nphc.solve(s2, opts)
-        sps = r2.stationary_points()
-        c2 = r2.counts()
-        del r2, s2
-        torch.cuda.synchronize()
-        if k >= args.warmup:
-            e2e_t.append(time.perf_counter() - t0)
-        d2h = sum(v.nbytes for v in sps.values()) + 8 * nphc.NCOUNTS
-    e2e_s = max_over_ranks(float(np.mean(e2e_t)), world)
+
+    def e2e(o):
+        ts, d2h = [], 0
+        for k in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s2 = nphc.System(inst.N, inst.sigma, J_host)
+            r2 = nphc.solve(s2, o)
+            sps = r2.stationary_points()
+            r2.counts()
+            del r2, s2
+            torch.cuda.synchronize()
+            if k >= args.warmup:
+                ts.append(time.perf_counter() - t0)
+            d2h = sum(v.nbytes for v in sps.values()) + 8 * nphc.NCOUNTS
+        return max_over_ranks(float(np.mean(ts)), world), d2h
+    e2e_s, d2h = e2e(opts)
+    e2e_untuned = e2e(opts_default)[0] if tuned["autotuned"] else None
 
     # ---- CPU oracle on a sample of the same workload (rank 0, N = 1 only)
     cpu, parity = None, None
@@ -483,7 +499,10 @@ def run_mine(args):
                 "certified_per_s": {"solutions": (counts["real"] + counts["nonreal"]) / (ms / 1e3),
                                     "real_sps": counts["real"] / (ms / 1e3)},
                 "e2e": {"value": replica_value(P, world, e2e_s), "unit": "paths/s",
-                        "h2d_bytes_per_step": int(J_host.nbytes), "d2h_bytes_per_step": int(d2h)},
+                        "h2d_bytes_per_step": int(J_host.nbytes), "d2h_bytes_per_step": int(d2h),
+                        "untuned_value": (replica_value(P, world, e2e_untuned)
+                                          if e2e_untuned else None)},
+                "untuned_ms_per_step": ms_untuned,
                 "roofline": {"bound": "alu", "kernel": "xy_track_kernel<9,float> (FP32 tracker)",
                              "achieved": achieved, "peak": p32["tflops"], "unit": "TFLOP/s",
                              "frac": achieved / p32["tflops"],
@@ -521,8 +540,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--cpu-paths", type=int, default=8192, help="oracle sample for cpu_baseline")
-    ap.add_argument("--autotune", action="store_true",
-                    help="autotuned launch shapes instead of the defaults")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="the library's default options instead of the autotuned ones")
     ap.add_argument("--ref-paths", type=int, default=2048, help="oracle sample per reference step")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-n12", action="store_true", help="skip the N = 12 solve")

@@ -1,22 +1,27 @@
-"""Autotuner for the launch shapes of the two tracking kernels, per (ring size, GPU).
+"""Autotuner for the trackers, per (ring size, GPU): launch shapes, threads per path of
+the FP64 lists, and the FP32 pass's step-control constants.
 
-It times the kernels on a calibration sample of the ring's own paths: the FP32 tracker over
-its resident blocks per SM (`nphc_options.blocks_per_sm`), then the FP64 list tracker over
-the sample's hand-offs at 1 to 4 blocks per SM (`list_blocks_per_sm`).  Only knobs that
-leave every path's arithmetic unchanged are searched.  A path's computation does not
-depend on the thread or SM that runs it, so a tuned solve gives the same endpoints, bit
-for bit.  The step-control constants keep their defaults: they decide which paths jump,
-and with that the re-tracking work, and the oracle uses the same values.  The result is
-cached in a JSON file under a key made of N, the GPU's name and its SM count.
+Stage 1 (scheduling: every path's arithmetic is unchanged, so a tuned solve gives the
+same endpoints bit for bit): the FP32 tracker over its resident blocks per SM
+(`nphc_options.blocks_per_sm`), then the FP64 continuation of the sample's hand-offs with
+one path per warp at 1 to 4 blocks per SM (`list_blocks_per_sm`).
+
+Stage 2 (gated by parity): the FP64 lists' threads per path (`threads_per_path`: one path
+per warp in (x, y), or one per thread in light-cone coordinates, whose rounding differs)
+and the FP32 pass's step control, the corrector's iteration cap (`max_newton_fp32`) and
+tolerance (`eps_fp32`), which decide which steps it accepts and which paths it hands to
+FP64.  Each candidate runs the calibration sample through the FP32 pass, the FP64
+continuation of its hand-offs and the certification, and is kept only if every sample
+path ends with the class it has under the options as given and every certified endpoint
+equals theirs within 1e-10 relative; among those the fastest wins.  With the default
+sample (every path up to N = 10) the gate covers the whole ring.
 
 The list tracker's best shape depends on how long the hand-off list is, so the sample
-must reproduce it: by default it is every path up to N = 10 (262,144).  On the N = 10
-ring a 65,536-path sample (241 hand-offs) preferred one block per SM, which is slower on
-the whole ring's 1,565 hand-offs than the default two (186.5 ms against 183.4 ms per
-solve).
+must reproduce it: by default it is every path up to N = 10 (262,144).  The result is
+cached in a JSON file under a key made of N, the GPU's name and its SM count.
 
-Every step runs through the C ABI (nphc_track on caller-owned device buffers); this
-module only chooses options and times calls with CUDA events.
+Every step runs through the C ABI (nphc_track, nphc_refine_certify on caller-owned device
+buffers); this module only chooses options and times calls with CUDA events.
 """
 from __future__ import annotations
 
@@ -30,6 +35,9 @@ from . import nphc as N_
 
 FP32_CANDIDATES = (0, 7, 6, 5, 4)   # resident blocks per SM; 0 = the occupancy maximum
 LIST_CANDIDATES = (2, 1, 3, 4)      # blocks of 4 warps per SM (the default, 2, first)
+# FP32 step control: (max_newton_fp32, eps_fp32); the defaults first
+STEP_CANDIDATES = ((3, 1e-5), (2, 1e-5), (3, 3e-5), (2, 3e-5))
+THREADS_PER_PATH = (0, 32, 1)       # FP64 lists; 0 = the library's automatic choice
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
@@ -72,12 +80,29 @@ def store_cache(path: str, key: str, entry: dict) -> None:
 
 
 def apply(opts, entry: dict):
-    """A copy of opts with the tuned launch shapes."""
+    """A copy of opts with the tuned values (the keys entry has)."""
     o = N_.nphc_options()
     ctypes.memmove(ctypes.byref(o), ctypes.byref(opts), ctypes.sizeof(o))
     o.blocks_per_sm = int(entry["blocks_per_sm"])
     o.list_blocks_per_sm = int(entry["list_blocks_per_sm"])
+    if "threads_per_path" in entry:
+        o.threads_per_path = int(entry["threads_per_path"])
+    if "max_newton_fp32" in entry:
+        o.max_newton_fp32 = int(entry["max_newton_fp32"])
+        o.eps_fp32 = float(entry["eps_fp32"])
     return o
+
+
+def same_certified(a: dict, b: dict, rel: float = 1e-10) -> bool:
+    """Two runs of the calibration sample agree: every path has the same class, and every
+    certified endpoint the same value within rel (1 + |z|)."""
+    if not np.array_equal(a["cls"], b["cls"]):
+        return False
+    c = np.isin(a["cls"], [N_.END_REAL, N_.END_NONREAL, N_.END_UNDECIDED])
+    if not c.any():
+        return True
+    d = np.abs(a["z"][c] - b["z"][c]).max(axis=1)
+    return bool((d <= rel * (1 + np.abs(b["z"][c]).max(axis=1))).all())
 
 
 def _median_ms(fn, reps: int) -> float:
@@ -138,7 +163,7 @@ def tune(system, opts, sample: int = 262144, reps: int = 3, cache: str | None = 
                 ep.tensors[k].copy_(v)
 
         for lb in LIST_CANDIDATES:
-            ol = apply(opts, dict(blocks_per_sm=bps32, list_blocks_per_sm=lb))
+            ol = apply(opts, dict(blocks_per_sm=bps32, list_blocks_per_sm=lb, threads_per_path=32))
             run = lambda: N_.track(system, ol, N_.PREC_FP64, ep, ws, ho, count, resume=True)
             restore()
             run()                                      # warm-up
@@ -150,10 +175,44 @@ def tune(system, opts, sample: int = 262144, reps: int = 3, cache: str | None = 
             lists[lb] = float(np.median(ts))
         restore()
     lb = pick(lists) if lists else 0
-    entry = dict(blocks_per_sm=bps32, list_blocks_per_sm=lb, sample=int(ep.count),
-                 handoffs=int(ho.numel()),
+    shapes = dict(blocks_per_sm=bps32, list_blocks_per_sm=lb)
+
+    # stage 2: threads per path and FP32 step control, each candidate gated on the
+    # certified sample of the options as given
+    def sample_run(o):
+        N_.track(system, o, N_.PREC_MIXED, ep, ws)
+        s32 = ep.tensors["status"]
+        h = torch.nonzero((s32 == N_.PATH_HANDOFF) | (s32 == N_.PATH_HANDOFF_COND)).flatten().to(torch.int32)
+        if h.numel() > 0:
+            n = torch.tensor([h.numel()], dtype=torch.int32, device="cuda")
+            N_.track(system, o, N_.PREC_FP64, ep, ws, h, n, resume=True)
+
+    cands = [(opts.threads_per_path, opts.max_newton_fp32, opts.eps_fp32)]   # as given: the reference
+    cands += [(t, mn, eps) for t in THREADS_PER_PATH for mn, eps in STEP_CANDIDATES
+              if (t, mn, eps) != cands[0]]
+    steps, gate = {}, {}
+    ref = None
+    for tpp, mn, eps in cands:
+        o = apply(opts, dict(shapes, threads_per_path=tpp, max_newton_fp32=mn, eps_fp32=eps))
+        sample_run(o)                                  # warm-up
+        steps[(tpp, mn, eps)] = _median_ms(lambda: sample_run(o), reps)
+        sample_run(o)
+        N_.refine_certify(system, o, ep)
+        torch.cuda.synchronize()
+        got = dict(cls=ep.tensors["cls"].cpu().numpy(),
+                   z=(ep.tensors["z_re"] + 1j * ep.tensors["z_im"]).cpu().numpy().T)
+        if ref is None:
+            ref = got
+        gate[(tpp, mn, eps)] = same_certified(got, ref)
+    ok = [k for k in cands if gate[k]]
+    tpp, mn, eps = min(ok, key=lambda k: (steps[k], cands.index(k)))
+    key_s = lambda k: f"{k[0]},{k[1]},{k[2]:g}"
+    entry = dict(shapes, threads_per_path=tpp, max_newton_fp32=mn, eps_fp32=eps,
+                 sample=int(ep.count), handoffs=int(ho.numel()),
                  fp32_ms={str(k): v for k, v in fp32.items()},
-                 list_ms={str(k): v for k, v in lists.items()})
+                 list_ms={str(k): v for k, v in lists.items()},
+                 step_ms={key_s(k): v for k, v in steps.items()},
+                 step_gate={key_s(k): bool(v) for k, v in gate.items()})
     if cache:
         store_cache(cache, key, entry)
     return apply(opts, entry), dict(entry, key=key, cached=False)

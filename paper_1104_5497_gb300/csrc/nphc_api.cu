@@ -159,6 +159,7 @@ nphc_status nphc_options_default(nphc_options *o) {
     o->block_size = 0;
     o->blocks_per_sm = 0;
     o->kappa_sing = 1e12;
+    o->threads_per_path = 0;
     o->kappa_fp32 = 1e6;
     return NPHC_OK;
 }
@@ -373,7 +374,8 @@ nphc_status check_opt(const nphc_options *o) {
           o->eg_tol_close > 0.0 && o->eg_tol_conv > 0.0 && o->eg_h_min > 0.0 &&
           o->eg_max_attempts > 0))
         return fail(NPHC_EINVAL, "endgame options out of range");
-    if (o->blocks_per_sm < 0 || o->list_blocks_per_sm < 0 || o->block_size < 0)
+    if (o->blocks_per_sm < 0 || o->list_blocks_per_sm < 0 || o->block_size < 0 ||
+        !(o->threads_per_path == 0 || o->threads_per_path == 1 || o->threads_per_path == 32))
         return fail(NPHC_EINVAL, "launch options out of range");
     return NPHC_OK;
 }
@@ -464,8 +466,11 @@ nphc_status track_impl(const nphc_system *S, const nphc_options *o, nphc_precisi
     const EPView v = view(ep);
     if (S->quad)
         NPHC_CK(launch_quad_track(S->n, quad_with_gamma(S, o), ctl, v, wl, 0, st));
-    else if (!f32 && list != nullptr)   // short FP64 lists: one path per warp
+    else if (!f32 && list != nullptr &&
+             (o->threads_per_path == 32 || (o->threads_per_path == 0 && S->N < 12)))   // one path per warp
         NPHC_CK(launch_xy_track_f64_warp_bps(S->M, xs, ctl, v, wl, o->list_blocks_per_sm, st));
+    else if (!f32 && list != nullptr)   // FP64 lists, one path per thread, full warps
+        NPHC_CK(launch_xy_track_f64(S->M, xs, ctl, v, wl, 0, 0, st));
     else if (f32)
         NPHC_CK(launch_xy_track_f32(S->M, xs, ctl, v, wl, 0, grid, st));
     else

@@ -61,7 +61,8 @@ class nphc_options(ctypes.Structure):
                 ("eg_tol_close", ctypes.c_double), ("eg_tol_conv", ctypes.c_double),
                 ("eg_h_min", ctypes.c_double), ("eg_max_attempts", ctypes.c_int),
                 ("list_blocks_per_sm", ctypes.c_int),
-                ("kappa_sing", ctypes.c_double), ("kappa_fp32", ctypes.c_double)]
+                ("kappa_sing", ctypes.c_double), ("threads_per_path", ctypes.c_int),
+                ("kappa_fp32", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p

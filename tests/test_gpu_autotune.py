@@ -1,6 +1,8 @@
-"""The autotuner on the GPU: it picks launch shapes among its candidates, a solve with them
-gives the endpoints of the default shapes bit for bit (the knobs are scheduling only),
-and the second call is served from the cache without launching anything."""
+"""The autotuner on the GPU: it picks launch shapes among its candidates, a solve with other
+shapes gives the endpoints of the default shapes bit for bit (the knobs are scheduling
+only); the step-control constants it picks pass its parity gate, and a solve with the
+tuned options gives the default options' certified set; the second call is served from
+the cache without launching anything."""
 import numpy as np
 import pytest
 
@@ -17,13 +19,22 @@ def test_tuned_shapes_change_no_result(tmp_path):
     system = N_.System(inst.N, inst.sigma)
     opts = N_.options_default(gamma=inst.gamma)
     cache = str(tmp_path / "autotune.json")
-    tuned, rep = A.tune(system, opts, sample=4096, reps=1, cache=cache)
+    tuned, rep = A.tune(system, opts, sample=system.npaths, reps=1, cache=cache)
     assert not rep["cached"]
     assert rep["blocks_per_sm"] in A.FP32_CANDIDATES
     assert rep["list_blocks_per_sm"] in A.LIST_CANDIDATES + (0,)
+    assert rep["threads_per_path"] in A.THREADS_PER_PATH
     assert set(rep["fp32_ms"]) == {str(c) for c in A.FP32_CANDIDATES}
+    assert (rep["max_newton_fp32"], rep["eps_fp32"]) in A.STEP_CANDIDATES
+    assert rep["step_gate"][f"{rep['threads_per_path']},{rep['max_newton_fp32']},{rep['eps_fp32']:g}"]
     # every other option is untouched
     assert (tuned.tol_sol, tuned.h_max, tuned.gamma_re) == (opts.tol_sol, opts.h_max, opts.gamma_re)
+    # the tuned solve certifies the default solve's set (the gate covered every path)
+    a, b = N_.solve(system, opts), N_.solve(system, tuned)
+    ea, eb = a.endpoints(), b.endpoints()
+    assert np.array_equal(ea["cls"], eb["cls"])
+    c = np.isin(ea["cls"], [N_.END_REAL, N_.END_NONREAL])
+    assert np.abs(ea["z"][c] - eb["z"][c]).max() <= 1e-10 * (1 + np.abs(ea["z"][c]).max())
     for shape in (dict(blocks_per_sm=4, list_blocks_per_sm=1), dict(blocks_per_sm=rep["blocks_per_sm"],
                                                                       list_blocks_per_sm=4)):
         a = N_.solve(system, opts).endpoints()
