@@ -482,6 +482,17 @@ nphc_status nphc_result_endpoints(const nphc_result *res, nphc_endpoints *ep);
 
 void nphc_result_destroy(nphc_result *res);
 
+/* Index checks of the debug build (the library compiled with NPHC_DEBUG; the paper has no
+ * counterpart: this stands in for a memory checker).  Its kernels check every work-list
+ * entry, list append, deduplication link and batch item against the bounds of the array
+ * it indexes; a failed check records a code and the access is skipped, so the kernel
+ * returns normally.  Writes the first recorded code since the last call and clears it:
+ * 0 none, 1 a work-list entry outside the endpoint set, 2 an append beyond a list's
+ * capacity, 3 a deduplication link outside the endpoint set, 4 a batch item outside its
+ * group, 5 a gathered entry outside the set; -1 in a release build (no checks).
+ * Synchronous.  NPHC_EINVAL for a NULL code. */
+nphc_status nphc_debug_check(int32_t *code);
+
 /* Message of the last failed call on this thread ("" when none). */
 const char *nphc_last_error(void);
 

@@ -61,48 +61,66 @@ def _stamp() -> str:
     return h.hexdigest()
 
 
-def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
-    """Compile and link libnphc.so; returns its path."""
-    os.makedirs(OUT, exist_ok=True)
-    stamp_file = os.path.join(OUT, "libnphc.stamp")
-    stamp = _stamp()
-    if (not force and os.path.exists(LIB) and os.path.exists(PEAK_LIB) and os.path.exists(stamp_file)
-            and open(stamp_file).read() == stamp):
-        return LIB
+DEBUG_OUT = os.path.join(OUT, "debug")
+DEBUG_LIB = os.path.join(DEBUG_OUT, "libnphc.so")
+DEBUG_FLAGS = ["-DNPHC_DEBUG", "-rdc=true"]   # one error word shared by every unit
+
+
+def _build_variant(out: str, lib: str, extra: list, peak: bool, force: bool, jobs, verbose) -> str:
+    os.makedirs(out, exist_ok=True)
+    stamp_file = os.path.join(out, "libnphc.stamp")
+    stamp = _stamp() + " ".join(extra)
+    if (not force and os.path.exists(lib) and (not peak or os.path.exists(PEAK_LIB))
+            and os.path.exists(stamp_file) and open(stamp_file).read() == stamp):
+        return lib
     nvcc = _nvcc()
     jobs = jobs or max(1, os.cpu_count() or 1)
 
     def compile_one(u):
         src, defs, obj = u
-        cmd = [nvcc] + ARCH + NVCC_FLAGS + defs + ["-c", os.path.join(CSRC, src),
-                                                   "-o", os.path.join(OUT, obj)]
+        cmd = [nvcc] + ARCH + NVCC_FLAGS + extra + defs + ["-c", os.path.join(CSRC, src),
+                                                           "-o", os.path.join(out, obj)]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"nvcc failed for {src} {defs}:\n{r.stderr}")
         if verbose:
             print("built", obj, flush=True)
-        return os.path.join(OUT, obj)
+        return os.path.join(out, obj)
 
-    units = _units() + [("alu_peak.cu", [], "alu_peak.o")]
+    units = _units() + ([("alu_peak.cu", [], "alu_peak.o")] if peak else [])
     # the biggest instantiations first so the pool's tail is short
     units.sort(key=lambda u: -int(u[1][0].split("=")[1]) if u[1] else 0)
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(compile_one, units))
-    peak_obj = os.path.join(OUT, "alu_peak.o")
-    tmp = PEAK_LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp, peak_obj], capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError("link failed (libnphc_peak):\n" + r.stderr)
-    os.replace(tmp, PEAK_LIB)
-    tmp = LIB + f".tmp{os.getpid()}"
-    r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + [o for o in objs if o != peak_obj],
-                       capture_output=True, text=True)
+    peak_obj = os.path.join(out, "alu_peak.o")
+    if peak:
+        tmp = PEAK_LIB + f".tmp{os.getpid()}"
+        r = subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp, peak_obj], capture_output=True,
+                           text=True)
+        if r.returncode != 0:
+            raise RuntimeError("link failed (libnphc_peak):\n" + r.stderr)
+        os.replace(tmp, PEAK_LIB)
+    tmp = lib + f".tmp{os.getpid()}"
+    link = [nvcc] + ARCH + [f for f in extra if f.startswith("-rdc")] + ["-shared", "-o", tmp]
+    r = subprocess.run(link + [o for o in objs if o != peak_obj], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stderr)
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp_file, "w") as fh:
         fh.write(stamp)
-    return LIB
+    return lib
+
+
+def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
+    """Compile and link libnphc.so (and the FMA microbenchmark's library); returns its path."""
+    return _build_variant(OUT, LIB, [], True, force, jobs, verbose)
+
+
+def build_debug(force: bool = False, jobs: int | None = None, verbose: bool = False) -> str:
+    """The debug build (NPHC_DEBUG: every kernel checks its work-list, list, dedup-link and
+    batch indices, records the first failure for nphc_debug_check and skips the access),
+    in _build/debug/; returns its path.  Not part of build(): a test builds it on demand."""
+    return _build_variant(DEBUG_OUT, DEBUG_LIB, DEBUG_FLAGS, False, force, jobs, verbose)
 
 
 if __name__ == "__main__":

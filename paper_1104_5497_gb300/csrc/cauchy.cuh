@@ -124,8 +124,8 @@ __device__ __forceinline__ void cauchy_body(const typename P::Sys &S, const EGCt
             base = __shfl_sync(0xffffffffu, base, leader);
             if (idle) {
                 const int64_t i = (int64_t)base + __popc(need & ((1u << lane) - 1u));
-                if (i < total) {
-                    e = worklist_entry(wl, i);
+                if (i < total) e = worklist_entry(wl, i, ep.count);   // -1: rejected (debug)
+                if (i < total && e >= 0) {
                     const int ts = ep.status[e];
                     if (ts != NPHC_PATH_REACHED) {   // tracking to 1 - r0 did not get there
                         cyc_out[e] = 0;

@@ -49,7 +49,8 @@ __global__ void __launch_bounds__(32 * WARPS)
         if (lane == 0) q = atomicAdd(wl.queue, 1ull);
         q = __shfl_sync(0xffffffffu, q, 0);
         if ((int64_t)q >= total) break;
-        const int64_t e = worklist_entry(wl, (int64_t)q);
+        const int64_t e = worklist_entry(wl, (int64_t)q, ep.count);
+        if (e < 0) continue;   // rejected by the debug build's check
         const int ts = ep.status[e];
         if (ts != NPHC_PATH_REACHED) {   // tracking to 1 - r0 did not get there
             if (lane == 0) {

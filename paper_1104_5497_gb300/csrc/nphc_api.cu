@@ -5,6 +5,7 @@
 // system owns no device memory.  A result owns one device allocation that holds every
 // per-path array, the work lists, the counters and the deduplication scratch.
 #include <cuda.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -18,6 +19,20 @@
 #include "nphc_internal.cuh"
 #include "xy_dispatch.cuh"
 #include "nphc_kernels.cuh"
+
+namespace {
+
+// A named range around a stage of the pipeline (NVTX, for profilers and tracers; it marks
+// the host thread's enqueueing of the stage's launches and costs nothing when no tool is
+// attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+
+}  // namespace
 
 namespace {
 
@@ -120,6 +135,14 @@ struct nphc_result {
 extern "C" {
 
 const char *nphc_last_error(void) { return g_err.c_str(); }
+
+nphc_status nphc_debug_check(int32_t *code) {
+    if (!code) return fail(NPHC_EINVAL, "code is NULL");
+    int c = 0;
+    NPHC_CK(nphc_debug_read(&c));
+    *code = c;
+    return NPHC_OK;
+}
 
 nphc_status nphc_options_default(nphc_options *o) {
     if (!o) return fail(NPHC_EINVAL, "nphc_options_default: NULL");
@@ -757,6 +780,7 @@ namespace {
 // solve has already run (a batch group's launch) and the pipeline starts after it.
 nphc_status solve_into_impl(const nphc_system *S, const nphc_options *o, nphc_result *R,
                             void *stream, bool fp32_done) {
+    const Range whole("nphc_solve_into");
     if (!S || !R) return fail(NPHC_EINVAL, "NULL argument");
     if (R->P != S->npaths || R->N != S->N) return fail(NPHC_EINVAL, "result does not match system");
     nphc_status s;
@@ -803,9 +827,12 @@ nphc_status solve_into_impl(const nphc_system *S, const nphc_options *o, nphc_re
     }
     if (mixed) {
         // FP32 pass over every path
-        if (!fp32_done &&
-            (s = track_impl(S, o, NPHC_PREC_MIXED, ep, nullptr, nullptr, false, false, R->ws, 0, st)))
-            return s;
+        if (!fp32_done) {
+            const Range r("fp32 pass");
+            if ((s = track_impl(S, o, NPHC_PREC_MIXED, ep, nullptr, nullptr, false, false, R->ws, 0, st)))
+                return s;
+        }
+        Range r_tail("fp64 hand-offs, refinement, certification");
         // hand-offs: refinement at t = 1 straight from the hand-off point (certified ones
         // are done), then FP64 continuation of the others
         NPHC_CK(launch_compact(v, PRED_HANDOFF, R->flags, R->list[0], R->lcount + 0, st));
@@ -842,6 +869,7 @@ nphc_status solve_into_impl(const nphc_system *S, const nphc_options *o, nphc_re
                                          R->P, l1, 0, st));
         // deduplicate; every path of a solution reached more than once is re-tracked in
         // FP64 and the endpoints are deduplicated again
+        const Range r_dedup("dedup and re-track of duplicates");
         NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, R->list[2], R->lcount + 2, st));
         NPHC_CK(launch_flag_list(R->list[2], R->lcount + 2, R->P, R->flags, FLAG_RETRACKED_DUP, st));
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[2], R->lcount + 2, false, true, R->ws, 3, st)))
@@ -874,7 +902,10 @@ nphc_status solve_into_impl(const nphc_system *S, const nphc_options *o, nphc_re
                                          R->P, l3, 0, st));
         NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st));
     }
-    NPHC_CK(launch_xy_classify(S->M, xs, v, R->theta, R->index, R->energy, R->mineig, R->logdet, st));
+    {
+        const Range r("classify");
+        NPHC_CK(launch_xy_classify(S->M, xs, v, R->theta, R->index, R->energy, R->mineig, R->logdet, st));
+    }
     if ((s = endgame())) return s;
     NPHC_CK(launch_counts(v, R->flags, R->index, R->counts, st, R->egst, R->cycle));
     R->stream = st;
@@ -1221,6 +1252,7 @@ nphc_status batch_tables(nphc_batch *B, const nphc_options *opts, cudaStream_t s
 }
 
 nphc_status batch_enqueue(nphc_batch *B, const nphc_options *opts, int mode, cudaStream_t st) {
+    const Range whole("nphc_batch_solve");
     NPHC_CK(cudaEventRecord(B->fork, st));
     for (int k = 0; k < NPHC_BATCH_STREAMS; k++) NPHC_CK(cudaStreamWaitEvent(B->streams[k], B->fork, 0));
     std::vector<int> group_of(B->sys.size(), -1);   // -1: the instance runs the whole solve
@@ -1252,6 +1284,7 @@ nphc_status batch_enqueue(nphc_batch *B, const nphc_options *opts, int mode, cud
                 NPHC_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
                 grid = sms * o0->blocks_per_sm;
             }
+            const Range r("batch group fp32 pass");
             NPHC_CK(cudaMemsetAsync(wl.queue, 0, sizeof(unsigned long long), gs));
             NPHC_CK(launch_xy_track_f32_batch(G.M, bg, ctl, wl, grid, gs));
             NPHC_CK(cudaEventRecord(G.done, gs));

@@ -178,11 +178,32 @@ struct WorkList {                           // which entries a launch processes
 // launches more threads than this).
 #define NPHC_TRACK_MAX_THREADS 65536
 
+// Index checks of the debug build (compiled with NPHC_DEBUG, relocatable device code):
+// NPHC_VALID(cond, code) is cond, and a false cond records code in nphc_dbg_error (the
+// first one wins; nphc_debug_check reads it) so that the caller skips the access.  In a
+// release build it is true and cond is not evaluated.  Codes: 1 a work-list entry outside
+// the endpoint set, 2 an append beyond a list's capacity, 3 a dedup link outside the
+// endpoint set, 4 a batch item outside its group, 5 a gathered entry outside the set.
+#ifdef NPHC_DEBUG
+extern __device__ int nphc_dbg_error;
+__device__ __forceinline__ bool nphc_dbg_fail(int code) {
+    atomicCAS(&nphc_dbg_error, 0, code);
+    return false;
+}
+#define NPHC_VALID(cond, code) ((cond) ? true : nphc_dbg_fail(code))
+#else
+#define NPHC_VALID(cond, code) true
+#endif
+
 __device__ __forceinline__ int64_t worklist_size(const WorkList &w, int64_t count) {
     return w.list ? (int64_t)(*w.list_count) : count;
 }
-__device__ __forceinline__ int64_t worklist_entry(const WorkList &w, int64_t i) {
-    return w.list ? (int64_t)w.list[i] : i;
+// Entry i of the work list (i itself without a list); -1 when the debug build finds the
+// entry outside [0, count).
+__device__ __forceinline__ int64_t worklist_entry(const WorkList &w, int64_t i, int64_t count) {
+    const int64_t e = w.list ? (int64_t)w.list[i] : i;
+    (void)count;
+    return NPHC_VALID(e >= 0 && e < count, 1) ? e : -1;
 }
 
 // A generic quadratic system (quad.cuh): P_i(z) = sum of c w(a) w(b), w(-1) = 1, terms

@@ -4,6 +4,22 @@
 
 #include <atomic>
 
+#ifdef NPHC_DEBUG
+__device__ int nphc_dbg_error = 0;   // the first failed index check's code (debug build)
+
+cudaError_t nphc_debug_read(int *code) {
+    cudaError_t e = cudaMemcpyFromSymbol(code, nphc_dbg_error, sizeof(int));
+    if (e != cudaSuccess) return e;
+    const int zero = 0;
+    return cudaMemcpyToSymbol(nphc_dbg_error, &zero, sizeof(int));
+}
+#else
+cudaError_t nphc_debug_read(int *code) {
+    *code = -1;   // a release build has no checks
+    return cudaSuccess;
+}
+#endif
+
 int64_t nphc_launch_counter(int64_t add) {
     static std::atomic<int64_t> n{0};
     return n.fetch_add(add) + add;
@@ -42,15 +58,20 @@ __global__ void compact_kernel(const EPView ep, int pred, int32_t *flags, int32_
             }
         }
     }
-    if (take) list[atomicAdd(count, 1)] = (int32_t)e;
+    if (take) {
+        const int32_t k = atomicAdd(count, 1);
+        if (NPHC_VALID(k < ep.count, 2)) list[k] = (int32_t)e;
+    }
 }
 
 // Marks the entries of a list re-tracked (used for the duplicate re-track).
 __global__ void flag_list_kernel(const int32_t *list, const int32_t *count, int32_t *flags,
-                                 int32_t bit) {
+                                 int32_t bit, int64_t cap) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= *count) return;
-    flags[list[i]] |= bit;
+    const int64_t e = list[i];
+    (void)cap;
+    if (NPHC_VALID(e >= 0 && e < cap, 1)) flags[e] |= bit;
 }
 
 // ------------------------------------------------------------------ dedup --
@@ -154,8 +175,12 @@ __global__ void dedup_insert_kernel(const EPView ep, int n, double delta0, Dedup
 }
 
 __device__ __forceinline__ void push_once(DedupScratch &w, int32_t *list, int32_t *count,
-                                          int64_t e) {
-    if (atomicExch(&w.inlist[e], 1) == 0 && list) list[atomicAdd(count, 1)] = (int32_t)e;
+                                          int64_t e, int64_t cap) {
+    if (atomicExch(&w.inlist[e], 1) == 0 && list) {
+        const int32_t k = atomicAdd(count, 1);
+        (void)cap;
+        if (NPHC_VALID(k < cap, 2)) list[k] = (int32_t)e;
+    }
 }
 
 __device__ __forceinline__ void dd_pair(const EPView &ep, DedupScratch &w, int32_t *list,
@@ -164,8 +189,8 @@ __device__ __forceinline__ void dd_pair(const EPView &ep, DedupScratch &w, int32
         ep.cls[e] = NPHC_END_DUPLICATE;
     else
         ep.cls[o] = NPHC_END_DUPLICATE;
-    push_once(w, list, count, e);
-    push_once(w, list, count, o);
+    push_once(w, list, count, e, ep.count);
+    push_once(w, list, count, o, ep.count);
 }
 
 // phase 2: compare with the endpoints of the own and the neighbouring cells at level L(e)
@@ -174,7 +199,11 @@ __device__ __forceinline__ void dd_pair(const EPView &ep, DedupScratch &w, int32
 __device__ __forceinline__ int64_t dd_entry(const EPView &ep, const int32_t *mlist,
                                             const int32_t *mcount) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (mlist) return i < *mcount ? (int64_t)mlist[i] : -1;
+    if (mlist) {
+        if (i >= *mcount) return -1;
+        const int64_t e = mlist[i];
+        return NPHC_VALID(e >= 0 && e < ep.count, 1) ? e : -1;
+    }
     return i < ep.count ? i : -1;
 }
 
@@ -220,6 +249,7 @@ __global__ void dedup_match_kernel(const EPView ep, int n, double delta0, DedupS
             slot = (slot + 1) & mask;
         }
         for (int64_t guard = 0; o >= 0 && guard < ep.count; guard++) {
+            if (!NPHC_VALID(o < ep.count, 3)) break;
             if (o != e && same_solution(ep, n, e, o)) dd_pair(ep, w, list, count, e, o);
             o = next[o];
         }
@@ -288,7 +318,10 @@ __global__ void counts_kernel(const EPView ep, const int32_t *flags, const int32
 __global__ void real_list_kernel(const EPView ep, int32_t *list, int32_t *count) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ep.count) return;
-    if (ep.cls[e] == NPHC_END_REAL) list[atomicAdd(count, 1)] = (int32_t)e;
+    if (ep.cls[e] == NPHC_END_REAL) {
+        const int32_t k = atomicAdd(count, 1);
+        if (NPHC_VALID(k < ep.count, 2)) list[k] = (int32_t)e;
+    }
 }
 
 __global__ void iota_kernel(int64_t *path, int64_t n) {
@@ -305,6 +338,7 @@ __global__ void gather_sps_kernel(const EPView ep, int M, const int32_t *list, c
     if (i >= *count) return;
     const int64_t e = list[i];
     const int64_t cnt = ep.count;
+    if (!NPHC_VALID(e >= 0 && e < cnt, 5)) return;
     for (int k = 0; k < M; k++) o_theta[i * M + k] = theta[k * cnt + e];
     o_index[i] = index[e];
     o_energy[i] = energy[e];
@@ -327,7 +361,7 @@ cudaError_t launch_compact(const EPView &ep, int pred, int32_t *flags, int32_t *
 cudaError_t launch_flag_list(const int32_t *list, const int32_t *count, int64_t cap,
                              int32_t *flags, int32_t bit, cudaStream_t st) {
     if (cap == 0) return cudaSuccess;
-    flag_list_kernel<<<blocks_for(cap, 256), 256, 0, st>>>(list, count, flags, bit);
+    flag_list_kernel<<<blocks_for(cap, 256), 256, 0, st>>>(list, count, flags, bit, cap);
     nphc_launch_counter(1);
     return cudaGetLastError();
 }

@@ -25,6 +25,9 @@ struct DedupScratch {
     int32_t *inlist;
 };
 
+// The debug build's first failed index check (0 if none), cleared; -1 in a release build.
+cudaError_t nphc_debug_read(int *code);
+
 cudaError_t launch_compact(const EPView &ep, int pred, int32_t *flags, int32_t *list,
                            int32_t *count, cudaStream_t st);
 cudaError_t launch_flag_list(const int32_t *list, const int32_t *count, int64_t cap,

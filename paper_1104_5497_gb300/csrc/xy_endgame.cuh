@@ -530,10 +530,9 @@ __device__ __forceinline__ void refine_body(const typename Q::Sys &S, double tol
         const int64_t i = base + lane;
         int64_t e = -1;
         bool rt = false;
-        if (i < total) {
-            e = worklist_entry(wl, i);
+        if (i < total) e = worklist_entry(wl, i, ep.count);   // -1: rejected (debug)
+        if (e >= 0)
             rt = eg_refine_certify_one<Q>(G, S, tol_sol, refine_eps, refine_iters, ep, e, shortcut);
-        }
         const unsigned m = __ballot_sync(0xffffffffu, rt);
         if (rt) rq[qn + __popc(m & ((1u << lane) - 1u))] = e;
         qn += __popc(m);

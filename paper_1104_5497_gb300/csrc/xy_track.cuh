@@ -223,7 +223,7 @@ struct SingleSrc {
     __device__ __forceinline__ int64_t total() const { return worklist_size(wl, ep.count); }
     __device__ __forceinline__ void take(int64_t i, int &g, int64_t &e) const {
         g = 0;
-        e = worklist_entry(wl, i);
+        e = worklist_entry(wl, i, ep.count);
     }
     __device__ __forceinline__ const Sys &sys(int) const { return S; }
     __device__ __forceinline__ const EPView &eps(int) const { return ep; }
@@ -246,6 +246,7 @@ struct BatchSrc {
         }
         g = lo;
         e = i - off[lo];
+        if (!NPHC_VALID(e >= 0 && e < ep[lo].count, 4)) e = -1;
     }
     __device__ __forceinline__ const Sys &sys(int g) const { return S[g]; }
     __device__ __forceinline__ const EPView &eps(int g) const { return ep[g]; }
@@ -304,8 +305,10 @@ __device__ __forceinline__ void track_body(const Src &src, const XYCtl &C, const
             base = __shfl_sync(0xffffffffu, base, leader);
             if (idle) {
                 const int64_t i = (int64_t)base + __popc(need & ((1u << lane) - 1u));
-                if (i < total) {
-                    src.take(i, g, e);
+                if (i < total) src.take(i, g, e);   // -1 (skipped) if the debug build rejects it
+                if (i >= total) {
+                    e = -2;
+                } else if (e >= 0) {
                     const EPView &ep = src.eps(g);
                     status = NPHC_PATH_RUNNING;
                     run = 0;
@@ -338,8 +341,6 @@ __device__ __forceinline__ void track_body(const Src &src, const XYCtl &C, const
                     since = 0;
                     far = false;
                     zlast = 0.0;
-                } else {
-                    e = -2;
                 }
             }
         }

@@ -78,6 +78,15 @@ class nphc_endpoints(ctypes.Structure):
 _lib = None
 
 
+def use_library(path: str) -> None:
+    """Load the library from `path` (e.g. the debug build) instead of the default; must
+    come before the first call that loads it."""
+    global LIB_PATH
+    if _lib is not None:
+        raise RuntimeError("libnphc is already loaded")
+    LIB_PATH = path
+
+
 def lib():
     """Load libnphc.so (built by paper_1104_5497_gb300.build); raise if it is missing."""
     global _lib
@@ -125,6 +134,7 @@ def lib():
         "nphc_batch_create": [i32, ctypes.POINTER(vp), ctypes.POINTER(vp)],
         "nphc_batch_solve": [vp, ctypes.POINTER(nphc_options), i32, vp],
         "nphc_batch_result": [vp, i32, ctypes.POINTER(vp)],
+        "nphc_debug_check": [pi32],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -354,6 +364,14 @@ class Batch:
         if getattr(self, "handle", None) and _lib is not None:
             _lib.nphc_batch_destroy(self.handle)
         self.handle = None
+
+
+def debug_check() -> int:
+    """nphc_debug_check: the debug build's first failed index check since the last call
+    (0 none; -1 for a release build), cleared."""
+    c = np.zeros(1, np.int32)
+    _check("nphc_debug_check", lib().nphc_debug_check(_pi32(c)))
+    return int(c[0])
 
 
 def solve_into(system: System, opts: nphc_options, result: Result, stream=None) -> None:
