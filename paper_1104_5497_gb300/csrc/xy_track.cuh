@@ -451,13 +451,15 @@ __device__ __forceinline__ void track_body(const Src &src, const XYCtl &C, const
         }
         go = go && status == NPHC_PATH_RUNNING;
 
-        // ---- FP32 pass: a step whose Schur system's condition estimate exceeds kappa
-        // (kappa = 0 outside the FP32 pass) is not taken; FP64 continues the path from its
-        // last accepted point (or the end zone's clean checkpoint), where the estimate was
-        // below kappa: the FP32 solve's relative error grows like the condition number
+        // ---- FP32 pass: a converged step whose Schur systems' condition estimate exceeds
+        // kappa (kappa = 0 outside the FP32 pass) is not taken; FP64 continues the path from
+        // its last accepted point (or the end zone's clean checkpoint), where the estimate
+        // was below kappa: the FP32 solve's relative error grows like the condition number
         // times 6e-8, and a step across an ill-conditioned stretch (two paths passing
-        // close) can land on the neighbouring path
-        if (go && C.kappa > 0.0 && !((double)kstep <= C.kappa)) {
+        // close) can land on the neighbouring path.  A step that did not converge lands
+        // nowhere: it is rejected and halved as usual, whatever its estimate (a poor
+        // prediction far off the path can see a large one)
+        if (go && conv && C.kappa > 0.0 && !((double)kstep <= C.kappa)) {
             status = NPHC_PATH_HANDOFF_COND;
             go = false;
         }
