@@ -1,20 +1,29 @@
 // xy_track_warp.cuh -- FP64 path tracking of the XY ring with one path per warp, for
 // short lists (paths handed off by the FP32 pass, re-tracks).
 //
-// GB300 runs FP64 at 1/64 of the FP32 rate, and the per-thread tracker (xy_track.cuh)
-// runs every solve on all 32 lanes of a warp whatever the number of paths in it: a
-// list of a few thousand paths then costs the latency of ~12k dependent FP64
-// instructions per solve.  Here the 32 lanes share one path: the per-site quantities
-// (frames, u, w, right-hand sides) are computed by lane j for site j, column j of the
-// Schur matrix is built by lane j, each Householder step updates one column per lane,
-// the back substitution updates one row per lane, and the compensated residual is one
-// row pair per lane.  The step logic (RK4 predictor, Newton corrector, step control,
-// divergence radius, budget) is the one of the per-thread FP64 tracker: the same
-// algorithm, so the same endpoints.
+// GB300 runs FP64 at 1/64 of the FP32 rate, and its FP64 pipe takes a warp instruction
+// at the same cost whatever the number of active lanes: a solve costs about 76 cycles of
+// an SM sub-partition per FP64 instruction on the longest chain that any lane runs.  So
+// the 32 lanes share one path, and every stage is laid out to keep each lane's own FP64
+// chain short rather than to save lanes:
+//   * per-site quantities (couplings sums, frames, the diagonal's terms): lane j for
+//     site j, the sums u_j and w_j on lanes j and 16 + j;
+//   * the off-diagonal Schur entries: one entry per lane, strided over the M x M matrix;
+//   * the right-hand sides: sums of J times per-site vectors, right-hand side r on the
+//     lanes 16 r + k (row k);
+//   * the factorisation: LU with partial pivoting (one reciprocal per column and no
+//     square root; the pivot search compares the bit patterns of |re| + |im| as integers
+//     and costs one FP64 add), the rank-one update strided over the trailing block;
+//   * the back substitution in registers (right-hand side r on lanes 16 r + row);
+//   * the compensated residual of row pair k on lanes k and 16 + k.
+// The step logic (RK4 predictor, Newton corrector, step control, divergence radius,
+// budget) is the per-thread FP64 tracker's, as are the equations and the scaled
+// light-cone frames of the Schur reduction (xy_solve.cuh): the same algorithm, with a
+// different linear solver, so the endpoints agree to the tracking tolerance.
 //
 // Storage: everything of a path in per-warp shared memory (complex doubles): the
 // augmented Schur matrix [S | b0 | b1] (column-major, M x (M + 2)), the five step
-// vectors Z0, K1, AC, ZC, W1 (2M each) and nine per-site arrays.
+// vectors Z0, K1, AC, ZC, W1 (2M each) and thirteen per-site arrays.
 #pragma once
 
 #include "xy_track.cuh"
@@ -30,16 +39,18 @@ struct WarpLayout {
     static constexpr int W1 = ZC + NV;
     static constexpr int AH = W1 + NV;    // frame a^_j
     static constexpr int BH = AH + M;     // frame b^_j
-    static constexpr int IV = BH + M;     // 1 / |(a_j, b_j)| (real part)
-    static constexpr int AJ = IV + M;     // diagonal entries A_jj, B_jj of the gradient rows
-    static constexpr int BJ = AJ + M;
-    static constexpr int P0 = BJ + M;     // conj(a^) q0, conj(b^) q0, conj(a^) q1, conj(b^) q1
-    static constexpr int Q0 = P0 + M;
-    static constexpr int P1 = Q0 + M;
-    static constexpr int Q1 = P1 + M;
-    static constexpr int SS = Q1 + M;     // light-cone scales (sp, sq) of each site
-    static constexpr int SC = SS + M;     // reflector scalars of the current Householder step
-    static constexpr int TOTAL = SC + 2;
+    static constexpr int SS = BH + M;     // light-cone scales (sp, sq) of site j
+    static constexpr int CB = SS + M;     // (i t / 2) sp_j b^_j: Schur column j is J_kj (q_k CB_j + p_k CA_j)
+    static constexpr int CA = CB + M;     // (i t / 2) sq_j a^_j
+    static constexpr int X0 = CA + M;     // sp_j conj(a^_j) q0_j, sq_j conj(b^_j) q0_j (right-hand side 0),
+    static constexpr int Y0 = X0 + M;
+    static constexpr int X1 = Y0 + M;     // the same with q1_j (right-hand side 1)
+    static constexpr int Y1 = X1 + M;
+    static constexpr int PK = Y1 + M;     // p_j = x_j + i y_j, q_j = x_j - i y_j
+    static constexpr int QK = PK + M;
+    static constexpr int QS0 = QK + M;    // the constraint rows' components q0_j, q1_j
+    static constexpr int QS1 = QS0 + M;
+    static constexpr int TOTAL = QS1 + M;
 };
 
 template <int M>
@@ -62,6 +73,26 @@ __device__ __forceinline__ double warp_max(double v) {
     return __shfl_sync(0xffffffffu, v, 0);
 }
 
+// c - a b with four fused multiply-adds
+__device__ __forceinline__ cx<double> cfnms(cx<double> c, cx<double> a, cx<double> b) {
+    return cx<double>{fma(a.im, b.im, fma(-a.re, b.re, c.re)), fma(-a.im, b.re, fma(-a.re, b.im, c.im))};
+}
+
+__device__ __forceinline__ cx<double> shfl_down16(cx<double> v) {
+    return cx<double>{__shfl_down_sync(0xffffffffu, v.re, 16), __shfl_down_sync(0xffffffffu, v.im, 16)};
+}
+
+__device__ __forceinline__ ext<double> shfl_down16(ext<double> v) {
+    return ext<double>{__shfl_down_sync(0xffffffffu, v.hi, 16), __shfl_down_sync(0xffffffffu, v.lo, 16)};
+}
+
+// (a.hi + a.lo) + (b.hi + b.lo), the rounding error of the leading sum kept in lo
+__device__ __forceinline__ ext<double> ext_add(ext<double> a, ext<double> b) {
+    double s, e;
+    two_sum(a.hi, b.hi, s, e);
+    return ext<double>{s, EFT<double>::add(e, EFT<double>::add(a.lo, b.lo))};
+}
+
 template <int M>
 struct WarpPath {
     cx<double> *s;   // this warp's shared memory
@@ -70,93 +101,121 @@ struct WarpPath {
     __device__ __forceinline__ cx<double> &A(int i, int c) const { return s[WarpLayout<M>::A + c * M + i]; }
 };
 
-// -H(z, t) at ZC into W1 with compensated sums (the per-thread tracker's xy_residual_comp,
-// rows k and M + k on lane k).
+// -H(z, t) at ZC into W1 with compensated sums (the per-thread tracker's xy_residual_comp
+// in (x, y)).  Row pair k: lane k sums u_k = J_kN + sum_l J_kl x_l and forms the f row,
+// lane 16 + k sums w_k = sum_l J_kl y_l, forms the g row (which needs no sums) and hands
+// its share of f_k = y_k u_k - x_k w_k to lane k.
 template <int M>
 __device__ void warp_residual(const WarpPath<M> &P, const double *__restrict__ J, double s,
                               double omt, cx<double> gam) {
+    static_assert(M <= 16, "one row pair per lane pair");
     using L = WarpLayout<M>;
     using E = EFT<double>;
-    const int k = P.lane;
+    const int k = P.lane & 15;
+    const bool hi = P.lane >= 16;
+    const ext<double> zero = {0.0, 0.0};
+    ext<double> fre = zero, fim = zero;   // lane k: the y u part of f; lane 16 + k: the -x w part
+    cx<double> xk = cx<double>{0.0, 0.0}, yk = xk;
+    const cx<double> gomt = cx<double>{E::mul(omt, gam.re), E::mul(omt, gam.im)};
     if (k < M) {
-        const cx<double> gomt = cx<double>{E::mul(omt, gam.re), E::mul(omt, gam.im)};
-        const cx<double> xk = P.at(L::ZC, k), yk = P.at(L::ZC, M + k);
+        xk = P.at(L::ZC, k);
+        yk = P.at(L::ZC, M + k);
         const double *Jk = J + k * NPHC_JSTRIDE;
-        const ext<double> zero = {0.0, 0.0};
-        ext<double> ure = {Jk[M], 0.0}, uim = zero, wre = zero, wim = zero;
+        const int off = hi ? L::ZC + M : L::ZC;
+        ext<double> sre = {hi ? 0.0 : Jk[M], 0.0}, sim = zero;
 #pragma unroll 1
         for (int l = 0; l < M; l++) {   // J_kk = 0 adds exact zeros
-            const cx<double> xl = P.at(L::ZC, l), yl = P.at(L::ZC, M + l);
-            ext_acc(ure, Jk[l], xl.re);
-            ext_acc(uim, Jk[l], xl.im);
-            ext_acc(wre, Jk[l], yl.re);
-            ext_acc(wim, Jk[l], yl.im);
+            const cx<double> v = P.at(off, l);
+            ext_acc(sre, Jk[l], v.re);
+            ext_acc(sim, Jk[l], v.im);
         }
-        ext<double> fre = zero, fim = zero;
-        ext_acc_ext(fre, yk.re, ure);
-        ext_acc_ext(fre, -yk.im, uim);
-        ext_acc_ext(fre, -xk.re, wre);
-        ext_acc_ext(fre, xk.im, wim);
-        ext_acc_ext(fim, yk.re, uim);
-        ext_acc_ext(fim, yk.im, ure);
-        ext_acc_ext(fim, -xk.re, wim);
-        ext_acc_ext(fim, -xk.im, wre);
-        ext<double> qxr = {-1.0, 0.0}, qxi = zero, qyr = {-1.0, 0.0}, qyi = zero;
+        if (!hi) {
+            ext_acc_ext(fre, yk.re, sre);
+            ext_acc_ext(fre, -yk.im, sim);
+            ext_acc_ext(fim, yk.re, sim);
+            ext_acc_ext(fim, yk.im, sre);
+        } else {
+            ext_acc_ext(fre, -xk.re, sre);
+            ext_acc_ext(fre, xk.im, sim);
+            ext_acc_ext(fim, -xk.re, sim);
+            ext_acc_ext(fim, -xk.im, sre);
+        }
+    }
+    const ext<double> wre = shfl_down16(fre), wim = shfl_down16(fim);
+    if (k < M) {
+        ext<double> qxr = {-1.0, 0.0}, qxi = zero;
         ext_acc(qxr, xk.re, xk.re);
         ext_acc(qxr, -xk.im, xk.im);
         ext_acc(qxi, 2.0 * xk.re, xk.im);
-        ext_acc(qyr, yk.re, yk.re);
-        ext_acc(qyr, -yk.im, yk.im);
-        ext_acc(qyi, 2.0 * yk.re, yk.im);
-        ext<double> hfr = zero, hfi = zero, hgr = zero, hgi = zero;
-        ext_acc_ext(hfr, gomt.re, qxr);
-        ext_acc_ext(hfr, -gomt.im, qxi);
-        ext_acc_ext(hfr, s, fre);
-        ext_acc_ext(hfi, gomt.re, qxi);
-        ext_acc_ext(hfi, gomt.im, qxr);
-        ext_acc_ext(hfi, s, fim);
-        ext_acc_ext(hgr, gomt.re, qyr);
-        ext_acc_ext(hgr, -gomt.im, qyi);
-        ext_acc_ext(hgr, s, qxr);
-        ext_acc_ext(hgr, s, qyr);
-        ext_acc(hgr, s, 1.0);
-        ext_acc_ext(hgi, gomt.re, qyi);
-        ext_acc_ext(hgi, gomt.im, qyr);
-        ext_acc_ext(hgi, s, qxi);
-        ext_acc_ext(hgi, s, qyi);
-        P.at(L::W1, k) = cx<double>{-ext_val(hfr), -ext_val(hfi)};
-        P.at(L::W1, M + k) = cx<double>{-ext_val(hgr), -ext_val(hgi)};
+        if (!hi) {
+            fre = ext_add(fre, wre);
+            fim = ext_add(fim, wim);
+            ext<double> hfr = zero, hfi = zero;
+            ext_acc_ext(hfr, gomt.re, qxr);
+            ext_acc_ext(hfr, -gomt.im, qxi);
+            ext_acc_ext(hfr, s, fre);
+            ext_acc_ext(hfi, gomt.re, qxi);
+            ext_acc_ext(hfi, gomt.im, qxr);
+            ext_acc_ext(hfi, s, fim);
+            P.at(L::W1, k) = cx<double>{-ext_val(hfr), -ext_val(hfi)};
+        } else {
+            ext<double> qyr = {-1.0, 0.0}, qyi = zero;
+            ext_acc(qyr, yk.re, yk.re);
+            ext_acc(qyr, -yk.im, yk.im);
+            ext_acc(qyi, 2.0 * yk.re, yk.im);
+            ext<double> hgr = zero, hgi = zero;
+            ext_acc_ext(hgr, gomt.re, qyr);
+            ext_acc_ext(hgr, -gomt.im, qyi);
+            ext_acc_ext(hgr, s, qxr);
+            ext_acc_ext(hgr, s, qyr);
+            ext_acc(hgr, s, 1.0);
+            ext_acc_ext(hgi, gomt.re, qyi);
+            ext_acc_ext(hgi, gomt.im, qyr);
+            ext_acc_ext(hgi, s, qxi);
+            ext_acc_ext(hgi, s, qyi);
+            P.at(L::W1, M + k) = cx<double>{-ext_val(hgr), -ext_val(hgi)};
+        }
     }
     __syncwarp();
 }
 
-// H_z(ZC, t) d = r, the per-thread xy_solve shared out over the warp.
+// H_z(ZC, t) d = r, the per-thread xy_solve's Schur reduction shared out over the warp.
 //   two_rhs false: r = -H_t, d into W1.
 //   two_rhs true:  r1 = W1 (the residual), d1 into W1; r2 = -H_t, d2 into `out2`.
 // Returns false (in every lane) when S is singular or the result is not finite.
 template <int M>
 __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, double s,
                            double omt, cx<double> gam, bool two_rhs, int out2) {
+    static_assert(M <= 16, "one site per lane of each half-warp");
     using L = WarpLayout<M>;
     const int lane = P.lane;
+    const int hrow = lane & 15, r = lane >> 4;   // row and right-hand side of the half-warp layout
     const cx<double> gomt = cscale(omt, gam);
     const cx<double> sg = cx<double>{s + gomt.re, gomt.im};   // t + gamma (1 - t)
-    // ---- per-site quantities (lane j = site j)
-    if (lane < M) {
-        const int j = lane;
-        const cx<double> xj = P.at(L::ZC, j), yj = P.at(L::ZC, M + j);
+    const double hs = 0.5 * s;
+
+    // ---- per-site quantities: u_j on lane j, w_j on lane 16 + j, the rest on lane j
+    cx<double> uw = cx<double>{0.0, 0.0};
+    if (hrow < M) {
+        const int j = hrow;
         const double *Jj = J + j * NPHC_JSTRIDE;
-        cx<double> u = cx<double>{Jj[M], 0.0}, w = cx<double>{0.0, 0.0};
+        const int off = r ? L::ZC + M : L::ZC;
+        uw = cx<double>{r ? 0.0 : Jj[M], 0.0};
 #pragma unroll 1
         for (int l = 0; l < M; l++) {
-            const cx<double> xl = P.at(L::ZC, l), yl = P.at(L::ZC, M + l);
-            u.re += Jj[l] * xl.re;
-            u.im += Jj[l] * xl.im;
-            w.re += Jj[l] * yl.re;
-            w.im += Jj[l] * yl.im;
+            const cx<double> v = P.at(off, l);
+            uw.re = fma(Jj[l], v.re, uw.re);
+            uw.im = fma(Jj[l], v.im, uw.im);
         }
+    }
+    const cx<double> w = shfl_down16(uw);
+    if (lane < M) {
+        const int j = lane;
+        const cx<double> u = uw;
+        const cx<double> xj = P.at(L::ZC, j), yj = P.at(L::ZC, M + j);
         cx<double> htf, htg;
         minus_ht_rows<double>(xj, yj, u, w, gam, htf, htg);
+        const cx<double> rf0 = two_rhs ? P.at(L::W1, j) : htf;
         const cx<double> rg0 = two_rhs ? P.at(L::W1, M + j) : htg;
         cx<double> ah, bh;
         double iv, sp, sq;
@@ -166,147 +225,137 @@ __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, d
                                    -s * w.im + 2.0 * (gomt.re * xj.im + gomt.im * xj.re)},
                         cscale(s, u), sp, sq, Ajj, Bjj);
         const cx<double> q0 = cscale(iv, rg0), q1 = cscale(iv, htg);
+        const cx<double> px0 = cmulc(ah, q0), py0 = cmulc(bh, q0);
         P.at(L::AH, j) = ah;
         P.at(L::BH, j) = bh;
-        P.at(L::IV, j) = cx<double>{iv, 0.0};
         P.at(L::SS, j) = cx<double>{sp, sq};
-        P.at(L::AJ, j) = Ajj;
-        P.at(L::BJ, j) = Bjj;
-        P.at(L::P0, j) = cmulc(ah, q0);
-        P.at(L::Q0, j) = cmulc(bh, q0);
-        P.at(L::P1, j) = cmulc(ah, q1);
-        P.at(L::Q1, j) = cmulc(bh, q1);
-        // the f-row right-hand sides wait in the right-hand-side columns
-        P.A(j, M) = two_rhs ? P.at(L::W1, j) : htf;
-        if (two_rhs) P.A(j, M + 1) = htf;
+        P.at(L::CB, j) = cmul_i(cscale(hs * sp, bh));
+        P.at(L::CA, j) = cmul_i(cscale(hs * sq, ah));
+        P.at(L::X0, j) = cscale(sp, px0);
+        P.at(L::Y0, j) = cscale(sq, py0);
+        P.at(L::PK, j) = cx<double>{xj.re - yj.im, xj.im + yj.re};
+        P.at(L::QK, j) = cx<double>{xj.re + yj.im, xj.im - yj.re};
+        P.at(L::QS0, j) = q0;
+        // the diagonal entry, and the diagonal's own terms of the right-hand sides
+        P.A(j, j) = csub(cmul(Ajj, bh), cmul(Bjj, ah));
+        P.A(j, M) = csub(rf0, cadd(cmul(Ajj, px0), cmul(Bjj, py0)));
+        if (two_rhs) {
+            const cx<double> px1 = cmulc(ah, q1), py1 = cmulc(bh, q1);
+            P.at(L::X1, j) = cscale(sp, px1);
+            P.at(L::Y1, j) = cscale(sq, py1);
+            P.at(L::QS1, j) = q1;
+            P.A(j, M + 1) = csub(htf, cadd(cmul(Ajj, px1), cmul(Bjj, py1)));
+        }
     }
     __syncwarp();
-    // ---- column j of S (lane j), right-hand-side row k (lane k)
-    // (off-diagonal: (i t J_kj / 2) (sp_j q_k b^_j + sq_j p_k a^_j) and right-hand-side terms
-    // (i t J_kj / 2) (sp_j q_k px_j - sq_j p_k py_j), p = x + i y, q = x - i y; see xy_solve.cuh)
-    if (lane < M) {
-        const int j = lane;
-        const cx<double> ah = P.at(L::AH, j), bh = P.at(L::BH, j);
-        const cx<double> sc = P.at(L::SS, j);
-        const double hs = 0.5 * s;
-        const cx<double> cb = cmul_i(cscale(hs * sc.re, bh)), ca = cmul_i(cscale(hs * sc.im, ah));
+
+    // ---- off-diagonal entries of S, one per lane (consecutive lanes: consecutive rows);
+    // right-hand side r of row k on lane 16 r + k:
+    //   b_k -= (i t / 2) (q_k sum_j J_kj X_j - p_k sum_j J_kj Y_j)   (J_kk = 0)
 #pragma unroll 1
-        for (int k = 0; k < M; k++) {
-            cx<double> e;
-            if (k == j) {
-                e = csub(cmul(P.at(L::AJ, j), bh), cmul(P.at(L::BJ, j), ah));
-            } else {
-                const cx<double> xk = P.at(L::ZC, k), yk = P.at(L::ZC, M + k);
-                const cx<double> pk = cx<double>{xk.re - yk.im, xk.im + yk.re};
-                const cx<double> qk = cx<double>{xk.re + yk.im, xk.im - yk.re};
-                e = cscale(J[k * NPHC_JSTRIDE + j], cadd(cmul(qk, cb), cmul(pk, ca)));
-            }
-            P.A(k, j) = e;
-        }
-        const int k = lane;
-        const cx<double> xk = P.at(L::ZC, k), yk = P.at(L::ZC, M + k);
-        const cx<double> pk = cx<double>{xk.re - yk.im, xk.im + yk.re};
-        const cx<double> qk = cx<double>{xk.re + yk.im, xk.im - yk.re};
-        cx<double> b0 = P.A(k, M), b1 = two_rhs ? P.A(k, M + 1) : cx<double>{0.0, 0.0};
+    for (int e = lane; e < M * M; e += 32) {
+        const int j = e / M, k = e - j * M;
+        if (k != j)
+            P.A(k, j) = cscale(J[k * NPHC_JSTRIDE + j],
+                               cadd(cmul(P.at(L::QK, k), P.at(L::CB, j)), cmul(P.at(L::PK, k), P.at(L::CA, j))));
+    }
+    if (hrow < M && (r == 0 || two_rhs)) {
+        const int k = hrow;
+        const double *Jk = J + k * NPHC_JSTRIDE;
+        const int ox = r ? L::X1 : L::X0, oy = r ? L::Y1 : L::Y0;
+        cx<double> sx = cx<double>{0.0, 0.0}, sy = sx;
 #pragma unroll 1
-        for (int jj = 0; jj < M; jj++) {
-            const cx<double> px0 = P.at(L::P0, jj), py0 = P.at(L::Q0, jj);
-            const cx<double> px1 = P.at(L::P1, jj), py1 = P.at(L::Q1, jj);
-            if (jj == k) {
-                const cx<double> Ak = P.at(L::AJ, k), Bk = P.at(L::BJ, k);
-                b0 = csub(b0, cadd(cmul(Ak, px0), cmul(Bk, py0)));
-                if (two_rhs) b1 = csub(b1, cadd(cmul(Ak, px1), cmul(Bk, py1)));
-            } else {
-                const cx<double> scj = P.at(L::SS, jj);
-                const double hJ = hs * J[k * NPHC_JSTRIDE + jj];
-                const cx<double> qs = cscale(hJ * scj.re, qk), ps = cscale(hJ * scj.im, pk);
-                b0 = csub(b0, cmul_i(csub(cmul(qs, px0), cmul(ps, py0))));
-                if (two_rhs) b1 = csub(b1, cmul_i(csub(cmul(qs, px1), cmul(ps, py1))));
-            }
+        for (int j = 0; j < M; j++) {
+            const double Jkj = Jk[j];
+            const cx<double> xv = P.at(ox, j), yv = P.at(oy, j);
+            sx.re = fma(Jkj, xv.re, sx.re);
+            sx.im = fma(Jkj, xv.im, sx.im);
+            sy.re = fma(Jkj, yv.re, sy.re);
+            sy.im = fma(Jkj, yv.im, sy.im);
         }
-        P.A(k, M) = b0;
-        if (two_rhs) P.A(k, M + 1) = b1;
+        const cx<double> d = csub(cmul(P.at(L::QK, k), sx), cmul(P.at(L::PK, k), sy));
+        P.A(k, M + r) = csub(P.A(k, M + r), cmul_i(cscale(hs, d)));
     }
     __syncwarp();
-    // ---- Householder QR, one column per lane; lane k forms the reflector of step k
-    // (FP64 work is paid per active lane: the other lanes read its scalars)
+
+    // ---- LU with partial pivoting of [S | b0 | b1]; the pivot's reciprocal replaces it
     const int ncol = two_rhs ? M + 2 : M + 1;
     bool ok = true;
 #pragma unroll 1
     for (int k = 0; k < M; k++) {
-        if (lane == k) {
-            const cx<double> al = P.A(k, k);
-            double xn2 = 0.0;
-#pragma unroll 1
-            for (int i = k + 1; i < M; i++) xn2 += cabs2(P.A(i, k));
-            const double an = sqrt(cabs2(al) + xn2);
-            const double beta = al.re >= 0.0 ? -an : an;
-            const double ib = 1.0 / beta;
-            P.at(L::SC, 0) = cx<double>{(beta - al.re) * ib, al.im * ib};   // conj(tau)
-            P.at(L::SC, 1) = crecip(cx<double>{al.re - beta, al.im});        // 1 / (al - beta)
-            P.A(k, k) = cx<double>{beta, an > 0.0 ? 1.0 : 0.0};              // flag in .im
+        // the row of the largest |re| + |im| at or below k (ties: the lowest row); the
+        // bit patterns of non-negative doubles order as the values do
+        unsigned long long key = 0ull;
+        int idx = lane;
+        if (lane >= k && lane < M) {
+            const cx<double> a = P.A(lane, k);
+            key = (unsigned long long)__double_as_longlong(fabs(a.re) + fabs(a.im));
         }
-        __syncwarp();
-        ok = ok && P.A(k, k).im != 0.0;
-        const cx<double> tauc = P.at(L::SC, 0);
-        // the reflector (1, v_{k+1}, .., v_{M-1}) replaces column k below the diagonal
-        if (lane > k && lane < M) P.A(lane, k) = cmul(P.A(lane, k), P.at(L::SC, 1));
-        __syncwarp();
-        const int c = lane;
-        if (c > k && c < ncol) {
-            cx<double> wv = P.A(k, c);
-#pragma unroll 1
-            for (int i = k + 1; i < M; i++) wv = cadd(wv, cmulc(P.A(i, k), P.A(i, c)));
-            wv = cmul(tauc, wv);
-            P.A(k, c) = csub(P.A(k, c), wv);
-#pragma unroll 1
-            for (int i = k + 1; i < M; i++) P.A(i, c) = csub(P.A(i, c), cmul(P.A(i, k), wv));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ko = __shfl_xor_sync(0xffffffffu, key, o);
+            const int io = __shfl_xor_sync(0xffffffffu, idx, o);
+            if (ko > key || (ko == key && io < idx)) {
+                key = ko;
+                idx = io;
+            }
         }
+        int p = idx;
+        if (key == 0ull) {   // the column is zero from row k down: S is singular
+            ok = false;
+            p = k;
+        }
+        if (p != k) {   // uniform
+            if (lane >= k && lane < ncol) {
+                const cx<double> a = P.A(k, lane);
+                P.A(k, lane) = P.A(p, lane);
+                P.A(p, lane) = a;
+            }
+            __syncwarp();
+        }
+        const cx<double> a = P.A(k, k);
+        const double rd = 1.0 / fma(a.re, a.re, a.im * a.im);
+        const cx<double> ip = cx<double>{a.re * rd, -a.im * rd};
+        if (lane > k && lane < M) P.A(lane, k) = cmul(P.A(lane, k), ip);
         __syncwarp();
-        if (lane == k) P.A(k, k).im = 0.0;   // R_kk = beta, real
+        const int nr = M - 1 - k, nc = ncol - 1 - k;
+#pragma unroll 1
+        for (int e = lane; e < nr * nc; e += 32) {
+            const int c = k + 1 + e / nr, i = k + 1 + (e - (e / nr) * nr);
+            P.A(i, c) = cfnms(P.A(i, c), P.A(i, k), P.A(k, c));
+        }
+        if (lane == 31) P.A(k, k) = ip;   // nothing reads the pivot in this step's update
         __syncwarp();
     }
-    // ---- back substitution: lane k scales row k, lanes i < k eliminate it
+
+    // ---- back substitution U x = b in registers: right-hand side r, row hrow
+    const bool act = r == 0 || two_rhs;
+    cx<double> cur = cx<double>{0.0, 0.0};
+    if (act && hrow < M) cur = P.A(hrow, M + r);
 #pragma unroll 1
     for (int k = M - 1; k >= 0; k--) {
-        if (lane == k) {
-            const double ir = 1.0 / P.A(k, k).re;
-            P.A(k, M) = cscale(ir, P.A(k, M));
-            if (two_rhs) P.A(k, M + 1) = cscale(ir, P.A(k, M + 1));
+        const int src = (lane & 16) | k;
+        const cx<double> bk = cx<double>{__shfl_sync(0xffffffffu, cur.re, src),
+                                         __shfl_sync(0xffffffffu, cur.im, src)};
+        if (hrow <= k) {
+            const cx<double> xk = cmul(bk, P.A(k, k));   // the pivot's reciprocal
+            cur = hrow == k ? xk : cfnms(cur, P.A(hrow, k), xk);
         }
-        __syncwarp();
-        if (lane < k) {
-            const cx<double> Rik = P.A(lane, k);
-            P.A(lane, M) = csub(P.A(lane, M), cmul(Rik, P.A(k, M)));
-            if (two_rhs) P.A(lane, M + 1) = csub(P.A(lane, M + 1), cmul(Rik, P.A(k, M + 1)));
-        }
-        __syncwarp();
     }
-    // ---- back to (dx, dy) (lane j = site j)
+
+    // ---- back to (dx, dy): site j of right-hand side r on lane 16 r + j,
+    // (dwp, dwq) = conj(a^, b^) q_j + (b^, -a^) s_j
     double chk = 0.0;
-    if (lane < M) {
-        const int j = lane;
-        const cx<double> ah = P.at(L::AH, j), bh = P.at(L::BH, j);
-        const double iv = P.at(L::IV, j).re;
+    if (act && hrow < M) {
+        const int j = hrow;
         const cx<double> sc = P.at(L::SS, j);
-        const cx<double> xj = P.at(L::ZC, j), yj = P.at(L::ZC, M + j);
-        const cx<double> htg = minus_ht_g<double>(xj, yj, gam);
-        const cx<double> q0 = cscale(iv, two_rhs ? P.at(L::W1, M + j) : htg);
-        cx<double> dx0, dy0;
-        lc_step<double>(ah, bh, sc.re, sc.im, q0, P.A(j, M), dx0, dy0);
-        chk += cabs2(dx0) + cabs2(dy0);
-        cx<double> dx1 = cx<double>{0.0, 0.0}, dy1 = dx1;
-        if (two_rhs) {
-            const cx<double> q1 = cscale(iv, htg);
-            lc_step<double>(ah, bh, sc.re, sc.im, q1, P.A(j, M + 1), dx1, dy1);
-            chk += cabs2(dx1) + cabs2(dy1);
-        }
-        P.at(L::W1, j) = dx0;   // lane j reads and writes only entries j and M + j
-        P.at(L::W1, M + j) = dy0;
-        if (two_rhs) {
-            P.at(out2, j) = dx1;
-            P.at(out2, M + j) = dy1;
-        }
+        cx<double> dx, dy;
+        lc_step<double>(P.at(L::AH, j), P.at(L::BH, j), sc.re, sc.im, P.at(r ? L::QS1 : L::QS0, j), cur,
+                        dx, dy);
+        chk = cabs2(dx) + cabs2(dy);
+        const int o = r ? out2 : L::W1;   // W1's entries j and M + j were read above only
+        P.at(o, j) = dx;
+        P.at(o, M + j) = dy;
     }
     __syncwarp();
     chk = warp_sum(chk);
