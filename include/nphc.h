@@ -130,13 +130,13 @@ typedef struct nphc_options {
                                   kappa_sing max(1, ||z||_inf^2), 1e12 */
     int threads_per_path;      /* FP64 tracking of lists (hand-offs, re-tracks): 32 = one path
                                   per warp (the path's solve shared over the lanes), 1 = one
-                                  path per thread (every lane a path); 0 = automatic: one per
-                                  thread for N >= 12 (the large lists of the big rings fill the
-                                  FP64 pipe better with every lane busy), else one per warp */
-    double kappa_fp32;         /* FP32 pass: a step whose condition estimate exceeds this is
-                                  not taken and FP64 continues the path (NPHC_PATH_HANDOFF_COND,
-                                  see nphc_track); FP32 solves lose about kappa x 6e-8 of
-                                  their relative accuracy.  0 = no such test; 1e6 */
+                                  path per thread (every lane a path); 0 = automatic (one path
+                                  per warp) */
+    double kappa_fp32;         /* FP32 pass: a converged step whose solves' condition estimate
+                                  exceeds this is not taken and FP64 continues the path
+                                  (NPHC_PATH_HANDOFF_COND, see nphc_track); FP32 solves lose
+                                  about kappa x 6e-8 of their relative accuracy.  0 = no such
+                                  test; 1e6 */
 } nphc_options;
 
 typedef struct nphc_system nphc_system;   /* opaque; owns the device copy of the couplings */

@@ -7,7 +7,7 @@ same endpoints bit for bit): the FP32 tracker over its resident blocks per SM
 one path per warp at 1 to 4 blocks per SM (`list_blocks_per_sm`).
 
 Stage 2 (gated by parity): the FP64 lists' threads per path (`threads_per_path`: one path
-per warp in (x, y), or one per thread in light-cone coordinates, whose rounding differs)
+per warp with an LU solve, or one per thread with a Householder QR, whose rounding differs)
 and the FP32 pass's step control, the corrector's iteration cap (`max_newton_fp32`) and
 tolerance (`eps_fp32`), which decide which steps it accepts and which paths it hands to
 FP64.  Each candidate runs the calibration sample through the FP32 pass, the FP64
@@ -37,7 +37,7 @@ FP32_CANDIDATES = (0, 7, 6, 5, 4)   # resident blocks per SM; 0 = the occupancy 
 LIST_CANDIDATES = (2, 1, 3, 4)      # blocks of 4 warps per SM (the default, 2, first)
 # FP32 step control: (max_newton_fp32, eps_fp32); the defaults first
 STEP_CANDIDATES = ((3, 1e-5), (2, 1e-5), (3, 3e-5), (2, 3e-5))
-THREADS_PER_PATH = (0, 32, 1)       # FP64 lists; 0 = the library's automatic choice
+THREADS_PER_PATH = (0, 1)           # FP64 lists; 0 = the library's automatic choice (32)
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 

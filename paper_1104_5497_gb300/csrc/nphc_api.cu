@@ -489,8 +489,7 @@ nphc_status track_impl(const nphc_system *S, const nphc_options *o, nphc_precisi
     const EPView v = view(ep);
     if (S->quad)
         NPHC_CK(launch_quad_track(S->n, quad_with_gamma(S, o), ctl, v, wl, 0, st));
-    else if (!f32 && list != nullptr &&
-             (o->threads_per_path == 32 || (o->threads_per_path == 0 && S->N < 12)))   // one path per warp
+    else if (!f32 && list != nullptr && o->threads_per_path != 1)   // one path per warp
         NPHC_CK(launch_xy_track_f64_warp_bps(S->M, xs, ctl, v, wl, o->list_blocks_per_sm, st));
     else if (!f32 && list != nullptr)   // FP64 lists, one path per thread, full warps
         NPHC_CK(launch_xy_track_f64(S->M, xs, ctl, v, wl, 0, 0, st));

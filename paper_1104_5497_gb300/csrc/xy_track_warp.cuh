@@ -17,9 +17,11 @@
 //   * the back substitution in registers (right-hand side r on lanes 16 r + row);
 //   * the compensated residual of row pair k on lanes k and 16 + k.
 // The step logic (RK4 predictor, Newton corrector, step control, divergence radius,
-// budget) is the per-thread FP64 tracker's, as are the equations and the scaled
-// light-cone frames of the Schur reduction (xy_solve.cuh): the same algorithm, with a
-// different linear solver, so the endpoints agree to the tracking tolerance.
+// budget) is the per-thread FP64 tracker's, as are the state in light-cone coordinates,
+// the equations and the scaled light-cone frames of the Schur reduction (xy_solve.cuh):
+// the same algorithm with a different linear solver, so the endpoints agree to the
+// tracking tolerance.  The Cauchy endgame (cauchy_warp.cuh) calls the same solve and
+// residual on points in (x, y).
 //
 // Storage: everything of a path in per-warp shared memory (complex doubles): the
 // augmented Schur matrix [S | b0 | b1] (column-major, M x (M + 2)), the five step
@@ -101,11 +103,14 @@ struct WarpPath {
     __device__ __forceinline__ cx<double> &A(int i, int c) const { return s[WarpLayout<M>::A + c * M + i]; }
 };
 
-// -H(z, t) at ZC into W1 with compensated sums (the per-thread tracker's xy_residual_comp
-// in (x, y)).  Row pair k: lane k sums u_k = J_kN + sum_l J_kl x_l and forms the f row,
-// lane 16 + k sums w_k = sum_l J_kl y_l, forms the g row (which needs no sums) and hands
-// its share of f_k = y_k u_k - x_k w_k to lane k.
-template <int M>
+// -H(z, t) at ZC into W1 with compensated sums (the per-thread trackers' residuals).
+// LC == false: ZC holds (x, y) (the Cauchy endgame); row pair k: lane k sums
+// u_k = J_kN + sum_l J_kl x_l and forms the f row, lane 16 + k sums w_k = sum_l J_kl y_l,
+// forms the g row (which needs no sums) and hands its share of f_k = y_k u_k - x_k w_k to
+// lane k.  LC == true: ZC holds the light-cone coordinates (p, q) (xy_residual_comp in
+// xy_solve.cuh); lane k sums U_p,k, lane 16 + k sums U_q,k, and D_k = q_k U_p,k - p_k U_q,k
+// is formed the same way.
+template <int M, bool LC = false>
 __device__ void warp_residual(const WarpPath<M> &P, const double *__restrict__ J, double s,
                               double omt, cx<double> gam) {
     static_assert(M <= 16, "one row pair per lane pair");
@@ -114,76 +119,126 @@ __device__ void warp_residual(const WarpPath<M> &P, const double *__restrict__ J
     const int k = P.lane & 15;
     const bool hi = P.lane >= 16;
     const ext<double> zero = {0.0, 0.0};
-    ext<double> fre = zero, fim = zero;   // lane k: the y u part of f; lane 16 + k: the -x w part
-    cx<double> xk = cx<double>{0.0, 0.0}, yk = xk;
+    ext<double> fre = zero, fim = zero;   // lane k's and lane 16 + k's shares of f (or D)
+    cx<double> zk = cx<double>{0.0, 0.0}, wk = zk;   // (x_k, y_k) or (p_k, q_k)
     const cx<double> gomt = cx<double>{E::mul(omt, gam.re), E::mul(omt, gam.im)};
     if (k < M) {
-        xk = P.at(L::ZC, k);
-        yk = P.at(L::ZC, M + k);
+        zk = P.at(L::ZC, k);
+        wk = P.at(L::ZC, M + k);
         const double *Jk = J + k * NPHC_JSTRIDE;
         const int off = hi ? L::ZC + M : L::ZC;
-        ext<double> sre = {hi ? 0.0 : Jk[M], 0.0}, sim = zero;
+        ext<double> sre = {(hi && !LC) ? 0.0 : Jk[M], 0.0}, sim = zero;
 #pragma unroll 1
         for (int l = 0; l < M; l++) {   // J_kk = 0 adds exact zeros
             const cx<double> v = P.at(off, l);
             ext_acc(sre, Jk[l], v.re);
             ext_acc(sim, Jk[l], v.im);
         }
-        if (!hi) {
-            ext_acc_ext(fre, yk.re, sre);
-            ext_acc_ext(fre, -yk.im, sim);
-            ext_acc_ext(fim, yk.re, sim);
-            ext_acc_ext(fim, yk.im, sre);
-        } else {
-            ext_acc_ext(fre, -xk.re, sre);
-            ext_acc_ext(fre, xk.im, sim);
-            ext_acc_ext(fim, -xk.re, sim);
-            ext_acc_ext(fim, -xk.im, sre);
-        }
+        // (x, y): lane k y_k u_k, lane 16 + k -x_k w_k;  (p, q): lane k q_k U_p, lane 16 + k -p_k U_q
+        const cx<double> c = hi ? cx<double>{-zk.re, -zk.im} : wk;
+        ext_acc_ext(fre, c.re, sre);
+        ext_acc_ext(fre, -c.im, sim);
+        ext_acc_ext(fim, c.re, sim);
+        ext_acc_ext(fim, c.im, sre);
     }
-    const ext<double> wre = shfl_down16(fre), wim = shfl_down16(fim);
+    const ext<double> ore = shfl_down16(fre), oim = shfl_down16(fim);
     if (k < M) {
-        ext<double> qxr = {-1.0, 0.0}, qxi = zero;
-        ext_acc(qxr, xk.re, xk.re);
-        ext_acc(qxr, -xk.im, xk.im);
-        ext_acc(qxi, 2.0 * xk.re, xk.im);
-        if (!hi) {
-            fre = ext_add(fre, wre);
-            fim = ext_add(fim, wim);
-            ext<double> hfr = zero, hfi = zero;
-            ext_acc_ext(hfr, gomt.re, qxr);
-            ext_acc_ext(hfr, -gomt.im, qxi);
-            ext_acc_ext(hfr, s, fre);
-            ext_acc_ext(hfi, gomt.re, qxi);
-            ext_acc_ext(hfi, gomt.im, qxr);
-            ext_acc_ext(hfi, s, fim);
-            P.at(L::W1, k) = cx<double>{-ext_val(hfr), -ext_val(hfi)};
+        if (!LC) {
+            const cx<double> xk = zk, yk = wk;
+            ext<double> qxr = {-1.0, 0.0}, qxi = zero;
+            ext_acc(qxr, xk.re, xk.re);
+            ext_acc(qxr, -xk.im, xk.im);
+            ext_acc(qxi, 2.0 * xk.re, xk.im);
+            if (!hi) {
+                fre = ext_add(fre, ore);
+                fim = ext_add(fim, oim);
+                ext<double> hfr = zero, hfi = zero;
+                ext_acc_ext(hfr, gomt.re, qxr);
+                ext_acc_ext(hfr, -gomt.im, qxi);
+                ext_acc_ext(hfr, s, fre);
+                ext_acc_ext(hfi, gomt.re, qxi);
+                ext_acc_ext(hfi, gomt.im, qxr);
+                ext_acc_ext(hfi, s, fim);
+                P.at(L::W1, k) = cx<double>{-ext_val(hfr), -ext_val(hfi)};
+            } else {
+                ext<double> qyr = {-1.0, 0.0}, qyi = zero;
+                ext_acc(qyr, yk.re, yk.re);
+                ext_acc(qyr, -yk.im, yk.im);
+                ext_acc(qyi, 2.0 * yk.re, yk.im);
+                ext<double> hgr = zero, hgi = zero;
+                ext_acc_ext(hgr, gomt.re, qyr);
+                ext_acc_ext(hgr, -gomt.im, qyi);
+                ext_acc_ext(hgr, s, qxr);
+                ext_acc_ext(hgr, s, qyr);
+                ext_acc(hgr, s, 1.0);
+                ext_acc_ext(hgi, gomt.re, qyi);
+                ext_acc_ext(hgi, gomt.im, qyr);
+                ext_acc_ext(hgi, s, qxi);
+                ext_acc_ext(hgi, s, qyi);
+                P.at(L::W1, M + k) = cx<double>{-ext_val(hgr), -ext_val(hgi)};
+            }
         } else {
-            ext<double> qyr = {-1.0, 0.0}, qyi = zero;
-            ext_acc(qyr, yk.re, yk.re);
-            ext_acc(qyr, -yk.im, yk.im);
-            ext_acc(qyi, 2.0 * yk.re, yk.im);
-            ext<double> hgr = zero, hgi = zero;
-            ext_acc_ext(hgr, gomt.re, qyr);
-            ext_acc_ext(hgr, -gomt.im, qyi);
-            ext_acc_ext(hgr, s, qxr);
-            ext_acc_ext(hgr, s, qyr);
-            ext_acc(hgr, s, 1.0);
-            ext_acc_ext(hgi, gomt.re, qyi);
-            ext_acc_ext(hgi, gomt.im, qyr);
-            ext_acc_ext(hgi, s, qxi);
-            ext_acc_ext(hgi, s, qyi);
-            P.at(L::W1, M + k) = cx<double>{-ext_val(hgr), -ext_val(hgi)};
+            const cx<double> pk = zk, qk = wk;
+            const double hs = 0.5 * s;
+            if (!hi) {
+                // H_f = gomt X + t f, f = i D / 2, X = x^2 - 1 = (p^2 + 2 p q + q^2) / 4 - 1
+                const ext<double> dr = ext_add(fre, ore), di = ext_add(fim, oim);
+                ext<double> xr = {-1.0, 0.0}, xi = zero;
+                ext_acc(xr, 0.25 * pk.re, pk.re);
+                ext_acc(xr, -0.25 * pk.im, pk.im);
+                ext_acc(xr, 0.5 * pk.re, qk.re);
+                ext_acc(xr, -0.5 * pk.im, qk.im);
+                ext_acc(xr, 0.25 * qk.re, qk.re);
+                ext_acc(xr, -0.25 * qk.im, qk.im);
+                ext_acc(xi, 0.5 * pk.re, pk.im);
+                ext_acc(xi, 0.5 * pk.re, qk.im);
+                ext_acc(xi, 0.5 * pk.im, qk.re);
+                ext_acc(xi, 0.5 * qk.re, qk.im);
+                ext<double> hfr = zero, hfi = zero;
+                ext_acc_ext(hfr, gomt.re, xr);
+                ext_acc_ext(hfr, -gomt.im, xi);
+                ext_acc_ext(hfr, -hs, di);
+                ext_acc_ext(hfi, gomt.re, xi);
+                ext_acc_ext(hfi, gomt.im, xr);
+                ext_acc_ext(hfi, hs, dr);
+                P.at(L::W1, k) = cx<double>{-ext_val(hfr), -ext_val(hfi)};
+            } else {
+                // H_g = gomt Y + t G, Y = y^2 - 1 = -(p^2 - 2 p q + q^2) / 4 - 1, G = p q - 1
+                ext<double> yr = {-1.0, 0.0}, yi = zero, gr = {-1.0, 0.0}, gi = zero;
+                ext_acc(yr, -0.25 * pk.re, pk.re);
+                ext_acc(yr, 0.25 * pk.im, pk.im);
+                ext_acc(yr, 0.5 * pk.re, qk.re);
+                ext_acc(yr, -0.5 * pk.im, qk.im);
+                ext_acc(yr, -0.25 * qk.re, qk.re);
+                ext_acc(yr, 0.25 * qk.im, qk.im);
+                ext_acc(yi, -0.5 * pk.re, pk.im);
+                ext_acc(yi, 0.5 * pk.re, qk.im);
+                ext_acc(yi, 0.5 * pk.im, qk.re);
+                ext_acc(yi, -0.5 * qk.re, qk.im);
+                ext_acc(gr, pk.re, qk.re);
+                ext_acc(gr, -pk.im, qk.im);
+                ext_acc(gi, pk.re, qk.im);
+                ext_acc(gi, pk.im, qk.re);
+                ext<double> hgr = zero, hgi = zero;
+                ext_acc_ext(hgr, gomt.re, yr);
+                ext_acc_ext(hgr, -gomt.im, yi);
+                ext_acc_ext(hgr, s, gr);
+                ext_acc_ext(hgi, gomt.re, yi);
+                ext_acc_ext(hgi, gomt.im, yr);
+                ext_acc_ext(hgi, s, gi);
+                P.at(L::W1, M + k) = cx<double>{-ext_val(hgr), -ext_val(hgi)};
+            }
         }
     }
     __syncwarp();
 }
 
-// H_z(ZC, t) d = r, the per-thread xy_solve's Schur reduction shared out over the warp.
+// H_z(ZC, t) d = r, the per-thread xy_solve's Schur reduction shared out over the warp;
+// ZC and d in (x, y) (LC == false) or in the light-cone coordinates (p, q).
 //   two_rhs false: r = -H_t, d into W1.
 //   two_rhs true:  r1 = W1 (the residual), d1 into W1; r2 = -H_t, d2 into `out2`.
 // Returns false (in every lane) when S is singular or the result is not finite.
-template <int M>
+template <int M, bool LC = false>
 __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, double s,
                            double omt, cx<double> gam, bool two_rhs, int out2) {
     static_assert(M <= 16, "one site per lane of each half-warp");
@@ -194,13 +249,14 @@ __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, d
     const cx<double> sg = cx<double>{s + gomt.re, gomt.im};   // t + gamma (1 - t)
     const double hs = 0.5 * s;
 
-    // ---- per-site quantities: u_j on lane j, w_j on lane 16 + j, the rest on lane j
+    // ---- per-site quantities: u_j (U_p,j) on lane j, w_j (U_q,j) on lane 16 + j, the
+    // rest on lane j
     cx<double> uw = cx<double>{0.0, 0.0};
     if (hrow < M) {
         const int j = hrow;
         const double *Jj = J + j * NPHC_JSTRIDE;
         const int off = r ? L::ZC + M : L::ZC;
-        uw = cx<double>{r ? 0.0 : Jj[M], 0.0};
+        uw = cx<double>{(r && !LC) ? 0.0 : Jj[M], 0.0};
 #pragma unroll 1
         for (int l = 0; l < M; l++) {
             const cx<double> v = P.at(off, l);
@@ -212,18 +268,29 @@ __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, d
     if (lane < M) {
         const int j = lane;
         const cx<double> u = uw;
-        const cx<double> xj = P.at(L::ZC, j), yj = P.at(L::ZC, M + j);
-        cx<double> htf, htg;
-        minus_ht_rows<double>(xj, yj, u, w, gam, htf, htg);
+        const cx<double> zj = P.at(L::ZC, j), wj = P.at(L::ZC, M + j);
+        cx<double> htf, htg, ah, bh, Ajj, Bjj, pj, qj;   // Ajj, Bjj: gradient row j on (dwp_j, dwq_j)
+        double iv, sp, sq;
+        if (LC) {
+            pj = zj;
+            qj = wj;
+            lc_minus_ht_rows<double>(pj, qj, u, w, gam, htf, htg);
+            g_frame_lc<double>(pj, qj, s, gomt, ah, bh, iv, sp, sq);
+            const cx<double> gpq = cmul(gomt, cadd(pj, qj));
+            Ajj = cscale(0.5 * sp, csub(gpq, cmul_i(cscale(s, w))));
+            Bjj = cscale(0.5 * sq, cadd(gpq, cmul_i(cscale(s, u))));
+        } else {
+            const cx<double> xj = zj, yj = wj;
+            pj = cx<double>{xj.re - yj.im, xj.im + yj.re};
+            qj = cx<double>{xj.re + yj.im, xj.im - yj.re};
+            minus_ht_rows<double>(xj, yj, u, w, gam, htf, htg);
+            g_frame<double>(xj, yj, s, sg, ah, bh, iv, sp, sq);
+            lc_coef<double>(cx<double>{-s * w.re + 2.0 * (gomt.re * xj.re - gomt.im * xj.im),
+                                       -s * w.im + 2.0 * (gomt.re * xj.im + gomt.im * xj.re)},
+                            cscale(s, u), sp, sq, Ajj, Bjj);
+        }
         const cx<double> rf0 = two_rhs ? P.at(L::W1, j) : htf;
         const cx<double> rg0 = two_rhs ? P.at(L::W1, M + j) : htg;
-        cx<double> ah, bh;
-        double iv, sp, sq;
-        g_frame<double>(xj, yj, s, sg, ah, bh, iv, sp, sq);
-        cx<double> Ajj, Bjj;   // diagonal entries of gradient row j on (dwp_j, dwq_j)
-        lc_coef<double>(cx<double>{-s * w.re + 2.0 * (gomt.re * xj.re - gomt.im * xj.im),
-                                   -s * w.im + 2.0 * (gomt.re * xj.im + gomt.im * xj.re)},
-                        cscale(s, u), sp, sq, Ajj, Bjj);
         const cx<double> q0 = cscale(iv, rg0), q1 = cscale(iv, htg);
         const cx<double> px0 = cmulc(ah, q0), py0 = cmulc(bh, q0);
         P.at(L::AH, j) = ah;
@@ -233,8 +300,8 @@ __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, d
         P.at(L::CA, j) = cmul_i(cscale(hs * sq, ah));
         P.at(L::X0, j) = cscale(sp, px0);
         P.at(L::Y0, j) = cscale(sq, py0);
-        P.at(L::PK, j) = cx<double>{xj.re - yj.im, xj.im + yj.re};
-        P.at(L::QK, j) = cx<double>{xj.re + yj.im, xj.im - yj.re};
+        P.at(L::PK, j) = pj;
+        P.at(L::QK, j) = qj;
         P.at(L::QS0, j) = q0;
         // the diagonal entry, and the diagonal's own terms of the right-hand sides
         P.A(j, j) = csub(cmul(Ajj, bh), cmul(Bjj, ah));
@@ -343,15 +410,20 @@ __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, d
         }
     }
 
-    // ---- back to (dx, dy): site j of right-hand side r on lane 16 r + j,
-    // (dwp, dwq) = conj(a^, b^) q_j + (b^, -a^) s_j
+    // ---- back to (dx, dy) or (dp, dq) = (sp dwp, sq dwq): site j of right-hand side r on
+    // lane 16 r + j, (dwp, dwq) = conj(a^, b^) q_j + (b^, -a^) s_j
     double chk = 0.0;
     if (act && hrow < M) {
         const int j = hrow;
-        const cx<double> sc = P.at(L::SS, j);
+        const cx<double> sc = P.at(L::SS, j), ah = P.at(L::AH, j), bh = P.at(L::BH, j);
+        const cx<double> qv = P.at(r ? L::QS1 : L::QS0, j);
         cx<double> dx, dy;
-        lc_step<double>(P.at(L::AH, j), P.at(L::BH, j), sc.re, sc.im, P.at(r ? L::QS1 : L::QS0, j), cur,
-                        dx, dy);
+        if (LC) {
+            dx = cscale(sc.re, cadd(cmulc(ah, qv), cmul(bh, cur)));
+            dy = cscale(sc.im, csub(cmulc(bh, qv), cmul(ah, cur)));
+        } else {
+            lc_step<double>(ah, bh, sc.re, sc.im, qv, cur, dx, dy);
+        }
         chk = cabs2(dx) + cabs2(dy);
         const int o = r ? out2 : L::W1;   // W1's entries j and M + j were read above only
         P.at(o, j) = dx;
@@ -362,7 +434,11 @@ __device__ bool warp_solve(const WarpPath<M> &P, const double *__restrict__ J, d
     return ok && isfinite(chk);
 }
 
-// One path per warp; the control flow of track_body in FP64, uniform over the warp.
+// One path per warp; the control flow of track_body in FP64, uniform over the warp.  The
+// path's state is in light-cone coordinates (p_k, q_k) = (x_k + i y_k, x_k - i y_k), like
+// the per-thread trackers' (xy_track.cuh): near infinity one of them is far below x_k and
+// y_k, and in (x, y) FP64 would lose it to cancellation.  Norms are those of (x, y):
+// ||(x, y)||_2 = sqrt(1/2) ||(p, q)||_2 and ||(x, y)||_inf = max_k max(|p + q|, |p - q|) / 2.
 template <int M, int WARPS>
 __global__ void __launch_bounds__(32 * WARPS)
     xy_track_warp64_kernel(const __grid_constant__ XYSys S, const __grid_constant__ XYCtl C,
@@ -388,7 +464,13 @@ __global__ void __launch_bounds__(32 * WARPS)
         double t, h, hacc;
         bool need_k1;
         if (C.resume) {
-            if (i < NV) P.at(L::Z0, i) = cx<double>{ep.z_re[i * cnt + e], ep.z_im[i * cnt + e]};
+            if (lane < M) {   // (x, y) to (p, q)
+                const int k = lane;
+                const double xr = ep.z_re[k * cnt + e], xi = ep.z_im[k * cnt + e];
+                const double yr = ep.z_re[(M + k) * cnt + e], yi = ep.z_im[(M + k) * cnt + e];
+                P.at(L::Z0, k) = cx<double>{xr - yi, xi + yr};
+                P.at(L::Z0, M + k) = cx<double>{xr + yi, xi - yr};
+            }
             t = ep.t[e];
             h = fmin(fmax(ep.h[e], 0.125 * (1.0 - t)), C.hmax);
             h = fmax(h, C.hmin * 4.0);
@@ -413,8 +495,17 @@ __global__ void __launch_bounds__(32 * WARPS)
                 cx<double> rf, rg;
                 minus_ht_rows<double>(xk, yk, u, w, gam, rf, rg);
                 const cx<double> ig = crecip(gam);
-                P.at(L::K1, k) = cscale(0.5 * xk.re, cmul(ig, rf));
-                P.at(L::K1, M + k) = cscale(0.5 * yk.re, cmul(ig, rg));
+                const cx<double> dx = cscale(0.5 * xk.re, cmul(ig, rf));
+                const cx<double> dy = cscale(0.5 * yk.re, cmul(ig, rg));
+                P.at(L::K1, k) = cadd(dx, cmul_i(dy));       // dp = dx + i dy
+                P.at(L::K1, M + k) = csub(dx, cmul_i(dy));   // dq = dx - i dy
+            }
+            __syncwarp();
+            if (lane < M) {   // p = x + i y, q = x - i y (x, y real at the start)
+                const int k = lane;
+                const double xk = P.at(L::Z0, k).re, yk = P.at(L::Z0, M + k).re;
+                P.at(L::Z0, k) = cx<double>{xk, yk};
+                P.at(L::Z0, M + k) = cx<double>{xk, -yk};
             }
             t = 0.0;
             h = C.h0;
@@ -452,8 +543,8 @@ __global__ void __launch_bounds__(32 * WARPS)
                     }
                     __syncwarp();
                 }
-                if (corr) warp_residual<M>(P, J, te, 1.0 - te, gam);
-                const bool oks = warp_solve<M>(P, J, te, 1.0 - te, gam, corr, L::AC);
+                if (corr) warp_residual<M, true>(P, J, te, 1.0 - te, gam);
+                const bool oks = warp_solve<M, true>(P, J, te, 1.0 - te, gam, corr, L::AC);
                 solves++;
                 if (ph == 0) {   // pull the resumed point onto the FP64 path; dz/dt there
                     if (i < NV) {
@@ -480,12 +571,12 @@ __global__ void __launch_bounds__(32 * WARPS)
                             P.at(L::ZC, i) = zp;
                             zz = cabs2(zp);
                         }
-                        zpn = sqrt(warp_sum(zz));
+                        zpn = sqrt(0.5 * warp_sum(zz));
                     }
                     __syncwarp();
                 } else {
                     newton++;
-                    const double dn = sqrt(warp_sum(i < NV ? cabs2(P.at(L::W1, i)) : 0.0));
+                    const double dn = sqrt(0.5 * warp_sum(i < NV ? cabs2(P.at(L::W1, i)) : 0.0));
                     if (!oks || !isfinite(dn)) {
                         bad = true;
                     } else if (ph == 4 && dn > C.trust * (1.0 + zpn)) {
@@ -497,7 +588,7 @@ __global__ void __launch_bounds__(32 * WARPS)
                             P.at(L::ZC, i) = zn;
                             zz = cabs2(zn);
                         }
-                        zz = warp_sum(zz);
+                        zz = 0.5 * warp_sum(zz);
                         if (dn <= C.eps * (1.0 + sqrt(zz))) conv = true;
                     }
                     __syncwarp();
@@ -506,12 +597,14 @@ __global__ void __launch_bounds__(32 * WARPS)
             if (status != NPHC_PATH_RUNNING) break;
             attempts++;
             if (conv) {
-                double zi = 0.0;
+                double zi = 0.0;   // ||(x, y)||_inf
                 if (i < NV) {
-                    const cx<double> v = P.at(L::ZC, i);
-                    P.at(L::Z0, i) = v;
+                    P.at(L::Z0, i) = P.at(L::ZC, i);
                     P.at(L::K1, i) = P.at(L::AC, i);
-                    zi = sqrt(cabs2(v));
+                }
+                if (lane < M) {
+                    const cx<double> pk = P.at(L::ZC, lane), qk = P.at(L::ZC, M + lane);
+                    zi = 0.5 * sqrt(fmax(cabs2(cadd(pk, qk)), cabs2(csub(pk, qk))));
                 }
                 zi = warp_max(zi);
                 __syncwarp();
@@ -535,10 +628,13 @@ __global__ void __launch_bounds__(32 * WARPS)
             }
             if (status == NPHC_PATH_RUNNING && attempts >= C.max_steps) status = NPHC_PATH_STEP_BUDGET;
         }
-        if (i < NV) {
-            const cx<double> v = P.at(L::Z0, i);
-            ep.z_re[i * cnt + e] = v.re;
-            ep.z_im[i * cnt + e] = v.im;
+        if (lane < M) {   // x = (p + q) / 2, y = -i (p - q) / 2
+            const int k = lane;
+            const cx<double> pk = P.at(L::Z0, k), qk = P.at(L::Z0, M + k);
+            ep.z_re[k * cnt + e] = 0.5 * (pk.re + qk.re);
+            ep.z_im[k * cnt + e] = 0.5 * (pk.im + qk.im);
+            ep.z_re[(M + k) * cnt + e] = 0.5 * (pk.im - qk.im);
+            ep.z_im[(M + k) * cnt + e] = -0.5 * (pk.re - qk.re);
         }
         if (lane == 0) {
             ep.t[e] = t;

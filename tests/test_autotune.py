@@ -43,7 +43,7 @@ def test_apply_copies_the_options():
 
 def test_candidates_list_the_defaults_first():
     assert A.STEP_CANDIDATES[0] == (3, 1e-5)
-    assert A.THREADS_PER_PATH[0] == 0 and set(A.THREADS_PER_PATH) == {0, 1, 32}
+    assert A.THREADS_PER_PATH[0] == 0 and set(A.THREADS_PER_PATH) == {0, 1}
 
 
 def test_apply_sets_threads_per_path_and_step_control():
