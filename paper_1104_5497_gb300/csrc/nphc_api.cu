@@ -125,6 +125,8 @@ struct nphc_result {
     int64_t *o_path;
     void *ws;
     size_t ws_bytes;
+    void *eg_s;              // the refinement's Schur matrices (XY rings), eg_s_threads of them
+    int64_t eg_s_threads;
     cudaStream_t stream;
     cudaStream_t side;        // second stream of the mixed pipeline (refinement beside the
     cudaEvent_t ev_fork, ev_join;   // FP64 continuation), forked and joined by events
@@ -652,6 +654,18 @@ nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
     const int64_t P = S->npaths;
     const int n = S->n, M = S->M;
     const WsLayout L = ws_layout(n, P);
+    // the refinement's M x M Schur matrices in global memory, one per thread of its largest
+    // launch (four one-warp blocks per SM, at most one thread per path)
+    int64_t eg_threads = 0;
+    if (!S->quad) {
+        int dev = 0, sms = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(NPHC_ECUDA, "no CUDA device");
+        }
+        eg_threads = std::min<int64_t>((P + 31) / 32 * 32, (int64_t)4 * 32 * sms);
+    }
     // sub-allocation plan
     std::vector<size_t> sz = {
         sizeof(int64_t) * P,            // 0 path
@@ -690,7 +704,8 @@ nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
         sizeof(double) * P,             // 33 o_logdet
         sizeof(int32_t) * P,            // 34 cycle
         sizeof(int32_t) * P,            // 35 egst
-        sizeof(int32_t) * P};           // 36 egtrack
+        sizeof(int32_t) * P,            // 36 egtrack
+        sizeof(double) * 2 * M * M * eg_threads};   // 37 refinement Schur matrices
     std::vector<size_t> off(sz.size());
     size_t tot = 0;
     for (size_t i = 0; i < sz.size(); i++) {
@@ -752,6 +767,8 @@ nphc_status nphc_result_create(const nphc_system *S, nphc_result **out) {
     R->cycle = (int32_t *)at(34);
     R->egst = (int32_t *)at(35);
     R->egtrack = (int32_t *)at(36);
+    R->eg_s = eg_threads > 0 ? at(37) : nullptr;
+    R->eg_s_threads = eg_threads;
     R->ws_bytes = L.total;
     R->stream = nullptr;
     R->solved = false;
@@ -835,7 +852,7 @@ nphc_status solve_into_impl(const nphc_system *S, const nphc_options *o, nphc_re
         // hand-offs: refinement at t = 1 straight from the hand-off point (certified ones
         // are done), then FP64 continuation of the others
         NPHC_CK(launch_compact(v, PRED_HANDOFF, R->flags, R->list[0], R->lcount + 0, st));
-        WorkList l0 = {R->list[0], R->lcount + 0, nullptr, nullptr, 0};
+        WorkList l0 = {R->list[0], R->lcount + 0, nullptr, R->eg_s, R->eg_s_threads};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
                                          R->P, l0, 1, st));
         NPHC_CK(launch_compact(v, PRED_HANDOFF, R->flags, R->list[0], R->lcount + 5, st));
@@ -847,7 +864,7 @@ nphc_status solve_into_impl(const nphc_system *S, const nphc_options *o, nphc_re
         NPHC_CK(cudaEventRecord(R->ev_fork, st));
         NPHC_CK(cudaStreamWaitEvent(R->side, R->ev_fork, 0));
         NPHC_CK(launch_compact(v, PRED_REACHED_DIRECT, R->flags, R->list[3], R->lcount + 3, R->side));
-        WorkList l3 = {R->list[3], R->lcount + 3, nullptr, nullptr, 0};
+        WorkList l3 = {R->list[3], R->lcount + 3, nullptr, R->eg_s, R->eg_s_threads};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
                                          R->P, l3, 0, R->side));
         NPHC_CK(cudaEventRecord(R->ev_join, R->side));
@@ -856,14 +873,14 @@ nphc_status solve_into_impl(const nphc_system *S, const nphc_options *o, nphc_re
         NPHC_CK(cudaStreamWaitEvent(st, R->ev_join, 0));
         // then the continued entries (the shortcut's certified ones included) that reached t = 1
         NPHC_CK(launch_compact(v, PRED_REACHED_CONTINUED, R->flags, R->list[0], R->lcount + 7, st));
-        WorkList l0c = {R->list[0], R->lcount + 7, nullptr, nullptr, 0};
+        WorkList l0c = {R->list[0], R->lcount + 7, nullptr, R->eg_s, R->eg_s_threads};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
                                          R->P, l0c, 0, st));
         // FP64 re-track from t = 0 of FP32 endpoints that did not certify
         NPHC_CK(launch_compact(v, PRED_UNCERTIFIED_FP32, R->flags, R->list[1], R->lcount + 1, st));
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[1], R->lcount + 1, false, true, R->ws, 2, st)))
             return s;
-        WorkList l1 = {R->list[1], R->lcount + 1, nullptr, nullptr, 0};
+        WorkList l1 = {R->list[1], R->lcount + 1, nullptr, R->eg_s, R->eg_s_threads};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
                                          R->P, l1, 0, st));
         // deduplicate; every path of a solution reached more than once is re-tracked in
@@ -873,7 +890,7 @@ nphc_status solve_into_impl(const nphc_system *S, const nphc_options *o, nphc_re
         NPHC_CK(launch_flag_list(R->list[2], R->lcount + 2, R->P, R->flags, FLAG_RETRACKED_DUP, st));
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, R->list[2], R->lcount + 2, false, true, R->ws, 3, st)))
             return s;
-        WorkList l2 = {R->list[2], R->lcount + 2, nullptr, nullptr, 0};
+        WorkList l2 = {R->list[2], R->lcount + 2, nullptr, R->eg_s, R->eg_s_threads};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
                                          R->P, l2, 0, st));
         // a solution still reached twice means a path jumped in FP64 too: its paths are
@@ -888,7 +905,7 @@ nphc_status solve_into_impl(const nphc_system *S, const nphc_options *o, nphc_re
         strict.trust = o->trust / 8.0;
         if ((s = track_impl(S, &strict, NPHC_PREC_FP64, ep, R->list[0], R->lcount + 0, false, true, R->ws, 4, st)))
             return s;
-        WorkList l0s = {R->list[0], R->lcount + 0, nullptr, nullptr, 0};
+        WorkList l0s = {R->list[0], R->lcount + 0, nullptr, R->eg_s, R->eg_s_threads};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
                                          R->P, l0s, 0, st));
         NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st, R->list[0], R->lcount + 0));
@@ -896,7 +913,7 @@ nphc_status solve_into_impl(const nphc_system *S, const nphc_options *o, nphc_re
         if ((s = track_impl(S, o, NPHC_PREC_FP64, ep, nullptr, nullptr, false, false, R->ws, 0, st)))
             return s;
         NPHC_CK(launch_compact(v, PRED_REACHED, R->flags, R->list[3], R->lcount + 3, st));
-        WorkList l3 = {R->list[3], R->lcount + 3, nullptr, nullptr, 0};
+        WorkList l3 = {R->list[3], R->lcount + 3, nullptr, R->eg_s, R->eg_s_threads};
         NPHC_CK(launch_xy_refine_certify(S->M, xs, o->tol_sol, o->refine_eps, o->refine_iters, v,
                                          R->P, l3, 0, st));
         NPHC_CK(launch_dedup(v, R->n, kDedupDelta, dsc, nullptr, nullptr, st));

@@ -56,7 +56,9 @@ cudaError_t NPHC_CAT(launch_quad_refine_certify_n, NPHC_QUAD_NV)(const QSys &sys
     if (e != cudaSuccess) return e;
     const int64_t need = (cap + EG_BLOCK - 1) / EG_BLOCK;
     const int grid = (int)(need < full ? need : full);
-    k<<<grid, EG_BLOCK, smem, st>>>(sys, tol_sol, refine_eps, refine_iters, ep, wl);
+    WorkList w = wl;
+    w.state = nullptr;   // S in shared memory (the launch is sized for it)
+    k<<<grid, EG_BLOCK, smem, st>>>(sys, tol_sol, refine_eps, refine_iters, ep, w);
     nphc_launch_counter(1);
     return cudaGetLastError();
 }

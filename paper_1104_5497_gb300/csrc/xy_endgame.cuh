@@ -50,11 +50,13 @@ struct EGVec {
     __device__ __forceinline__ void set(int i, cx<double> v) const { p[i * EG_BLOCK] = v; }
 };
 
-// Per-thread working set of the endgame (complex doubles, in this order).
+// Per-thread working set of the endgame (complex doubles, in this order).  The M x M
+// matrix S comes last: in shared memory with the rest, or (refinement launches given a
+// scratch buffer) in global memory, interleaved across the launch's threads, so that the
+// shared part alone sets the occupancy.
 template <int M>
 struct EGLayout {
-    static constexpr int S = 0;                 // M x M, column-major: entry (i, c) at c M + i
-    static constexpr int TQ = S + M * M;        // conj(tau) of the reflectors
+    static constexpr int TQ = 0;                // conj(tau) of the reflectors
     static constexpr int AH = TQ + M;           // frame a^
     static constexpr int BH = AH + M;           // frame b^
     static constexpr int IV = BH + M;           // iv (real part)
@@ -64,18 +66,24 @@ struct EGLayout {
     static constexpr int Y = X + M;             // s_1..s_M
     static constexpr int R = Y + M;             // right-hand side / residual, 2M
     static constexpr int D = R + 2 * M;         // solution, 2M
-    static constexpr int TOTAL = D + 2 * M;
+    static constexpr int S = D + 2 * M;         // M x M, column-major: entry (i, c) at c M + i
+    static constexpr int TOTAL = S + M * M;
 };
 
+// Shared memory per thread, with S or without it (S in a global scratch buffer).
 template <int M>
-constexpr size_t eg_smem_per_thread() { return sizeof(cx<double>) * (size_t)EGLayout<M>::TOTAL; }
+constexpr size_t eg_smem_per_thread(bool with_s = true) {
+    return sizeof(cx<double>) * (size_t)(with_s ? EGLayout<M>::TOTAL : EGLayout<M>::S);
+}
 
 template <int M>
 struct EG {
-    cx<double> *base;
+    cx<double> *base;   // this thread's first entry in shared memory (stride EG_BLOCK)
+    cx<double> *sp;     // this thread's entry (0, 0) of S, in shared or global memory
+    int64_t ss;         // S's stride between entries
     __device__ __forceinline__ EGVec v(int off) const { return EGVec{base + off * EG_BLOCK}; }
-    __device__ __forceinline__ cx<double> S(int i, int c) const { return base[(c * M + i) * EG_BLOCK]; }
-    __device__ __forceinline__ void setS(int i, int c, cx<double> a) const { base[(c * M + i) * EG_BLOCK] = a; }
+    __device__ __forceinline__ cx<double> S(int i, int c) const { return sp[(c * M + i) * ss]; }
+    __device__ __forceinline__ void setS(int i, int c, cx<double> a) const { sp[(c * M + i) * ss] = a; }
 };
 
 // P(z) with exact products and double-double sums, rounded once: at ||z|| >> 1 the
@@ -514,15 +522,23 @@ __device__ void eg_real_test(const EG<Q::DIM> &G, const typename Q::Sys &S, cons
 // One warp per block.  Entries are taken 32 at a time; the few that need the real test
 // (about one in thirty at N = 10) go to a per-warp queue that is drained 32 at a time,
 // so that the test runs on full warps instead of costing most warps a pass with one
-// active lane.
+// active lane.  With wl.state set (a scratch buffer of at least gridDim.x x EG_BLOCK
+// threads' matrices), S lives there: the launch then needs shared memory for the rest
+// only, and fits more warps per SM (GB300's FP64 pipes are per SM sub-partition: at M = 9
+// four warps use all four where the 3 KB per thread of the whole set allowed two).
 template <class Q>
 __device__ __forceinline__ void refine_body(const typename Q::Sys &S, double tol_sol,
                                             double refine_eps, int refine_iters, const EPView &ep,
                                             const WorkList &wl, int shortcut) {
+    using L = EGLayout<Q::DIM>;
     extern __shared__ __align__(16) unsigned char egraw[];
     __shared__ int64_t rq[2 * EG_BLOCK];
     const int lane = threadIdx.x;
-    const EG<Q::DIM> G{reinterpret_cast<cx<double> *>(egraw) + lane};
+    cx<double> *const sb = reinterpret_cast<cx<double> *>(egraw) + lane;
+    const EG<Q::DIM> G = wl.state
+        ? EG<Q::DIM>{sb, reinterpret_cast<cx<double> *>(wl.state) + (int64_t)blockIdx.x * EG_BLOCK + lane,
+                     (int64_t)gridDim.x * EG_BLOCK}
+        : EG<Q::DIM>{sb, sb + L::S * EG_BLOCK, EG_BLOCK};
     const int64_t total = worklist_size(wl, ep.count);
     int qn = 0;   // queued real tests (the same in every lane)
     for (int64_t base = (int64_t)blockIdx.x * EG_BLOCK; base < total;

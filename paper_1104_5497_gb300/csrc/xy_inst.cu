@@ -157,11 +157,15 @@ cudaError_t NPHC_CAT(launch_xy_refine_certify_m, NPHC_INST_M)(const XYSys &sys, 
                                                              cudaStream_t st) {
     if (cap <= 0) return cudaSuccess;
     constexpr int M = NPHC_INST_M;
-    const size_t smem = eg_smem_per_thread<M>() * EG_BLOCK;
+    // with a scratch buffer (wl.state, wl.state_threads threads) S lives there and the
+    // shared memory holds the rest only
+    const bool gs = wl.state != nullptr && wl.state_threads >= EG_BLOCK;
+    const size_t smem = eg_smem_per_thread<M>(!gs) * EG_BLOCK;
     auto k = xy_refine_certify_kernel<M>;
-    static bool attr_set = false;   // once per process for this instantiation
+    static bool attr_set = false;   // once per process for this instantiation (the larger size)
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)(eg_smem_per_thread<M>() * EG_BLOCK));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
@@ -170,11 +174,15 @@ cudaError_t NPHC_CAT(launch_xy_refine_certify_m, NPHC_INST_M)(const XYSys &sys, 
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, EG_BLOCK, smem);
     if (e != cudaSuccess) return e;
-    // grid-stride over the entries: at most every SM filled, at most one entry per thread
+    // grid-stride over the entries: at most every SM filled, at most one entry per thread,
+    // and no more threads than the scratch buffer holds
     const int64_t need = (cap + EG_BLOCK - 1) / EG_BLOCK;
-    const int64_t full = (int64_t)sms * (per > 0 ? per : 1);
+    int64_t full = (int64_t)sms * (per > 0 ? per : 1);
+    if (gs && full > wl.state_threads / EG_BLOCK) full = wl.state_threads / EG_BLOCK;
     const int grid = (int)(need < full ? need : full);
-    k<<<grid, EG_BLOCK, smem, st>>>(sys, tol_sol, refine_eps, refine_iters, ep, wl, shortcut);
+    WorkList w = wl;
+    if (!gs) w.state = nullptr;
+    k<<<grid, EG_BLOCK, smem, st>>>(sys, tol_sol, refine_eps, refine_iters, ep, w, shortcut);
     nphc_launch_counter(1);
     return cudaGetLastError();
 }
