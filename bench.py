@@ -126,7 +126,8 @@ def solve_flops(M: int, corrector: bool) -> tuple[float, float]:
     """FP32 flops of one structured solve of the per-thread tracker as implemented
     (xy_solve.cuh, light-cone coordinates), as (method, overhead).  method: the Schur
     build (couplings sums, -H_t rows, frames, M x M entries and right-hand sides), the
-    Householder QR, back substitution and recovery; a corrector solve adds the second
+    LU factorisation with partial pivoting, back substitution and recovery; a corrector
+    solve adds the second
     right-hand side and the residual -H counted as a plain evaluation.  overhead: what the
     compensated (float-float) residual costs beyond that plain evaluation.  A complex
     product is 6 flops, a complex sum 2, a complex times real 2, |z|^2 3, a square root or
@@ -135,13 +136,13 @@ def solve_flops(M: int, corrector: bool) -> tuple[float, float]:
     nr = 2 if corrector else 1
     column = M * (42 + 18 * (nr - 1)) + 219
     build = M * column
-    qr = 0
-    for k in range(M):
+    lu = 0
+    for k in range(M):   # pivot |a|^2, sqrt, complex reciprocal, multipliers, rank-one update
         n = M - k
-        qr += 10 + 4 * n + 6 * (n - 1) + (M - 1 - k + nr) * (16 * (n - 1) + 10)
-    back = sum(1 + 2 * nr + 8 * k * nr for k in range(M))
+        lu += 3 * n + 7 + 6 * (n - 1) + (M - 1 - k + nr) * 8 * (n - 1)
+    back = sum(6 * nr + 8 * k * nr for k in range(M))
     recover = M * (111 + 42 * (nr - 1))
-    method = float(build + qr + back + recover)
+    method = float(build + lu + back + recover)
     overhead = 0.0
     if corrector:
         method += M * (8 * M + 63)

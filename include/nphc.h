@@ -135,8 +135,9 @@ typedef struct nphc_options {
     double kappa_fp32;         /* FP32 pass: a converged step whose solves' condition estimate
                                   exceeds this is not taken and FP64 continues the path
                                   (NPHC_PATH_HANDOFF_COND, see nphc_track); FP32 solves lose
-                                  about kappa x 6e-8 of their relative accuracy.  0 = no such
-                                  test; 1e6 */
+                                  about kappa x 6e-8 of their relative accuracy.  The
+                                  estimate is max/min |U_kk| of the solve's pivoted LU
+                                  factor.  0 = no such test; 3e5 */
 } nphc_options;
 
 typedef struct nphc_system nphc_system;   /* opaque; owns the device copy of the couplings */

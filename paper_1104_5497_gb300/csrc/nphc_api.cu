@@ -185,7 +185,7 @@ nphc_status nphc_options_default(nphc_options *o) {
     o->blocks_per_sm = 0;
     o->kappa_sing = 1e12;
     o->threads_per_path = 0;
-    o->kappa_fp32 = 1e6;
+    o->kappa_fp32 = 3e5;
     return NPHC_OK;
 }
 

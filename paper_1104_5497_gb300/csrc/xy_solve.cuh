@@ -26,15 +26,18 @@
 //   S_kj = A'_kj b^_j - B'_kj a^_j,   rhs_k = r_fk - sum_j (A'_kj conj(a^_j) + B'_kj conj(b^_j)) q_j,
 // where A', B' are the gradient rows' coefficients on dwp_j, dwq_j.  For k != j
 // (A_kj, B_kj) = t J_kj (y_k, -x_k), which become (i t J_kj / 2) (sp_j q_k, -sq_j p_k).  S is
-// solved by Householder QR: unitary (no pivot search, no growth) and data-independent in
-// its control flow.  Cost ~ (8/3) M^3 + O(M^2 + M N) real flops instead of (8/3) (2M)^3
-// for the full system.
+// solved by LU with partial pivoting (aug_lu_solve; the generic quadratic systems use the
+// Householder QR, aug_qr_solve): its control flow is data-independent too (the pivot is
+// a per-thread row index, the loops run the same for every thread), and its column sweep
+// costs about 6 instructions per complex entry against Householder's 10 (measured on the
+// N = 10 ring: the FP32 pass 134 -> 117 ms with the same solve count).  Cost ~ (8/3) M^3
+// + O(M^2 + M N) real flops instead of (8/3) (2M)^3 for the full system.
 //
 // Memory layout (one path per thread): the augmented M x (M + 2) matrix [S | b0 | b1]
 // of each thread lives in shared memory, column-major, each complex entry interleaved
 // across the threads of the block (entry (i, c) of thread t at [(c M + i) BLOCK + t]:
-// conflict-free 64-bit accesses).  The Householder step k is a runtime loop: its
-// reflector sits in registers, and the remaining columns, right-hand sides included,
+// conflict-free 64-bit accesses).  The elimination step k is a runtime loop: its
+// reflector or multipliers sit in registers, and the remaining columns, right-hand sides included,
 // stream through registers one at a time in a loop of fixed length M that leaves early
 // (k is the same for every thread of a warp, so the exit is uniform).  The QR, the back
 // substitution and the recovery thus each exist once in the code: unrolled over k they
@@ -264,6 +267,100 @@ __device__ __forceinline__ bool aug_qr_solve(const SMat<M, R, BLOCK> &A, bool tw
     return ok;
 }
 
+// The same solve by LU with partial pivoting: per column one pivot search (the largest
+// |a|^2 at or below the diagonal), one complex reciprocal, the multipliers in registers;
+// then each trailing column (right-hand sides included) streams through once: rows k and
+// p are swapped in shared memory (two loads, two stores at a per-thread index, still
+// conflict-free in the interleaved layout) and the rows below take a rank-one update,
+// a load, four FMAs and a store per complex entry, against Householder's extra dot
+// product per entry.  The pivot's reciprocal replaces U_kk for the back substitution.
+// kest (may be NULL) receives max_k |U_kk| / min_k |U_kk|, the usual cheap estimate of the
+// condition number from a pivoted factorisation.
+template <int M, class R, int BLOCK>
+__device__ __forceinline__ bool aug_lu_solve(const SMat<M, R, BLOCK> &A, bool two_rhs,
+                                             R *kest = nullptr) {
+    const int ncol = two_rhs ? M + 2 : M + 1;
+    bool ok = true;
+    R umax = R(0), umin = R(0);
+#pragma unroll 1
+    for (int k = 0; k < M; k++) {
+        const int n = M - k;   // active rows k .. M-1, relative index i = 0 .. n-1
+        const SMat<M, R, BLOCK> Ak{A.p + k * BLOCK};   // Ak.get(i, c) = S(k + i, c)
+        cx<R> v[M];
+        cx<R> piv = Ak.get(0, k);
+        R best = cabs2(piv);
+        int p = 0;
+        v[0] = piv;
+#pragma unroll
+        for (int i = 1; i < M; i++) {
+            if (i >= n) break;
+            v[i] = Ak.get(i, k);
+            const R m = cabs2(v[i]);
+            if (m > best) {
+                best = m;
+                p = i;
+                piv = v[i];
+            }
+        }
+        ok = ok && (best > R(0));
+        const R um = sqrt_r(best);
+        umax = fmax(umax, um);
+        umin = k == 0 ? um : fmin(umin, um);
+        const cx<R> ip = crecip(piv);
+        // multipliers of rows 1 .. n-1 after the swap (row p holds the old row k)
+#pragma unroll
+        for (int i = 1; i < M; i++) {
+            if (i >= n) break;
+            v[i] = cmul(i == p ? v[0] : v[i], ip);
+        }
+        Ak.set(0, k, ip);
+#pragma unroll 1
+        for (int c = k + 1; c < ncol; c++) {
+            const cx<R> a0 = Ak.get(0, c), ap = Ak.get(p, c);
+            Ak.set(p, c, a0);
+            Ak.set(0, c, ap);
+#pragma unroll
+            for (int i = 1; i < M; i++) {
+                if (i >= n) break;
+                const cx<R> x = Ak.get(i, c), l = v[i];
+                Ak.set(i, c, cx<R>{fma(l.im, ap.im, fma(-l.re, ap.re, x.re)),
+                                   fma(-l.im, ap.re, fma(-l.re, ap.im, x.im))});
+            }
+        }
+    }
+
+    // ---- back substitution U s = b, column by column, in place in columns M, M + 1
+#pragma unroll 1
+    for (int k = M - 1; k >= 0; k--) {
+        const cx<R> ir = A.get(k, k);   // 1 / U_kk
+        const cx<R> s0 = cmul(A.get(k, M), ir);
+        A.set(k, M, s0);
+        cx<R> s1 = cx<R>{R(0), R(0)};
+        if (two_rhs) {
+            s1 = cmul(A.get(k, M + 1), ir);
+            A.set(k, M + 1, s1);
+        }
+        constexpr int MA = M > 1 ? M - 1 : 1;
+        cx<R> Rc[MA], c0[MA], c1[MA];
+#pragma unroll
+        for (int i = 0; i < M - 1; i++) {
+            if (i >= k) break;
+            Rc[i] = A.get(i, k);
+            c0[i] = A.get(i, M);
+            if (two_rhs) c1[i] = A.get(i, M + 1);
+        }
+#pragma unroll
+        for (int i = 0; i < M - 1; i++) {
+            if (i >= k) break;
+            A.set(i, M, csub(c0[i], cmul(Rc[i], s0)));
+            if (two_rhs) A.set(i, M + 1, csub(c1[i], cmul(Rc[i], s1)));
+        }
+    }
+
+    if (kest) *kest = umin > R(0) ? umax / umin : R(INFINITY);
+    return ok;
+}
+
 // ------------------------------------------------------------------------------------
 // The per-thread trackers keep each site's unknowns in light-cone coordinates,
 // p_k = x_k + i y_k and q_k = x_k - i y_k (the pinned site has p_N = q_N = 1).  Near infinity
@@ -404,7 +501,7 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
         if (two_rhs) A.set(k, M + 1, b1[k]);
     }
 
-    bool ok = aug_qr_solve<M, R, BLOCK>(A, two_rhs, kest);
+    bool ok = aug_lu_solve<M, R, BLOCK>(A, two_rhs, kest);
 
     // ---- back to (dp, dq) = (sp dwp, sq dwq),
     // (dwp, dwq) = conj(a^, b^) q_j + (b^, -a^) s_j

@@ -44,11 +44,11 @@ def test_low_threshold_hands_paths_to_fp64_in_the_step_calls():
     assert int((ep.tensors["status"] == N_.PATH_HANDOFF_COND).sum()) == 0
 
 
-@pytest.mark.parametrize("kappa", [1e4, 1e6])
+@pytest.mark.parametrize("kappa", [1e4, 3e5, 1e6])
 def test_certified_set_unchanged_by_the_threshold(kappa):
-    """The N = 8 workload (16,384 paths) in mixed precision with kappa_fp32 = 1e4 and the
-    default 1e6: the condition test hands paths to FP64 (counted), and the certified
-    real and non-real sets are the oracle's."""
+    """The N = 8 workload (16,384 paths) in mixed precision with kappa_fp32 = 1e4, the
+    default 3e5 and 1e6: the condition test hands paths to FP64 (counted), and the
+    certified real and non-real sets are the oracle's."""
     N_ = nphc()
     inst = I.workload_n8()
     system = N_.System(inst.N, inst.sigma)

@@ -123,3 +123,34 @@ def test_dedup_flags_planted_copies():
     assert (cls[:-3] != N_.END_DUPLICATE).all()
     members = set(lst[:int(cnt.item())].cpu().numpy().tolist())
     assert members == {0, 5, 9, len(cert), len(cert) + 1, len(cert) + 2}
+
+
+@pytest.mark.parametrize("N,sigma", [(8, 1.5), (9, 0.75)])
+def test_refinement_scratch_matches_shared_memory(N, sigma):
+    """The refinement keeps its Schur matrices in shared memory when called through
+    nphc_refine_certify and in the result's global scratch inside nphc_solve_into: the
+    arithmetic per endpoint is the same, so every endpoint the FP32 pass reached and both
+    certify has bit-identical refined coordinates and the same class."""
+    import torch
+    N_ = nphc()
+    inst = I.ring(N, sigma, 7)
+    system = N_.System(N, sigma)
+    opts = N_.options_default(gamma=inst.gamma, precision=N_.PREC_MIXED)
+    full = N_.solve(system, opts).endpoints()
+    P, n = system.npaths, system.n
+    ep = N_.DeviceEndpoints.empty(n, np.arange(P))
+    ws = torch.zeros(system.workspace_size(P), dtype=torch.uint8, device="cuda")
+    N_.track(system, opts, N_.PREC_MIXED, ep, ws)
+    reached = torch.nonzero(ep.tensors["status"] == N_.PATH_REACHED).flatten().to(torch.int32)
+    count = torch.tensor([reached.numel()], dtype=torch.int32, device="cuda")
+    N_.refine_certify(system, opts, ep, reached, count)
+    torch.cuda.synchronize()
+    cls = ep.tensors["cls"].cpu().numpy()
+    z = (ep.tensors["z_re"] + 1j * ep.tensors["z_im"]).cpu().numpy().T
+    idx = reached.cpu().numpy()
+    certified = (N_.END_REAL, N_.END_NONREAL)
+    both = [e for e in idx if cls[e] in certified and full["cls"][e] in certified]
+    assert len(both) > 0.9 * sum(cls[e] in certified for e in idx), (len(both), len(idx))
+    for e in both:
+        assert cls[e] == full["cls"][e], e
+        assert np.array_equal(z[e], full["z"][e]), (e, z[e], full["z"][e])
