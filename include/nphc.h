@@ -235,9 +235,10 @@ nphc_status nphc_workspace_size(const nphc_system *sys, int64_t count, size_t *b
  * (classical RK4 on dz/dt = -H_z^-1 H_t) and a Newton corrector, in precision prec:
  *   FP64:  plain FP64 tracking;
  *   MIXED: FP32 tracking; a path the FP32 tracker cannot finish ends with status
- *          NPHC_PATH_HANDOFF, or NPHC_PATH_HANDOFF_COND when a step's condition estimate
- *          (max |R_kk| / min |R_kk| of the Householder factor of the step's Schur system)
- *          exceeded opt->kappa_fp32, and its (z, t, h) for an FP64 call with resume = 1.
+ *          NPHC_PATH_HANDOFF, or NPHC_PATH_HANDOFF_COND when a converged step's condition
+ *          estimate (max |U_kk| / min |U_kk| of the pivoted LU factor of the step's Schur
+ *          system) exceeded opt->kappa_fp32, and its (z, t, h) for an FP64 call with
+ *          resume = 1.
  * list (device int32, may be NULL) selects entries list[0 .. *list_count - 1]
  * (list_count: device int32); NULL tracks every entry.  resume = 0 starts each selected
  * path at its start point; resume = 1 continues from ep's (z, t, h).  Writes z, t, h,

@@ -37,10 +37,11 @@
 // of each thread lives in shared memory, column-major, each complex entry interleaved
 // across the threads of the block (entry (i, c) of thread t at [(c M + i) BLOCK + t]:
 // conflict-free 64-bit accesses).  The elimination step k is a runtime loop: its
-// reflector or multipliers sit in registers, and the remaining columns, right-hand sides included,
-// stream through registers one at a time in a loop of fixed length M that leaves early
-// (k is the same for every thread of a warp, so the exit is uniform).  The QR, the back
-// substitution and the recovery thus each exist once in the code: unrolled over k they
+// reflector or multipliers sit in registers, and the remaining columns, right-hand sides
+// included, stream through registers one at a time in a loop of fixed length M that leaves
+// early (k is the same for every thread of a warp, so the exit is uniform).  The
+// factorisation, the back substitution and the recovery thus each exist once in the code:
+// unrolled over k they
 // outgrow the instruction cache from M ~ 8 on, and the kernel stalls on instruction
 // fetch.
 #pragma once

@@ -1,5 +1,5 @@
-"""The condition-estimate hand-off of the mixed-precision pipeline: an FP32 step whose
-Schur system's condition estimate (max |R_kk| / min |R_kk| of its Householder factor)
+"""The condition-estimate hand-off of the mixed-precision pipeline: a converged FP32 step
+whose Schur system's condition estimate (max |U_kk| / min |U_kk| of its pivoted LU factor)
 exceeds kappa_fp32 is not taken, and FP64 continues the path from its last accepted
 point.  Those paths end in FP64, and the certified set is the oracle's whatever the
 threshold."""
