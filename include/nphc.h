@@ -491,7 +491,8 @@ void nphc_result_destroy(nphc_result *res);
  * returns normally.  Writes the first recorded code since the last call and clears it:
  * 0 none, 1 a work-list entry outside the endpoint set, 2 an append beyond a list's
  * capacity, 3 a deduplication link outside the endpoint set, 4 a batch item outside its
- * group, 5 a gathered entry outside the set; -1 in a release build (no checks).
+ * group, 5 a gathered or listed-for-classification entry outside the set; -1 in a release
+ * build (no checks).
  * Synchronous.  NPHC_EINVAL for a NULL code. */
 nphc_status nphc_debug_check(int32_t *code);
 

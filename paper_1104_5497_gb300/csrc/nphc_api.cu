@@ -920,7 +920,16 @@ nphc_status solve_into_impl(const nphc_system *S, const nphc_options *o, nphc_re
     }
     {
         const Range r("classify");
-        NPHC_CK(launch_xy_classify(S->M, xs, v, R->theta, R->index, R->energy, R->mineig, R->logdet, st));
+        // defaults for every entry (theta, energy, |lambda|_min, log|det H| 0; index -1), then
+        // the real stationary points, compacted so that they fill whole warps
+        NPHC_CK(cudaMemsetAsync(R->theta, 0, sizeof(double) * R->M * R->P, st));
+        NPHC_CK(cudaMemsetAsync(R->energy, 0, sizeof(double) * R->P, st));
+        NPHC_CK(cudaMemsetAsync(R->mineig, 0, sizeof(double) * R->P, st));
+        NPHC_CK(cudaMemsetAsync(R->logdet, 0, sizeof(double) * R->P, st));
+        NPHC_CK(cudaMemsetAsync(R->index, 0xff, sizeof(int32_t) * R->P, st));
+        NPHC_CK(launch_real_list(v, R->real_list, R->lcount + 4, st));
+        NPHC_CK(launch_xy_classify(S->M, xs, v, R->theta, R->index, R->energy, R->mineig, R->logdet, st,
+                                   R->real_list, R->lcount + 4));
     }
     if ((s = endgame())) return s;
     NPHC_CK(launch_counts(v, R->flags, R->index, R->counts, st, R->egst, R->cycle));

@@ -247,10 +247,13 @@ cudaError_t launch_xy_track_f64_warp(int M, const XYSys &sys, const XYCtl &ctl, 
 cudaError_t launch_xy_refine_certify(int M, const XYSys &sys, double tol_sol, double refine_eps,
                                      int refine_iters, const EPView &ep, int64_t cap,
                                      const WorkList &wl, int shortcut, cudaStream_t st);
+// Classification of every entry, or (list, device list_count) of listed real entries only,
+// 32 to a warp (the other entries' outputs are then left as they are).
 cudaError_t launch_xy_classify(int M, const XYSys &sys, const EPView &ep, double *theta,
                                int32_t *index, double *energy, double *min_eig,
                                double *log_abs_det,
-                               cudaStream_t st);
+                               cudaStream_t st, const int32_t *list = nullptr,
+                               const int32_t *list_count = nullptr);
 cudaError_t launch_quad_track(int n, const QSys &sys, const XYCtl &ctl, const EPView &ep,
                               const WorkList &wl, int grid, cudaStream_t st);
 cudaError_t launch_quad_refine_certify(int n, const QSys &sys, double tol_sol, double refine_eps,

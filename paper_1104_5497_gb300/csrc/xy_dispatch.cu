@@ -55,8 +55,9 @@ cudaError_t launch_xy_adjoint(int M, const XYSys &sys, int64_t count, const doub
 
 cudaError_t launch_xy_classify(int M, const XYSys &sys, const EPView &ep, double *theta,
                                int32_t *index, double *energy, double *min_eig,
-                               double *log_abs_det, cudaStream_t st) {
-#define C(MM) case MM: return launch_xy_classify_m##MM(sys, ep, theta, index, energy, min_eig, log_abs_det, st);
+                               double *log_abs_det, cudaStream_t st, const int32_t *list,
+                               const int32_t *list_count) {
+#define C(MM) case MM: return launch_xy_classify_m##MM(sys, ep, theta, index, energy, min_eig, log_abs_det, list, list_count, st);
     switch (M) { NPHC_FOR_EACH_M(C) default: return cudaErrorInvalidValue; }
 #undef C
 }

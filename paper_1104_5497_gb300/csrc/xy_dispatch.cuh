@@ -26,7 +26,8 @@
     cudaError_t launch_xy_adjoint_m##MM(const XYSys &, int64_t, const double *, const double *, \
                                         const double *, double *, cudaStream_t);              \
     cudaError_t launch_xy_classify_m##MM(const XYSys &, const EPView &, double *, int32_t *, \
-                                         double *, double *, double *, cudaStream_t);        \
+                                         double *, double *, double *, const int32_t *,      \
+                                         const int32_t *, cudaStream_t);                      \
     cudaError_t launch_xy_cauchy_m##MM(const XYSys &, const EGCtl &, const EPView &,        \
                                        const WorkList &, int32_t *, int32_t *, cudaStream_t);
 NPHC_FOR_EACH_M(NPHC_DECL)

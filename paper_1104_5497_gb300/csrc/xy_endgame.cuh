@@ -572,9 +572,19 @@ __global__ void __launch_bounds__(EG_BLOCK)
 template <int M>
 __global__ void __launch_bounds__(128)
     xy_classify_kernel(const __grid_constant__ XYSys S, const EPView ep, double *theta,
-                       int32_t *index, double *energy, double *min_eig, double *log_abs_det) {
-    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                       int32_t *index, double *energy, double *min_eig, double *log_abs_det,
+                       const int32_t *list, const int32_t *list_count) {
+    // every entry, or the listed ones: the real stationary points packed 32 to a warp, so
+    // that the FP64 Jacobi runs on full warps (GB300's FP64 pipe charges a warp instruction
+    // whatever the number of active lanes, and scattered real points cost a warp each)
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t cnt = ep.count;
+    int64_t e = i;
+    if (list) {
+        if (i >= *list_count) return;
+        e = list[i];
+        if (!NPHC_VALID(e >= 0 && e < cnt, 5)) return;
+    }
     if (e >= cnt) return;
     if (ep.cls[e] != NPHC_END_REAL) {
         index[e] = -1;

@@ -201,12 +201,14 @@ cudaError_t NPHC_CAT(launch_xy_adjoint_m, NPHC_INST_M)(const XYSys &sys, int64_t
 cudaError_t NPHC_CAT(launch_xy_classify_m, NPHC_INST_M)(const XYSys &sys, const EPView &ep,
                                                        double *theta, int32_t *index,
                                                        double *energy, double *min_eig,
-                                                       double *log_abs_det,
+                                                       double *log_abs_det, const int32_t *list,
+                                                       const int32_t *list_count,
                                                        cudaStream_t st) {
     if (ep.count <= 0) return cudaSuccess;
+    // a list is at most ep.count long (its length is on the device)
     const int grid = (int)((ep.count + 127) / 128);
     xy_classify_kernel<NPHC_INST_M><<<grid, 128, 0, st>>>(sys, ep, theta, index, energy, min_eig,
-                                                                   log_abs_det);
+                                                                   log_abs_det, list, list_count);
     nphc_launch_counter(1);
     return cudaGetLastError();
 }
