@@ -77,7 +77,13 @@ __global__ void flag_list_kernel(const int32_t *list, const int32_t *count, int3
 // ------------------------------------------------------------------ dedup --
 // Two certified endpoints of one solution lie within 2 (beta_a + beta_b) of each other
 // (each is within 2 beta of it).  Candidates are found through grids on four
-// coordinates (Re/Im of c_1 and of s_1) at DD_LEVELS pitches delta_L = delta_0 100^L.
+// coordinates at DD_LEVELS pitches delta_L = delta_0 100^L: the projections of the point
+// (Re z, Im z) in R^(2n) onto four fixed pseudo-random unit vectors.  A projection onto a
+// unit vector moves by at most the distance between two points, so every bound below
+// holds for them as for single coordinates; projections of the whole point, unlike
+// (c_1, s_1), do not put the many solutions that the ring's symmetries give equal first
+// coordinates into one cell (on the N = 9 ring up to 48 per cell, each pair then compared
+// in FP64).
 // Every hashed endpoint is listed under its cell at every level; an endpoint e looks up
 // level L(e), the finest with 4 beta_e <= DD_BAND delta_L, in its own cell plus, in
 // each coordinate within DD_BAND cells of a boundary, the neighbour across it.  A copy
@@ -105,15 +111,49 @@ __device__ __forceinline__ double dd_pitch(double delta0, int level) {
     return d;
 }
 
-// The four grid coordinates of entry e, in units of the pitch.
-__device__ __forceinline__ void dd_coords(const EPView &ep, int n, int64_t e, double inv_delta,
-                                          double (&v)[4]) {
+// The projections' weights, fixed pseudo-random numbers in [-1, 1) (splitmix64 of (i, r),
+// r = 2k: Re z_k, 2k + 1: Im z_k), and the prefix sums of their squares that normalise a
+// projection over the first 2n real coordinates; built at compile time.  A point has at
+// most DD_MAXR real coordinates (24 unknowns: the N = 13 ring).
+#define DD_MAXR 48
+struct DDTable {
+    double w[4][DD_MAXR];
+    double n2[4][DD_MAXR + 1];
+};
+constexpr uint64_t dd_splitmix(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+constexpr DDTable dd_make_table() {
+    DDTable t{};
+    for (int i = 0; i < 4; i++) {
+        t.n2[i][0] = 0.0;
+        for (int r = 0; r < DD_MAXR; r++) {
+            const uint64_t h = dd_splitmix(0x5851F42D4C957F2Dull ^ ((uint64_t)i << 32) ^ (uint64_t)r);
+            const double w = (double)(int64_t)h * (1.0 / 9223372036854775808.0);
+            t.w[i][r] = w;
+            t.n2[i][r + 1] = t.n2[i][r] + w * w;
+        }
+    }
+    return t;
+}
+__constant__ DDTable dd_tab = dd_make_table();
+
+// The four grid coordinates of entry e at pitch 1: its projections onto the four unit
+// vectors (the weights over the 2n real coordinates, normalised).
+__device__ __forceinline__ void dd_project(const EPView &ep, int n, int64_t e, double (&u)[4]) {
     const int64_t cnt = ep.count;
-    const int m = n / 2;
-    v[0] = ep.z_re[e] * inv_delta;
-    v[1] = ep.z_im[e] * inv_delta;
-    v[2] = ep.z_re[m * cnt + e] * inv_delta;
-    v[3] = ep.z_im[m * cnt + e] * inv_delta;
+    double dot[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k = 0; k < n; k++) {
+        const double re = ep.z_re[k * cnt + e], im = ep.z_im[k * cnt + e];
+#pragma unroll
+        for (int i = 0; i < 4; i++)
+            dot[i] = fma(dd_tab.w[i][2 * k], re, fma(dd_tab.w[i][2 * k + 1], im, dot[i]));
+    }
+#pragma unroll
+    for (int i = 0; i < 4; i++) u[i] = dot[i] / sqrt(dd_tab.n2[i][2 * n]);
 }
 
 __device__ __forceinline__ uint64_t dd_cell_key(int level, const long long (&q)[4]) {
@@ -154,11 +194,12 @@ __global__ void dedup_insert_kernel(const EPView ep, int n, double delta0, Dedup
     for (int L = 0; L < DD_LEVELS; L++) w.next[L * ep.count + e] = -1;
     if (!is_certified(ep.cls[e])) return;
     const uint64_t mask = (uint64_t)w.table_size - 1;
+    double u[4];
+    dd_project(ep, n, e, u);
     for (int L = 0; L < DD_LEVELS; L++) {
-        double v[4];
+        const double inv = 1.0 / dd_pitch(delta0, L);
         long long q[4];
-        dd_coords(ep, n, e, 1.0 / dd_pitch(delta0, L), v);
-        for (int i = 0; i < 4; i++) q[i] = (long long)floor(v[i]);
+        for (int i = 0; i < 4; i++) q[i] = (long long)floor(u[i] * inv);
         const unsigned long long key = dd_cell_key(L, q);
         unsigned long long *keys = w.keys + L * w.table_size;
         int32_t *head = w.head + L * w.table_size;
@@ -217,7 +258,9 @@ __global__ void dedup_match_kernel(const EPView ep, int n, double delta0, DedupS
     double v[4];
     long long q0[4];
     int dir[4];
-    dd_coords(ep, n, e, 1.0 / dd_pitch(delta0, L), v);
+    dd_project(ep, n, e, v);
+    const double inv = 1.0 / dd_pitch(delta0, L);
+    for (int i = 0; i < 4; i++) v[i] *= inv;
     for (int i = 0; i < 4; i++) {
         q0[i] = (long long)floor(v[i]);
         const double f = v[i] - (double)q0[i];
