@@ -446,9 +446,13 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
         p[k] = pt.get(k);
         q[k] = pt.get(M + k);
     }
-    cx<R> b0[M], b1[M];
+    // right-hand sides as sums over the columns: b_k = d_k - (i t / 2) (q_k sum_j J_kj X_j -
+    // p_k sum_j J_kj Y_j), X_j = sp_j conj(a^_j) q_j, Y_j = sq_j conj(b^_j) q_j, d_k the
+    // diagonal's own terms (J_kk = 0): real-times-complex sums in the inner loop
+    cx<R> sx0[M], sy0[M], sx1[M], sy1[M];
 #pragma unroll
-    for (int k = 0; k < M; k++) b0[k] = b1[k] = cx<R>{R(0), R(0)};
+    for (int k = 0; k < M; k++) sx0[k] = sy0[k] = sx1[k] = sy1[k] = cx<R>{R(0), R(0)};
+    const R hs = R(0.5) * s;
 
     // ---- build S column by column (columns j in a loop; rows unrolled)
 #pragma unroll 1
@@ -470,26 +474,25 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
         const cx<R> q0 = cscale(iv, rg0), q1 = cscale(iv, htg);
         const cx<R> px0 = cmulc(ah, q0), py0 = cmulc(bh, q0);
         const cx<R> px1 = cmulc(ah, q1), py1 = cmulc(bh, q1);
-        // the diagonal's own contributions, added to row j below
-        const cx<R> d0 = csub(rf0, cadd(cmul(Ajj, px0), cmul(Bjj, py0)));
-        const cx<R> d1 = csub(htf, cadd(cmul(Ajj, px1), cmul(Bjj, py1)));
         if (two_rhs && wr) out2.set(M + j, rg0);   // the residual's g row, for the recovery
-        // off-diagonal entries J_kj (q_k cb + p_k ca) and right-hand-side terms
-        // J_kj (q_k cpx - p_k cpy), with the factor i t / 2 and the scales folded in
-        const R hs = R(0.5) * s;
+        // the diagonal's own terms wait in row j of the right-hand-side columns (this
+        // column's residual entries there were read above)
+        A.set(j, M, csub(rf0, cadd(cmul(Ajj, px0), cmul(Bjj, py0))));
+        if (two_rhs) A.set(j, M + 1, csub(htf, cadd(cmul(Ajj, px1), cmul(Bjj, py1))));
+        // off-diagonal entries J_kj (q_k cb + p_k ca), with the factor i t / 2 and the scales
+        // folded in (J_jj = 0 makes the k == j entry vanish; it is set below)
         const cx<R> cb = cmul_i(cscale(hs * sp, bh)), ca = cmul_i(cscale(hs * sq, ah));
-        const cx<R> cpx0 = cmul_i(cscale(hs * sp, px0)), cpy0 = cmul_i(cscale(hs * sq, py0));
-        const cx<R> cpx1 = cmul_i(cscale(hs * sp, px1)), cpy1 = cmul_i(cscale(hs * sq, py1));
+        const cx<R> x0 = cscale(sp, px0), y0 = cscale(sq, py0);
+        const cx<R> x1 = cscale(sp, px1), y1 = cscale(sq, py1);
 #pragma unroll
         for (int k = 0; k < M; k++) {
-            // J_jj = 0 makes the k == j term vanish
             const R Jkj = J[k * NPHC_JSTRIDE + j];
             A.set(k, j, cscale(Jkj, cadd(cmul(q[k], cb), cmul(p[k], ca))));
-            b0[k] = csub(b0[k], cscale(Jkj, csub(cmul(q[k], cpx0), cmul(p[k], cpy0))));
-            if (two_rhs) b1[k] = csub(b1[k], cscale(Jkj, csub(cmul(q[k], cpx1), cmul(p[k], cpy1))));
-            if (k == j) {
-                b0[k] = cadd(b0[k], d0);
-                b1[k] = cadd(b1[k], d1);
+            sx0[k] = cx<R>{fma(Jkj, x0.re, sx0[k].re), fma(Jkj, x0.im, sx0[k].im)};
+            sy0[k] = cx<R>{fma(Jkj, y0.re, sy0[k].re), fma(Jkj, y0.im, sy0[k].im)};
+            if (two_rhs) {
+                sx1[k] = cx<R>{fma(Jkj, x1.re, sx1[k].re), fma(Jkj, x1.im, sx1[k].im)};
+                sy1[k] = cx<R>{fma(Jkj, y1.re, sy1[k].re), fma(Jkj, y1.im, sy1[k].im)};
             }
         }
         A.set(j, j, csub(cmul(Ajj, bh), cmul(Bjj, ah)));
@@ -498,8 +501,9 @@ __device__ __forceinline__ bool xy_solve(const R *__restrict__ J, const SMat<M, 
     // right-hand sides into columns M and M + 1
 #pragma unroll
     for (int k = 0; k < M; k++) {
-        A.set(k, M, b0[k]);
-        if (two_rhs) A.set(k, M + 1, b1[k]);
+        A.set(k, M, csub(A.get(k, M), cmul_i(cscale(hs, csub(cmul(q[k], sx0[k]), cmul(p[k], sy0[k]))))));
+        if (two_rhs)
+            A.set(k, M + 1, csub(A.get(k, M + 1), cmul_i(cscale(hs, csub(cmul(q[k], sx1[k]), cmul(p[k], sy1[k]))))));
     }
 
     bool ok = aug_lu_solve<M, R, BLOCK>(A, two_rhs, kest);
