@@ -382,18 +382,27 @@ struct EGXY {
 // the solution tolerance: the equations are quadratic, the Jacobian's entries grow like
 // ||z|| and an isolated solution near the solution set at infinity has a smallest singular
 // value shrinking like 1 / ||z|| (a solution of norm 1e6 has a condition number ~1e12).
+// The same from a factorisation already made at the point in G: fro = ||DP||_F, dn =
+// ||DP^-1 P|| from its solve (inv_fro takes D as scratch).
+template <class Q>
+__device__ bool eg_certify_factored(const EG<Q::DIM> &G, const typename Q::Sys &S, double fro,
+                                    double dn, double &beta, double &invF) {
+    beta = dn;
+    invF = Q::inv_fro(G, S);
+    double zi = 0.0;
+#pragma unroll 1
+    for (int k = 0; k < Q::NZ; k++) zi = fmax(zi, sqrt(cabs2(Q::zget(G, k))));
+    return isfinite(beta) && isfinite(invF) && fro * invF <= S.kappa_sing * fmax(1.0, zi * zi);
+}
+
 template <class Q>
 __device__ bool eg_beta_invnorm_p(const EG<Q::DIM> &G, const typename Q::Sys &S, double &beta,
                                   double &invF, double &res) {
     res = Q::minus_p(G, S);
     if (!Q::factor(G, S)) return false;
     const double fro = Q::jac_fro(G, S);
-    beta = sqrt(Q::solve(G, S));
-    invF = Q::inv_fro(G, S);
-    double zi = 0.0;
-#pragma unroll 1
-    for (int k = 0; k < Q::NZ; k++) zi = fmax(zi, sqrt(cabs2(Q::zget(G, k))));
-    return isfinite(beta) && isfinite(invF) && fro * invF <= S.kappa_sing * fmax(1.0, zi * zi);
+    const double dn = sqrt(Q::solve(G, S));
+    return eg_certify_factored<Q>(G, S, fro, dn, beta, invF);
 }
 
 // Refinement and certification of entry e.  Returns true when e still needs the
@@ -426,35 +435,53 @@ __device__ bool eg_refine_certify_one(const EG<Q::DIM> &G, const typename Q::Sys
     for (int k = 0; k < NZ; k++) Q::zset(G, k, cx<double>{ep.z_re[k * cnt + e], ep.z_im[k * cnt + e]});
     int cls = NPHC_END_SINGULAR;
     bool finite = true;
-    // Newton refinement on P
+    double beta = INFINITY, invF = INFINITY, res = INFINITY;
+    bool certified = false, cert_ok = false;
+    // Newton refinement on P.  The iteration whose correction meets refine_eps certifies its
+    // own point z_k from the factorisation it has just made (beta = ||dz_k||, exactly what a
+    // separate certification at z_k computes), and the output is z_k's Newton iterate
+    // z_k + dz_k, closer still to the same zero: one evaluation, factorisation and solve
+    // less than certifying the output point afresh
 #pragma unroll 1
     for (int it = 0; it < refine_iters; it++) {
-        Q::minus_p(G, S);
+        const double rk = Q::minus_p(G, S);
         if (!Q::factor(G, S)) break;
         const double dn = sqrt(Q::solve(G, S));
-        if (sc && it == 0) {
-            double z0 = 0.0;
+        double z2 = 0.0;
 #pragma unroll 1
-            for (int k = 0; k < NZ; k++) z0 += cabs2(Q::zget(G, k));
-            if (!(dn <= SHORTCUT_TRUST * (1.0 + sqrt(z0)))) return false;   // not in a basin
+        for (int k = 0; k < NZ; k++) z2 += cabs2(Q::zget(G, k));
+        if (sc && it == 0 && !(dn <= SHORTCUT_TRUST * (1.0 + sqrt(z2)))) return false;   // not in a basin
+        if (!isfinite(dn) || !isfinite(z2)) {
+            finite = false;
+            break;
+        }
+        const bool last = dn <= refine_eps * (1.0 + sqrt(z2));
+        const EGVec Step = last ? G.v(EGLayout<Q::DIM>::R) : Dv;
+        if (last) {
+#pragma unroll 1
+            for (int k = 0; k < NZ; k++) Step.set(k, Dv.get(k));   // inv_fro takes D as scratch
+            const double fro = Q::jac_fro(G, S);
+            cert_ok = eg_certify_factored<Q>(G, S, fro, dn, beta, invF);
+            res = rk;
+            certified = true;
         }
         double zn = 0.0;
 #pragma unroll 1
         for (int k = 0; k < NZ; k++) {
-            const cx<double> zk = cadd(Q::zget(G, k), Dv.get(k));
+            const cx<double> zk = cadd(Q::zget(G, k), Step.get(k));
             Q::zset(G, k, zk);
             zn += cabs2(zk);
         }
-        if (!isfinite(dn) || !isfinite(zn)) {
+        if (!isfinite(zn)) {
             finite = false;
             break;
         }
-        if (dn <= refine_eps * (1.0 + sqrt(zn))) break;
+        if (last) break;
     }
-    double beta = INFINITY, invF = INFINITY, res = INFINITY;
+    if (finite && !certified) cert_ok = eg_beta_invnorm_p<Q>(G, S, beta, invF, res);
     double alpha = INFINITY, gam = INFINITY;
     bool real_test = false;
-    if (finite && eg_beta_invnorm_p<Q>(G, S, beta, invF, res)) {
+    if (finite && cert_ok) {
         gam = invF * Q::d2norm(S);
         alpha = beta * gam;
         // Delta_sol relative to the size of the (quadratic) terms: max(1, ||z||_inf^2)
