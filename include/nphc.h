@@ -254,7 +254,9 @@ nphc_status nphc_track(const nphc_system *sys, const nphc_options *opt, nphc_pre
  * of Smale's constant: an FP64 test keeps a margin where alphaCertified is exact);
  * real when z and Re z share their zero (alpha < 0.03, ||Im z|| < 1/(20 gamma)) and the
  * same test passes at Re z, otherwise non-real when ||Im z|| > 2 beta, else undecided.
- * Writes z
+ * The certificate is taken at the iterate whose Newton correction met the refinement
+ * tolerance, from that iteration's own factorisation (beta = the correction's norm); z is
+ * its Newton iterate, closer still to the same zero.  Writes z
  * (refined), cls, alpha, beta, gamma, resid.  Other statuses get NPHC_END_NONE
  * (diverged) or NPHC_END_FAILED.  list / list_count as in nphc_track. */
 nphc_status nphc_refine_certify(const nphc_system *sys, const nphc_options *opt,
