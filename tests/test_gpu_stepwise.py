@@ -154,3 +154,34 @@ def test_refinement_scratch_matches_shared_memory(N, sigma):
     for e in both:
         assert cls[e] == full["cls"][e], e
         assert np.array_equal(z[e], full["z"][e]), (e, z[e], full["z"][e])
+
+
+@pytest.mark.parametrize("N,sigma", [(7, 0.75), (9, 0.75)])
+def test_solve_classification_matches_full_scan(N, sigma):
+    """A solve classifies a compacted list of its real stationary points (32 to a warp);
+    nphc_classify scans every entry.  The arithmetic per point is the same, so angles,
+    indices, energies and log|det H| agree bit for bit, and every other entry of the scan
+    has index -1."""
+    import torch
+    N_ = nphc()
+    inst = I.ring(N, sigma, 11)
+    system = N_.System(N, sigma)
+    res = N_.solve(system, N_.options_default(gamma=inst.gamma))
+    sps = res.stationary_points()
+    full = res.endpoints()
+    P = system.npaths
+    ep = device_endpoints(N_, full["z"], np.arange(P), cls=full["cls"], status=full["status"])
+    M = N - 1
+    theta = torch.zeros(M, P, dtype=torch.float64, device="cuda")
+    index = torch.zeros(P, dtype=torch.int32, device="cuda")
+    energy = torch.zeros(P, dtype=torch.float64, device="cuda")
+    logdet = torch.zeros(P, dtype=torch.float64, device="cuda")
+    N_.classify(system, ep, theta, index, energy, None, logdet)
+    torch.cuda.synchronize()
+    th, ix, en, ld = theta.cpu().numpy().T, index.cpu().numpy(), energy.cpu().numpy(), logdet.cpu().numpy()
+    real = full["cls"] == N_.END_REAL
+    assert np.all(ix[~real] == -1)
+    assert sorted(sps["path"].tolist()) == sorted(np.nonzero(real)[0].tolist())
+    for i, e in enumerate(sps["path"]):
+        assert np.array_equal(sps["theta"][i], th[e]), e
+        assert sps["index"][i] == ix[e] and sps["energy"][i] == en[e] and sps["log_abs_det"][i] == ld[e], e
