@@ -32,8 +32,10 @@
 // FP32 pass (ctl.handoff = 1): on a step size underflow, ten consecutive rejects, a
 // crawl near t = 1 (1 - t failing to halve within crawl_steps accepted steps), its own
 // (smaller) attempt budget or a radius crossing within RDIV_BAND close to t = 1, a path
-// is handed to FP64 (NPHC_PATH_HANDOFF) with the (z, t, h) where it entered the end
-// zone 1 - t < CRAWL_ZONE (its current state if it never got there).  FP64 tracks like
+// is handed to FP64 (NPHC_PATH_HANDOFF) with the (z, t, h) of its last clean accepted
+// point in the end zone 1 - t < CRAWL_ZONE (accepted right after another accepted step),
+// or of its last accepted point if it never got there; a converged step whose condition
+// estimate exceeds ctl.kappa ends it the same way (NPHC_PATH_HANDOFF_COND).  FP64 tracks like
 // the oracle: no crawl test, the same step budget and minimum step.  The FP32 bound on
 // the first correction (trust_fp32) keeps its accepted steps no longer than the FP64
 // tolerance allows, so that it does not step across a sharp turn of the path onto a
