@@ -27,9 +27,14 @@
 // needs only 2M triangular solves after one Householder QR of S (stored: R above the
 // diagonal with a real diagonal, the reflectors below, conj(tau) aside).
 //
-// Storage: one endpoint per thread, everything in shared memory, interleaved across the
-// 32 threads of a block (element i of a thread's array at [i * 32 + lane]), so that the
-// rolled loops index it at run time without local memory.
+// The refinement certifies the iterate whose Newton correction met the tolerance, from
+// the factorisation of that iteration, and outputs its Newton iterate.
+//
+// Storage: one endpoint per thread, interleaved across the 32 threads of a block
+// (element i of a thread's array at [i * 32 + lane]) so that the rolled loops index it
+// at run time without local memory: the per-site arrays, point and vectors in shared
+// memory, the M x M factor in shared memory too or, when a solve provides a scratch
+// buffer, in global memory (L2-resident), which leaves room for more warps per SM.
 #pragma once
 
 #include "nphc_internal.cuh"
