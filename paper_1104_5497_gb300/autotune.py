@@ -7,7 +7,7 @@ same endpoints bit for bit): the FP32 tracker over its resident blocks per SM
 one path per warp at 1 to 4 blocks per SM (`list_blocks_per_sm`).
 
 Stage 2 (gated by parity): the FP64 lists' threads per path (`threads_per_path`: one path
-per warp with an LU solve, or one per thread with a Householder QR, whose rounding differs)
+per warp with the solve laid out over the lanes, or one per thread; their rounding differs)
 and the FP32 pass's step control, the corrector's iteration cap (`max_newton_fp32`) and
 tolerance (`eps_fp32`), which decide which steps it accepts and which paths it hands to
 FP64.  Each candidate runs the calibration sample through the FP32 pass, the FP64
