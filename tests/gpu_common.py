@@ -48,12 +48,14 @@ def assert_same_point_sets(za, zb, rel=1e-10):
     assert len(np.unique(partner)) == len(zb)
 
 
-def compare_with_oracle(N, sigma, gamma, prec, ref=None):
+def compare_with_oracle(N, sigma, gamma, prec, ref=None, system=None):
     """Solve on the GPU and check: certified real and non-real sets equal the oracle's
     (within 1e-10 relative, one to one), the real SPs carry the same theta, index and
-    energy."""
+    energy.  system: a prepared system (e.g. with disordered couplings; ref must then be
+    the oracle's solve of the same couplings)."""
     N_ = nphc()
-    system = N_.System(N, sigma)
+    if system is None:
+        system = N_.System(N, sigma)
     res = N_.solve(system, N_.options_default(gamma=gamma, precision=prec))
     ep = res.endpoints()
     sps = res.stationary_points()

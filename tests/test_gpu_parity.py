@@ -62,3 +62,16 @@ def test_disordered_ring():
     c = res.counts()
     assert c["real"] == (ref["cls"] == O.C_REAL).sum()
     assert c["nonreal"] == (ref["cls"] == O.C_NONREAL).sum()
+
+
+def test_disordered_n9_ring_point_sets():
+    """An N = 9 ring of the 64-instance batch workload (per-pair disorder, 65,536 paths) in
+    mixed precision: the certified real and non-real sets are the oracle's one to one, and
+    every real SP has the oracle's angles, index and energy."""
+    N_ = nphc()
+    inst = I.workload_batch64()[0]
+    assert inst.N == 9
+    J = N_.xy_couplings(inst.N, inst.sigma, inst.g, inst.eps)
+    system = N_.System(inst.N, inst.sigma, J)
+    ref = O.solve_xy(inst.N, inst.sigma, inst.gamma, g=inst.g, eps=inst.eps)
+    compare_with_oracle(inst.N, inst.sigma, inst.gamma, N_.PREC_MIXED, ref=ref, system=system)
